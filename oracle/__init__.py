@@ -1,0 +1,139 @@
+"""FP64 CPU oracle for landmark geodesic shooting -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product library never does.
+
+The arithmetic lives in ``oracle.c`` (plain double loops, OpenMP over target
+landmarks).  This module compiles it with gcc on first use (or via
+:func:`build`) and exposes numpy-in / numpy-out wrappers.  Arrays are (N, 3)
+float64, row-major.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (gcc, OpenMP, no FMA contraction so
+    that x86 and Arm hosts round identically)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+               "-Wall", "-Wextra", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            i64, cint, cd = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+            lib.orc_set_threads.argtypes = [cint]
+            lib.orc_max_threads.restype = cint
+            lib.orc_step_forward.argtypes = [i64, cd, _D, _D, _D, _D]
+            lib.orc_step_backward.argtypes = [i64, cd, _D, _D, _D, _D, _D, _D]
+            lib.orc_hamiltonian.argtypes = [i64, cd, _D, _D]
+            lib.orc_hamiltonian.restype = cd
+            lib.orc_shoot_forward.argtypes = [i64, cint, cd, _D, _D, _D, _D, _D, _D]
+            lib.orc_loss.argtypes = [i64, cint, cd, cd, _D, _D, _D]
+            lib.orc_loss.restype = cd
+            lib.orc_shoot_gradient.argtypes = [i64, cint, cd, cd, _D, _D, _D, _D, _D, _D, _D, _D]
+            lib.orc_shoot_gradient.restype = cd
+            lib.orc_velocity.argtypes = [i64, _D, i64, _D, _D, cd, _D]
+            _lib = lib
+    return _lib
+
+
+def _in(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.ndim != 2 or a.shape[1] != 3 or (n is not None and a.shape[0] != n):
+        raise ValueError("expected an (N, 3) array, got shape %r" % (a.shape,))
+    return a
+
+
+def _p(a):
+    return a.ctypes.data_as(_D) if a is not None else None
+
+
+def set_threads(n: int) -> None:
+    _load().orc_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(_load().orc_max_threads())
+
+
+def step_forward(q, p, sigma):
+    """StepForward: returns (Hq, Hp) of Eq. 2 at (q, p)."""
+    q = _in(q); n = q.shape[0]; p = _in(p, n)
+    Hq = np.empty_like(q); Hp = np.empty_like(q)
+    _load().orc_step_forward(n, float(sigma), _p(q), _p(p), _p(Hq), _p(Hp))
+    return Hq, Hp
+
+
+def step_backward(q, p, alpha, beta, sigma):
+    """StepBackward: returns (dalpha, dbeta), the adjoint pair sums."""
+    q = _in(q); n = q.shape[0]
+    p, alpha, beta = _in(p, n), _in(alpha, n), _in(beta, n)
+    da = np.empty_like(q); db = np.empty_like(q)
+    _load().orc_step_backward(n, float(sigma), _p(q), _p(p), _p(alpha), _p(beta), _p(da), _p(db))
+    return da, db
+
+
+def hamiltonian(q, p, sigma) -> float:
+    q = _in(q); p = _in(p, q.shape[0])
+    return float(_load().orc_hamiltonian(q.shape[0], float(sigma), _p(q), _p(p)))
+
+
+def shoot_forward(q0, p0, T, sigma, trajectory=False):
+    """Forward flow; returns (q1, p1) or (q1, p1, traj_q, traj_p) with
+    trajectories shaped (T+1, N, 3)."""
+    q0 = _in(q0); n = q0.shape[0]; p0 = _in(p0, n)
+    q1 = np.empty_like(q0); p1 = np.empty_like(q0)
+    tq = tp = None
+    if trajectory:
+        tq = np.empty((T + 1, n, 3)); tp = np.empty((T + 1, n, 3))
+    _load().orc_shoot_forward(n, int(T), float(sigma), _p(q0), _p(p0), _p(q1), _p(p1), _p(tq), _p(tp))
+    return (q1, p1, tq, tp) if trajectory else (q1, p1)
+
+
+def loss(q0, p0, target, T, sigma, lam) -> float:
+    q0 = _in(q0); n = q0.shape[0]
+    p0, target = _in(p0, n), _in(target, n)
+    return float(_load().orc_loss(n, int(T), float(sigma), float(lam), _p(q0), _p(p0), _p(target)))
+
+
+def shoot_gradient(q0, p0, target, T, sigma, lam):
+    """ComputeGradient: returns dict(loss, grad_p0, grad_q0, q1, p1, H0)."""
+    q0 = _in(q0); n = q0.shape[0]
+    p0, target = _in(p0, n), _in(target, n)
+    gp = np.empty_like(q0); gq = np.empty_like(q0)
+    q1 = np.empty_like(q0); p1 = np.empty_like(q0)
+    h0 = ctypes.c_double(0.0)
+    L = _load().orc_shoot_gradient(n, int(T), float(sigma), float(lam), _p(q0), _p(p0), _p(target),
+                                   _p(gp), _p(gq), _p(q1), _p(p1), ctypes.byref(h0))
+    return dict(loss=float(L), grad_p0=gp, grad_q0=gq, q1=q1, p1=p1, H0=float(h0.value))
+
+
+def velocity(x, q, p, sigma):
+    """Eq. 4 velocity field at query points x (M, 3)."""
+    x = _in(x); q = _in(q); p = _in(p, q.shape[0])
+    v = np.empty_like(x)
+    _load().orc_velocity(x.shape[0], _p(x), q.shape[0], _p(q), _p(p), float(sigma), _p(v))
+    return v

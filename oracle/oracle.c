@@ -1,0 +1,263 @@
+/*
+ * FP64 CPU oracle for landmark matching by geodesic shooting
+ * (J. Wang, "Fast geodesic shooting for landmark matching using CUDA").
+ *
+ * TEST INFRASTRUCTURE.  Only the test suite, the package smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  The product (the CUDA
+ * library under paper_1907_04839_gb300/) never calls it, shares no code,
+ * header, table or constant with it, and fails loudly when its own CUDA
+ * library is missing.
+ *
+ * Everything here is plain double-precision C: straightforward double loops
+ * over landmark pairs i, j (the loop structure of Algorithm 2, with the
+ * per-target local accumulator that Section 2.2 recommends), OpenMP over the
+ * target index i only.  No blocking, fusion, reordering or approximation.
+ *
+ * Notation (Section 2.1): q_i, p_i in R^3 are landmark positions and momenta,
+ * N landmarks, Gaussian kernel g_ij = exp(-||q_i - q_j||^2 / (2 sigma^2)),
+ * s = 1/sigma^2, d_ij = q_i - q_j, c_ij = p_i . p_j.
+ *
+ * Readings of the garbled extraction (each is listed in the design doc):
+ *   Eq. 1     H(p, q) = 1/2 <p, K(q) p> = 1/2 sum_ij g_ij p_i . p_j.
+ *   Eq. 2     dq/dt = Hp = dH/dp,  dp/dt = -Hq = -dH/dq, so
+ *             Hp_i = sum_j g_ij p_j,  Hq_i = -s sum_j c_ij g_ij d_ij.
+ *   Alg. 2    the kernel is exp(-r^2 / (2 sigma^2)), sigma the Gaussian std.
+ *   Alg. 1    dt = 1/T; T simultaneous explicit Euler steps from q0, p0:
+ *             q <- q + dt Hp(q, p),  p <- p - dt Hq(q, p).
+ *   Eq. 3     loss L(p0) = H(p0, q0) + lambda ||q(1) - target||^2, minimised.
+ *   Alg. 1    the adjoint runs backwards through the same T Euler steps.  With
+ *             alpha = dL/dq and beta = dL/dp (through the flow), one reverse
+ *             step is alpha <- alpha + dt dalpha, beta <- beta + dt dbeta with
+ *             (dalpha, dbeta) the transposed Jacobian of (Hp, -Hq) applied to
+ *             (alpha, beta) -- StepBackward, whose formula the paper omits:
+ *               e_ij = beta_i - beta_j,  u_ij = alpha_i . p_j + alpha_j . p_i,
+ *               dalpha_i = s sum_j g_ij [ c_ij e_ij - (u_ij + s c_ij e_ij.d_ij) d_ij ]
+ *               dbeta_i  =   sum_j g_ij [ alpha_j + s (e_ij . d_ij) p_j ]
+ *             started from alpha(1) = 2 lambda (q(1) - target), beta(1) = 0.
+ *             Gradient: dL/dp0 = beta(0) + Hp(q0, p0), dL/dq0 = alpha(0) + Hq(q0, p0).
+ *   Eq. 4     v(x, t) = sum_l g(||q_l(t) - x||) p_l(t).
+ *
+ * Pins (tests/test_oracle_pins.py) tie these functions to the mathematics:
+ * single landmark moves on a straight line; total momentum is conserved;
+ * H drift falls at first order in dt; two-body head-on reduction to a scalar
+ * recursion; rigid-motion invariance; the closed-form gradient at p0 = 0;
+ * lambda = 0; a dense K matrix-vector product; brute-force central finite
+ * differences of the loss; and an independent autograd of the Euler loop.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* Gaussian kernel G_sigma of Section 2.1 on a squared distance. */
+static double gauss(double r2, double sigma) { return exp(-r2 / (2.0 * sigma * sigma)); }
+
+/* StepForward (Algorithm 2): Hq and Hp of Eq. 2 at state (q, p). */
+void orc_step_forward(int64_t n, double sigma, const double* q, const double* p,
+                      double* Hq, double* Hp) {
+    const double s = 1.0 / (sigma * sigma);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double hq[3] = {0, 0, 0}, hp[3] = {0, 0, 0};
+        for (int64_t j = 0; j < n; ++j) {
+            double d[3], r2 = 0.0, c = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                d[k] = q[3 * i + k] - q[3 * j + k];
+                r2 += d[k] * d[k];
+                c += p[3 * i + k] * p[3 * j + k];
+            }
+            const double g = gauss(r2, sigma);
+            for (int k = 0; k < 3; ++k) {
+                hp[k] += g * p[3 * j + k];
+                hq[k] += -s * c * g * d[k];
+            }
+        }
+        for (int k = 0; k < 3; ++k) {
+            Hq[3 * i + k] = hq[k];
+            Hp[3 * i + k] = hp[k];
+        }
+    }
+}
+
+/* StepBackward: the transposed Jacobian of (Hp, -Hq) at (q, p) applied to the
+ * adjoint (alpha, beta) of the state after the step.  See the header. */
+void orc_step_backward(int64_t n, double sigma, const double* q, const double* p,
+                       const double* alpha, const double* beta,
+                       double* dalpha, double* dbeta) {
+    const double s = 1.0 / (sigma * sigma);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double da[3] = {0, 0, 0}, db[3] = {0, 0, 0};
+        for (int64_t j = 0; j < n; ++j) {
+            double d[3], e[3], r2 = 0.0, c = 0.0, ed = 0.0, u = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                d[k] = q[3 * i + k] - q[3 * j + k];
+                e[k] = beta[3 * i + k] - beta[3 * j + k];
+                r2 += d[k] * d[k];
+                c += p[3 * i + k] * p[3 * j + k];
+                ed += e[k] * d[k];
+                u += alpha[3 * i + k] * p[3 * j + k] + alpha[3 * j + k] * p[3 * i + k];
+            }
+            const double g = gauss(r2, sigma);
+            for (int k = 0; k < 3; ++k) {
+                da[k] += s * g * (c * e[k] - (u + s * c * ed) * d[k]);
+                db[k] += g * (alpha[3 * j + k] + s * ed * p[3 * j + k]);
+            }
+        }
+        for (int k = 0; k < 3; ++k) {
+            dalpha[3 * i + k] = da[k];
+            dbeta[3 * i + k] = db[k];
+        }
+    }
+}
+
+/* Eq. 1: H(p, q) = 1/2 sum_i sum_j g_ij p_i . p_j. */
+double orc_hamiltonian(int64_t n, double sigma, const double* q, const double* p) {
+    double h = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : h)
+    for (int64_t i = 0; i < n; ++i) {
+        double hi = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            double r2 = 0.0, c = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                const double d = q[3 * i + k] - q[3 * j + k];
+                r2 += d * d;
+                c += p[3 * i + k] * p[3 * j + k];
+            }
+            hi += gauss(r2, sigma) * c;
+        }
+        h += hi;
+    }
+    return 0.5 * h;
+}
+
+/* Forward flow of Algorithm 1 (lines 2-9 with q_t <- q0): T explicit Euler
+ * steps of Eq. 2.  traj_q / traj_p, when non-null, receive all T+1 states as
+ * (T+1, N, 3) arrays. */
+void orc_shoot_forward(int64_t n, int T, double sigma, const double* q0, const double* p0,
+                       double* q1, double* p1, double* traj_q, double* traj_p) {
+    const double dt = 1.0 / T;
+    const size_t m = (size_t)n * 3;
+    double* q = malloc(m * sizeof(double));
+    double* p = malloc(m * sizeof(double));
+    double* Hq = malloc(m * sizeof(double));
+    double* Hp = malloc(m * sizeof(double));
+    memcpy(q, q0, m * sizeof(double));
+    memcpy(p, p0, m * sizeof(double));
+    if (traj_q) memcpy(traj_q, q, m * sizeof(double));
+    if (traj_p) memcpy(traj_p, p, m * sizeof(double));
+    for (int t = 0; t < T; ++t) {
+        orc_step_forward(n, sigma, q, p, Hq, Hp);
+        for (size_t k = 0; k < m; ++k) {
+            q[k] += Hp[k] * dt;
+            p[k] -= Hq[k] * dt;
+        }
+        if (traj_q) memcpy(traj_q + (size_t)(t + 1) * m, q, m * sizeof(double));
+        if (traj_p) memcpy(traj_p + (size_t)(t + 1) * m, p, m * sizeof(double));
+    }
+    memcpy(q1, q, m * sizeof(double));
+    memcpy(p1, p, m * sizeof(double));
+    free(q); free(p); free(Hq); free(Hp);
+}
+
+/* Eq. 3 objective: H(p0, q0) + lambda ||q(1) - target||^2. */
+double orc_loss(int64_t n, int T, double sigma, double lambda, const double* q0,
+                const double* p0, const double* target) {
+    const size_t m = (size_t)n * 3;
+    double* q1 = malloc(m * sizeof(double));
+    double* p1 = malloc(m * sizeof(double));
+    orc_shoot_forward(n, T, sigma, q0, p0, q1, p1, NULL, NULL);
+    double mis = 0.0;
+    for (size_t k = 0; k < m; ++k) mis += (q1[k] - target[k]) * (q1[k] - target[k]);
+    const double L = orc_hamiltonian(n, sigma, q0, p0) + lambda * mis;
+    free(q1); free(p1);
+    return L;
+}
+
+/* ComputeGradient of Algorithm 1: forward flow, loss, reverse sweep.
+ * Returns the loss; grad_p0 = dL/dp0 and grad_q0 = dL/dq0 (either may be
+ * null).  q1, p1 and H0 receive the end state and H(p0, q0) when non-null. */
+double orc_shoot_gradient(int64_t n, int T, double sigma, double lambda,
+                          const double* q0, const double* p0, const double* target,
+                          double* grad_p0, double* grad_q0,
+                          double* q1_out, double* p1_out, double* H0_out) {
+    const double dt = 1.0 / T;
+    const size_t m = (size_t)n * 3;
+    double* tq = malloc((size_t)(T + 1) * m * sizeof(double));
+    double* tp = malloc((size_t)(T + 1) * m * sizeof(double));
+    double* q1 = malloc(m * sizeof(double));
+    double* p1 = malloc(m * sizeof(double));
+    double* alpha = malloc(m * sizeof(double));
+    double* beta = malloc(m * sizeof(double));
+    double* da = malloc(m * sizeof(double));
+    double* db = malloc(m * sizeof(double));
+    double* Hq0 = malloc(m * sizeof(double));
+    double* Hp0 = malloc(m * sizeof(double));
+
+    orc_shoot_forward(n, T, sigma, q0, p0, q1, p1, tq, tp);
+    const double H0 = orc_hamiltonian(n, sigma, q0, p0);
+    double mis = 0.0;
+    for (size_t k = 0; k < m; ++k) mis += (q1[k] - target[k]) * (q1[k] - target[k]);
+    const double L = H0 + lambda * mis;
+
+    for (size_t k = 0; k < m; ++k) {
+        alpha[k] = 2.0 * lambda * (q1[k] - target[k]);
+        beta[k] = 0.0;
+    }
+    for (int t = T - 1; t >= 0; --t) {
+        orc_step_backward(n, sigma, tq + (size_t)t * m, tp + (size_t)t * m, alpha, beta, da, db);
+        for (size_t k = 0; k < m; ++k) {
+            alpha[k] += dt * da[k];
+            beta[k] += dt * db[k];
+        }
+    }
+    orc_step_forward(n, sigma, q0, p0, Hq0, Hp0);
+    for (size_t k = 0; k < m; ++k) {
+        if (grad_p0) grad_p0[k] = beta[k] + Hp0[k];
+        if (grad_q0) grad_q0[k] = alpha[k] + Hq0[k];
+    }
+    if (q1_out) memcpy(q1_out, q1, m * sizeof(double));
+    if (p1_out) memcpy(p1_out, p1, m * sizeof(double));
+    if (H0_out) *H0_out = H0;
+    free(tq); free(tp); free(q1); free(p1); free(alpha); free(beta);
+    free(da); free(db); free(Hq0); free(Hp0);
+    return L;
+}
+
+/* Eq. 4: velocity v(x) = sum_l g(||q_l - x||) p_l at m query points x. */
+void orc_velocity(int64_t m, const double* x, int64_t n, const double* q, const double* p,
+                  double sigma, double* v) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < m; ++i) {
+        double acc[3] = {0, 0, 0};
+        for (int64_t l = 0; l < n; ++l) {
+            double r2 = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                const double d = q[3 * l + k] - x[3 * i + k];
+                r2 += d * d;
+            }
+            const double g = gauss(r2, sigma);
+            for (int k = 0; k < 3; ++k) acc[k] += g * p[3 * l + k];
+        }
+        for (int k = 0; k < 3; ++k) v[3 * i + k] = acc[k];
+    }
+}

@@ -1,0 +1,144 @@
+/*
+ * gshoot — landmark matching by geodesic shooting on one GB300 (sm_103a).
+ *
+ * C ABI of the library libgshoot.so.  It evaluates the method of
+ * J. Wang, "Fast geodesic shooting for landmark matching using CUDA":
+ * 3-D landmarks q_i, momenta p_i (i < N), Gaussian kernel
+ * g_ij = exp(-||q_i - q_j||^2 / (2 sigma^2)), Hamiltonian
+ * H = 1/2 sum_ij g_ij p_i . p_j (Eq. 1), Hamiltonian flow (Eq. 2) integrated by
+ * T explicit Euler steps of dt = 1/T (Algorithm 1), loss
+ * L(p0) = H(p0, q0) + lambda ||q(1) - target||^2 (Eq. 3), its gradient by the
+ * exact reverse sweep of those Euler steps, and L-BFGS over p0 (Section 2.1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Arrays.  Every landmark array is (N, 3) row-major float32, contiguous
+ *   (x0 y0 z0 x1 y1 z1 ...).  A pointer may be device memory (cudaMalloc,
+ *   managed) or host memory (pageable or pinned); the library checks with
+ *   cudaPointerGetAttributes and stages host arrays through its own device
+ *   workspace.  The caller owns every array; the library never keeps a pointer
+ *   past the call.
+ * Scalars.  Scalar outputs (double*, int32_t*) are host pointers and may be
+ *   NULL when not wanted.
+ * Streams.  `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *   Work is enqueued on it.  A call returns only after the stream has
+ *   finished the call's work when any output is a host pointer or a scalar
+ *   output is requested; otherwise the call is asynchronous and its outputs
+ *   are ready in stream order.
+ * Workspace.  The library owns one device workspace per CUDA device, grown on
+ *   demand and freed by gs_release_workspace().  Calls into the library are
+ *   serialised by a process-wide mutex.
+ * Status.  GS_OK (0) on success; a negative gs_status on error, in which case
+ *   the outputs are undefined and gs_last_error() describes the failure;
+ *   a positive status is a warning with valid outputs.
+ * Device errors.  Kernels record non-finite inputs and expired waits in a
+ *   device status word instead of faulting; the synchronous path reads it and
+ *   returns GS_ENONFINITE or GS_ETIMEOUT.
+ */
+#ifndef GSHOOT_H
+#define GSHOOT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gs_status {
+    GS_OK = 0,
+    GS_NOT_CONVERGED = 1,   /* register_landmarks stopped at max_iter */
+    GS_EINVAL = -1,         /* bad argument (N < 1, T < 1, sigma <= 0, NULL array, ...) */
+    GS_ENOMEM = -2,         /* device allocation failed */
+    GS_ECUDA = -3,          /* a CUDA runtime call failed (message in gs_last_error) */
+    GS_ETIMEOUT = -4,       /* a bounded device-side wait expired */
+    GS_ENONFINITE = -5,     /* an input or an intermediate was NaN or Inf */
+    GS_ENOLIB = -6          /* no usable CUDA device */
+} gs_status;
+
+/* Parameters of one registration problem (Algorithm 1 inputs, Section 2.2). */
+typedef struct gs_params {
+    int64_t N;          /* number of landmarks, >= 1 */
+    int32_t T;          /* number of Euler time steps, >= 1; dt = 1/T */
+    int32_t ckpt_every; /* 0: keep the whole trajectory; k > 0: keep the FP64
+                           state every k steps and recompute the rest in the
+                           reverse sweep */
+    double sigma;       /* Gaussian kernel standard deviation, > 0 */
+    double lambda;      /* weight of the landmark mismatch term of Eq. 3, >= 0 */
+    int32_t lbfgs_m;    /* L-BFGS memory (pairs kept), 1..64 (register only) */
+    int32_t max_iter;   /* L-BFGS iteration limit (register only) */
+    double grad_tol;    /* stop when ||g_k|| <= grad_tol ||g_0|| (register only) */
+} gs_params;
+
+/*
+ * step_forward — StepForward of Algorithm 2 / Algorithm 4 (Section 2.2, 2.5):
+ * the two derivative terms of Eq. 2 at state (q, p),
+ *   Hp_i = dH/dp_i =  sum_j g_ij p_j,
+ *   Hq_i = dH/dq_i = -(1/sigma^2) sum_j (p_i . p_j) g_ij (q_i - q_j).
+ * In: N, sigma, q, p.  Out: Hq, Hp (all (N,3) float32).
+ */
+gs_status step_forward(int64_t N, double sigma, const float* q, const float* p,
+                       float* Hq, float* Hp, void* stream);
+
+/*
+ * step_backward — StepBackward (Section 2.2; formula not printed in the paper):
+ * the transposed Jacobian of (Hp, -Hq) at (q, p) applied to the adjoint
+ * (alpha, beta) = (dL/dq, dL/dp) of the state after the step.  With
+ * e_ij = beta_i - beta_j, u_ij = alpha_i . p_j + alpha_j . p_i, s = 1/sigma^2:
+ *   dalpha_i = s sum_j g_ij [ c_ij e_ij - (u_ij + s c_ij e_ij . d_ij) d_ij ]
+ *   dbeta_i  =   sum_j g_ij [ alpha_j + s (e_ij . d_ij) p_j ]
+ * One reverse Euler step is alpha <- alpha + dt dalpha, beta <- beta + dt dbeta.
+ * In: N, sigma, q, p, alpha, beta.  Out: dalpha, dbeta.
+ */
+gs_status step_backward(int64_t N, double sigma, const float* q, const float* p,
+                        const float* alpha, const float* beta,
+                        float* dalpha, float* dbeta, void* stream);
+
+/*
+ * shoot_forward — the forward flow of Algorithm 1 (lines 2-9): T explicit
+ * Euler steps q <- q + dt Hp, p <- p - dt Hq from (q0, p0).
+ * In: prm (N, T, sigma used), q0, p0.  Out: q1, p1 = state at t = 1 (either
+ * may be NULL), *H0 = H(p0, q0) (Eq. 1) in FP64 (NULL to skip).
+ */
+gs_status shoot_forward(const gs_params* prm, const float* q0, const float* p0,
+                        float* q1, float* p1, double* H0, void* stream);
+
+/*
+ * shoot_gradient — ComputeGradient of Algorithm 1: forward flow, the loss of
+ * Eq. 3, and the reverse sweep.
+ * In: prm (N, T, sigma, lambda, ckpt_every used), q0, p0, target.
+ * Out: *loss (FP64, NULL to skip), grad_p0 = dL/dp0 (NULL to skip),
+ *      grad_q0 = dL/dq0 (NULL to skip), all (N,3) float32.
+ */
+gs_status shoot_gradient(const gs_params* prm, const float* q0, const float* p0,
+                         const float* target, double* loss,
+                         float* grad_p0, float* grad_q0, void* stream);
+
+/*
+ * gs_time_pair_kernels — diagnostics (no counterpart in the paper): the
+ * average device time of one launch of each pair-sum kernel, StepForward and
+ * StepBackward, in the tile configuration shoot_gradient uses for prm->N.
+ * Runs shoot_gradient(prm, q0, p0, target) once to set up the trajectory and
+ * adjoint state, then launches each pair kernel `reps` times back to back on
+ * `stream` between two CUDA events (middle time step of the trajectory).
+ * Out: *fwd_ms, *bwd_ms (host, per launch); *launches_per_eval = kernel
+ * launches of one shoot_gradient call (NULL to skip any of them).
+ * Synchronises `stream`.
+ */
+gs_status gs_time_pair_kernels(const gs_params* prm, const float* q0, const float* p0,
+                               const float* target, int32_t reps, double* fwd_ms,
+                               double* bwd_ms, int32_t* launches_per_eval, void* stream);
+
+/* Message for the last error of the calling thread ("" if none). */
+const char* gs_last_error(void);
+
+/* Free the device workspace and cached CUDA graphs of every device. */
+void gs_release_workspace(void);
+
+/* Library ABI version: 100 * major + minor. */
+int32_t gs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSHOOT_H */

@@ -56,6 +56,9 @@ def _load():
             lib.orc_shoot_gradient.argtypes = [i64, cint, cd, cd, _D, _D, _D, _D, _D, _D, _D, _D]
             lib.orc_shoot_gradient.restype = cd
             lib.orc_velocity.argtypes = [i64, _D, i64, _D, _D, cd, _D]
+            _I = ctypes.POINTER(ctypes.c_int64)
+            lib.orc_step_forward_rows.argtypes = [i64, cd, _D, _D, i64, _I, _D, _D]
+            lib.orc_step_backward_rows.argtypes = [i64, cd, _D, _D, _D, _D, i64, _I, _D, _D]
             _lib = lib
     return _lib
 
@@ -93,6 +96,35 @@ def step_backward(q, p, alpha, beta, sigma):
     p, alpha, beta = _in(p, n), _in(alpha, n), _in(beta, n)
     da = np.empty_like(q); db = np.empty_like(q)
     _load().orc_step_backward(n, float(sigma), _p(q), _p(p), _p(alpha), _p(beta), _p(da), _p(db))
+    return da, db
+
+
+def _rows(rows):
+    r = np.ascontiguousarray(rows, dtype=np.int64)
+    return r, r.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+def step_forward_rows(q, p, sigma, rows):
+    """StepForward for the target landmarks ``rows`` only: (Hq, Hp), (m, 3)."""
+    q = _in(q); n = q.shape[0]; p = _in(p, n)
+    r, rp = _rows(rows)
+    if r.size and (r.min() < 0 or r.max() >= n):
+        raise IndexError("row index out of range")
+    Hq = np.empty((r.size, 3)); Hp = np.empty((r.size, 3))
+    _load().orc_step_forward_rows(n, float(sigma), _p(q), _p(p), r.size, rp, _p(Hq), _p(Hp))
+    return Hq, Hp
+
+
+def step_backward_rows(q, p, alpha, beta, sigma, rows):
+    """StepBackward for the target landmarks ``rows`` only: (dalpha, dbeta)."""
+    q = _in(q); n = q.shape[0]
+    p, alpha, beta = _in(p, n), _in(alpha, n), _in(beta, n)
+    r, rp = _rows(rows)
+    if r.size and (r.min() < 0 or r.max() >= n):
+        raise IndexError("row index out of range")
+    da = np.empty((r.size, 3)); db = np.empty((r.size, 3))
+    _load().orc_step_backward_rows(n, float(sigma), _p(q), _p(p), _p(alpha), _p(beta), r.size, rp,
+                                   _p(da), _p(db))
     return da, db
 
 

@@ -130,6 +130,67 @@ void orc_step_backward(int64_t n, double sigma, const double* q, const double* p
     }
 }
 
+/* StepForward restricted to the m target rows rows[0..m): (Hq, Hp) of those
+ * landmarks only, each summed over all N sources.  Output (m, 3). */
+void orc_step_forward_rows(int64_t n, double sigma, const double* q, const double* p,
+                           int64_t m, const int64_t* rows, double* Hq, double* Hp) {
+    const double s = 1.0 / (sigma * sigma);
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < m; ++r) {
+        const int64_t i = rows[r];
+        double hq[3] = {0, 0, 0}, hp[3] = {0, 0, 0};
+        for (int64_t j = 0; j < n; ++j) {
+            double d[3], r2 = 0.0, c = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                d[k] = q[3 * i + k] - q[3 * j + k];
+                r2 += d[k] * d[k];
+                c += p[3 * i + k] * p[3 * j + k];
+            }
+            const double g = gauss(r2, sigma);
+            for (int k = 0; k < 3; ++k) {
+                hp[k] += g * p[3 * j + k];
+                hq[k] += -s * c * g * d[k];
+            }
+        }
+        for (int k = 0; k < 3; ++k) {
+            Hq[3 * r + k] = hq[k];
+            Hp[3 * r + k] = hp[k];
+        }
+    }
+}
+
+/* StepBackward restricted to the m target rows rows[0..m).  Output (m, 3). */
+void orc_step_backward_rows(int64_t n, double sigma, const double* q, const double* p,
+                            const double* alpha, const double* beta, int64_t m,
+                            const int64_t* rows, double* dalpha, double* dbeta) {
+    const double s = 1.0 / (sigma * sigma);
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < m; ++r) {
+        const int64_t i = rows[r];
+        double da[3] = {0, 0, 0}, db[3] = {0, 0, 0};
+        for (int64_t j = 0; j < n; ++j) {
+            double d[3], e[3], r2 = 0.0, c = 0.0, ed = 0.0, u = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                d[k] = q[3 * i + k] - q[3 * j + k];
+                e[k] = beta[3 * i + k] - beta[3 * j + k];
+                r2 += d[k] * d[k];
+                c += p[3 * i + k] * p[3 * j + k];
+                ed += e[k] * d[k];
+                u += alpha[3 * i + k] * p[3 * j + k] + alpha[3 * j + k] * p[3 * i + k];
+            }
+            const double g = gauss(r2, sigma);
+            for (int k = 0; k < 3; ++k) {
+                da[k] += s * g * (c * e[k] - (u + s * c * ed) * d[k]);
+                db[k] += g * (alpha[3 * j + k] + s * ed * p[3 * j + k]);
+            }
+        }
+        for (int k = 0; k < 3; ++k) {
+            dalpha[3 * r + k] = da[k];
+            dbeta[3 * r + k] = db[k];
+        }
+    }
+}
+
 /* Eq. 1: H(p, q) = 1/2 sum_i sum_j g_ij p_i . p_j. */
 double orc_hamiltonian(int64_t n, double sigma, const double* q, const double* p) {
     double h = 0.0;

@@ -1,0 +1,142 @@
+"""gshoot: landmark matching by geodesic shooting on one GB300 (sm_103a).
+
+A thin Python binding over the C ABI of ``libgshoot.so`` (include/gshoot.h).
+The names are the same as in the ABI.  The binding only marshals arguments;
+the CUDA kernels of the library do every step of the computation.
+
+Arrays are (N, 3).  Two forms are accepted:
+* torch CUDA tensors.  They are cast to contiguous float32, and the work runs
+  on the current torch stream.  The outputs are CUDA tensors.
+* numpy arrays or CPU tensors.  The library stages them through its device
+  workspace and returns numpy float32 arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from ._lib import EXPORTS, GShootError, GsParams, check, load
+
+__all__ = [
+    "step_forward", "step_backward", "shoot_forward", "shoot_gradient",
+    "release_workspace", "version", "GShootError", "GsParams", "EXPORTS",
+]
+
+
+def _is_cuda_tensor(x) -> bool:
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        return False
+    return isinstance(x, torch.Tensor) and x.is_cuda
+
+
+class _Marshal:
+    """Pointers for one call: either all-device (torch) or all-host (numpy)."""
+
+    def __init__(self, first, n=None):
+        self.device = _is_cuda_tensor(first)
+        self.keep = []
+        if self.device:
+            import torch
+            self.torch = torch
+            self.dev = first.device
+            self.stream = ctypes.c_void_p(torch.cuda.current_stream(self.dev).cuda_stream)
+        else:
+            self.stream = ctypes.c_void_p(0)
+        self.n = n
+
+    def inp(self, x, name):
+        if x is None:
+            return None
+        if self.device:
+            if not _is_cuda_tensor(x):
+                raise TypeError("%s: expected a CUDA tensor like the other inputs" % name)
+            t = x.detach().to(device=self.dev, dtype=self.torch.float32).contiguous()
+            arr_shape = tuple(t.shape)
+            ptr = t.data_ptr()
+        else:
+            if hasattr(x, "detach"):
+                x = x.detach().cpu().numpy()
+            t = np.ascontiguousarray(x, dtype=np.float32)
+            arr_shape = t.shape
+            ptr = t.ctypes.data
+        if len(arr_shape) != 2 or arr_shape[1] != 3:
+            raise ValueError("%s: expected shape (N, 3), got %r" % (name, arr_shape))
+        if self.n is None:
+            self.n = arr_shape[0]
+        elif arr_shape[0] != self.n:
+            raise ValueError("%s: expected %d rows, got %d" % (name, self.n, arr_shape[0]))
+        self.keep.append(t)
+        return ctypes.c_void_p(ptr)
+
+    def out(self):
+        if self.device:
+            t = self.torch.empty((self.n, 3), dtype=self.torch.float32, device=self.dev)
+            ptr = t.data_ptr()
+        else:
+            t = np.empty((self.n, 3), dtype=np.float32)
+            ptr = t.ctypes.data
+        self.keep.append(t)
+        return t, ctypes.c_void_p(ptr)
+
+
+def _params(n, T, sigma, lam=0.0, ckpt_every=0, lbfgs_m=10, max_iter=100, grad_tol=1e-5):
+    return GsParams(N=int(n), T=int(T), ckpt_every=int(ckpt_every), sigma=float(sigma),
+                    lambda_=float(lam), lbfgs_m=int(lbfgs_m), max_iter=int(max_iter),
+                    grad_tol=float(grad_tol))
+
+
+def step_forward(q, p, sigma):
+    """StepForward: returns (Hq, Hp), the two derivative terms of Eq. 2."""
+    m = _Marshal(q)
+    pq, pp = m.inp(q, "q"), m.inp(p, "p")
+    Hq, oq = m.out()
+    Hp, op = m.out()
+    check(load().step_forward(m.n, float(sigma), pq, pp, oq, op, m.stream))
+    return Hq, Hp
+
+
+def step_backward(q, p, alpha, beta, sigma):
+    """StepBackward: returns (dalpha, dbeta), the adjoint pair sums of one
+    reverse Euler step (alpha <- alpha + dt dalpha, beta <- beta + dt dbeta)."""
+    m = _Marshal(q)
+    pq, pp, pa, pb = m.inp(q, "q"), m.inp(p, "p"), m.inp(alpha, "alpha"), m.inp(beta, "beta")
+    da, oa = m.out()
+    db, ob = m.out()
+    check(load().step_backward(m.n, float(sigma), pq, pp, pa, pb, oa, ob, m.stream))
+    return da, db
+
+
+def shoot_forward(q0, p0, T, sigma):
+    """Forward flow of Algorithm 1: returns (q1, p1, H0) with H0 = H(p0, q0)."""
+    m = _Marshal(q0)
+    pq, pp = m.inp(q0, "q0"), m.inp(p0, "p0")
+    prm = _params(m.n, T, sigma)
+    q1, o1 = m.out()
+    p1, o2 = m.out()
+    h0 = ctypes.c_double(0.0)
+    check(load().shoot_forward(ctypes.byref(prm), pq, pp, o1, o2, ctypes.byref(h0), m.stream))
+    return q1, p1, h0.value
+
+
+def shoot_gradient(q0, p0, target, T, sigma, lam, ckpt_every=0):
+    """ComputeGradient of Algorithm 1: returns (loss, dL/dp0, dL/dq0) for
+    L = H(p0, q0) + lam ||q(1) - target||^2."""
+    m = _Marshal(q0)
+    pq, pp, pt = m.inp(q0, "q0"), m.inp(p0, "p0"), m.inp(target, "target")
+    prm = _params(m.n, T, sigma, lam, ckpt_every)
+    gp, og = m.out()
+    gq, oq = m.out()
+    loss = ctypes.c_double(0.0)
+    check(load().shoot_gradient(ctypes.byref(prm), pq, pp, pt, ctypes.byref(loss), og, oq, m.stream))
+    return loss.value, gp, gq
+
+
+def release_workspace() -> None:
+    load().gs_release_workspace()
+
+
+def version() -> int:
+    return int(load().gs_version())

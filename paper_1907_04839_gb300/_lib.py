@@ -1,0 +1,85 @@
+"""ctypes loader for libgshoot.so (the C ABI declared in include/gshoot.h).
+
+There is no fallback.  If the library cannot be built or loaded, every entry
+point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import _build
+
+_lock = threading.Lock()
+_lib = None
+
+GS_STATUS = {
+    0: "GS_OK", 1: "GS_NOT_CONVERGED", -1: "GS_EINVAL", -2: "GS_ENOMEM", -3: "GS_ECUDA",
+    -4: "GS_ETIMEOUT", -5: "GS_ENONFINITE", -6: "GS_ENOLIB",
+}
+
+# Every symbol the header declares; tests check the library exports them all.
+EXPORTS = [
+    "step_forward", "step_backward", "shoot_forward", "shoot_gradient",
+    "gs_time_pair_kernels", "gs_last_error", "gs_release_workspace", "gs_version",
+]
+
+
+class GsParams(ctypes.Structure):
+    """Mirror of ``gs_params`` in include/gshoot.h."""
+    _fields_ = [
+        ("N", ctypes.c_int64),
+        ("T", ctypes.c_int32),
+        ("ckpt_every", ctypes.c_int32),
+        ("sigma", ctypes.c_double),
+        ("lambda_", ctypes.c_double),
+        ("lbfgs_m", ctypes.c_int32),
+        ("max_iter", ctypes.c_int32),
+        ("grad_tol", ctypes.c_double),
+    ]
+
+
+class GShootError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s (%d): %s" % (GS_STATUS.get(status, "?"), status, msg))
+        self.status = status
+
+
+def _declare(lib):
+    vp, fp, dp, i64, i32, cd = (ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                ctypes.c_int64, ctypes.c_int32, ctypes.c_double)
+    P = ctypes.POINTER(GsParams)
+    lib.step_forward.argtypes = [i64, cd, fp, fp, fp, fp, vp]
+    lib.step_backward.argtypes = [i64, cd, fp, fp, fp, fp, fp, fp, vp]
+    lib.shoot_forward.argtypes = [P, fp, fp, fp, fp, dp, vp]
+    lib.shoot_gradient.argtypes = [P, fp, fp, fp, dp, fp, fp, vp]
+    lib.gs_time_pair_kernels.argtypes = [P, fp, fp, fp, i32, dp, dp, ctypes.c_void_p, vp]
+    for name in ("step_forward", "step_backward", "shoot_forward", "shoot_gradient", "gs_time_pair_kernels"):
+        getattr(lib, name).restype = ctypes.c_int
+    lib.gs_last_error.restype = ctypes.c_char_p
+    lib.gs_last_error.argtypes = []
+    lib.gs_release_workspace.restype = None
+    lib.gs_version.restype = i32
+
+
+def load(build_if_missing: bool = True):
+    """Load libgshoot.so, building it first if it is absent or stale."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if build_if_missing:
+                path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError("libgshoot.so is not built; run paper_1907_04839_gb300._build.build()")
+            lib = ctypes.CDLL(path)
+            _declare(lib)
+            _lib = lib
+    return _lib
+
+
+def check(status: int) -> int:
+    if status < 0:
+        raise GShootError(status, load().gs_last_error().decode(errors="replace"))
+    return status

@@ -1,0 +1,598 @@
+// Host engine and C ABI of libgshoot.so.
+//
+// The engine owns one workspace per CUDA device:
+//  * the FP32 trajectory that the pair kernels read;
+//  * the FP64 master state;
+//  * the split partials;
+//  * staging buffers for host arrays;
+//  * the reduction scratch and the device status word;
+//  * a cache of instantiated CUDA graphs.
+// Each graph holds the T forward steps, and for gradients also the T reverse
+// steps: a pair-sum kernel followed by a combine kernel per step, linked by
+// programmatic dependent launch.  A call packs the inputs, replays the
+// graph, then copies the outputs out.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "gs_internal.h"
+#include "../../include/gshoot.h"
+
+namespace gs {
+
+namespace {
+
+thread_local std::string g_err;
+std::mutex g_mu;
+
+gs_status fail(gs_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+#define GS_CUDA(call)                                                                      \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(e_ == cudaErrorMemoryAllocation ? GS_ENOMEM : GS_ECUDA,                  \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                     \
+  } while (0)
+
+int round_up(long long x, int m) { return static_cast<int>((x + m - 1) / m * m); }
+
+struct GraphKey {
+  int kind;  // 0 forward only, 1 gradient
+  int n, T;
+  double sigma, lambda;
+  bool operator<(const GraphKey& o) const {
+    return std::tie(kind, n, T, sigma, lambda) < std::tie(o.kind, o.n, o.T, o.sigma, o.lambda);
+  }
+};
+
+struct Workspace {
+  int device = -1;
+  int num_sms = 0;
+  // capacities
+  int cap_npad = 0, cap_T = 0, cap_splits = 0;
+  int cap_red = 0;
+  std::vector<void*> allocs;
+  float4* traj_q = nullptr;  // (cap_T + 1) * cap_npad
+  float4* traj_p = nullptr;
+  float4* adj_a = nullptr;   // cap_npad
+  float4* adj_b = nullptr;
+  double *q64 = nullptr, *p64 = nullptr, *a64 = nullptr, *b64 = nullptr, *t64 = nullptr;
+  double *hp0 = nullptr, *hq0 = nullptr;
+  Partial* part = nullptr;   // cap_splits * cap_npad
+  float *in_q = nullptr, *in_p = nullptr, *in_t = nullptr, *in_a = nullptr;
+  float *out_a = nullptr, *out_b = nullptr;
+  double *red_h = nullptr, *red_m = nullptr, *scalars = nullptr;
+  unsigned *ticket = nullptr, *status = nullptr;
+  // The trajectory and adjoint float4 arrays hold zero padding for this N.
+  int clean_n = -1;
+  cudaStream_t capture_stream = nullptr;
+  std::map<GraphKey, cudaGraphExec_t> graphs;
+
+  void drop_graphs() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    graphs.clear();
+  }
+  void free_all() {
+    drop_graphs();
+    for (void* p : allocs) cudaFree(p);
+    allocs.clear();
+    cap_npad = cap_T = cap_splits = cap_red = 0;
+    clean_n = -1;
+  }
+};
+
+std::map<int, Workspace*> g_ws;
+
+template <typename T>
+cudaError_t dalloc(Workspace& w, T** p, size_t count) {
+  void* v = nullptr;
+  cudaError_t e = cudaMalloc(&v, count * sizeof(T) + 256);
+  if (e != cudaSuccess) return e;
+  w.allocs.push_back(v);
+  *p = static_cast<T*>(v);
+  return cudaSuccess;
+}
+
+gs_status get_workspace(Workspace** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(GS_ENOLIB, std::string("no CUDA device: ") + cudaGetErrorString(e));
+  auto it = g_ws.find(dev);
+  if (it == g_ws.end()) {
+    Workspace* w = new Workspace();
+    w->device = dev;
+    GS_CUDA(cudaDeviceGetAttribute(&w->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    GS_CUDA(cudaStreamCreateWithFlags(&w->capture_stream, cudaStreamNonBlocking));
+    it = g_ws.emplace(dev, w).first;
+  }
+  *out = it->second;
+  return GS_OK;
+}
+
+// Make room for npad landmarks, T steps and the given split counts.
+gs_status reserve(Workspace& w, int npad, int T, int splits) {
+  const int red = (3 * npad + combine_threads() - 1) / combine_threads() + 1;
+  if (npad <= w.cap_npad && T <= w.cap_T && splits <= w.cap_splits && red <= w.cap_red) return GS_OK;
+  const int cn = std::max(npad, w.cap_npad), cT = std::max(T, w.cap_T);
+  const int cs = std::max(splits, w.cap_splits), cr = std::max(red, w.cap_red);
+  w.free_all();
+  const size_t n3 = 3 * static_cast<size_t>(cn);
+  GS_CUDA(dalloc(w, &w.traj_q, static_cast<size_t>(cT + 1) * cn));
+  GS_CUDA(dalloc(w, &w.traj_p, static_cast<size_t>(cT + 1) * cn));
+  GS_CUDA(dalloc(w, &w.adj_a, cn));
+  GS_CUDA(dalloc(w, &w.adj_b, cn));
+  GS_CUDA(dalloc(w, &w.q64, n3));
+  GS_CUDA(dalloc(w, &w.p64, n3));
+  GS_CUDA(dalloc(w, &w.a64, n3));
+  GS_CUDA(dalloc(w, &w.b64, n3));
+  GS_CUDA(dalloc(w, &w.t64, n3));
+  GS_CUDA(dalloc(w, &w.hp0, n3));
+  GS_CUDA(dalloc(w, &w.hq0, n3));
+  GS_CUDA(dalloc(w, &w.part, static_cast<size_t>(cs) * cn));
+  GS_CUDA(dalloc(w, &w.in_q, n3));
+  GS_CUDA(dalloc(w, &w.in_p, n3));
+  GS_CUDA(dalloc(w, &w.in_t, n3));
+  GS_CUDA(dalloc(w, &w.in_a, n3));
+  GS_CUDA(dalloc(w, &w.out_a, n3));
+  GS_CUDA(dalloc(w, &w.out_b, n3));
+  GS_CUDA(dalloc(w, &w.red_h, cr));
+  GS_CUDA(dalloc(w, &w.red_m, cr));
+  GS_CUDA(dalloc(w, &w.scalars, 8));
+  GS_CUDA(dalloc(w, &w.ticket, 8));
+  GS_CUDA(dalloc(w, &w.status, 8));
+  GS_CUDA(cudaMemset(w.ticket, 0, 8 * sizeof(unsigned)));
+  GS_CUDA(cudaMemset(w.status, 0, 8 * sizeof(unsigned)));
+  GS_CUDA(cudaMemset(w.scalars, 0, 8 * sizeof(double)));
+  w.cap_npad = cn;
+  w.cap_T = cT;
+  w.cap_splits = cs;
+  w.cap_red = cr;
+  return GS_OK;
+}
+
+// Zero the float4 trajectory and adjoint arrays when the landmark count
+// changes: padded entries must be exactly zero (they are never written).
+gs_status ensure_clean(Workspace& w, int n, cudaStream_t st) {
+  if (w.clean_n == n) return GS_OK;
+  GS_CUDA(cudaMemsetAsync(w.traj_q, 0, sizeof(float4) * (w.cap_T + 1) * static_cast<size_t>(w.cap_npad), st));
+  GS_CUDA(cudaMemsetAsync(w.traj_p, 0, sizeof(float4) * (w.cap_T + 1) * static_cast<size_t>(w.cap_npad), st));
+  GS_CUDA(cudaMemsetAsync(w.adj_a, 0, sizeof(float4) * w.cap_npad, st));
+  GS_CUDA(cudaMemsetAsync(w.adj_b, 0, sizeof(float4) * w.cap_npad, st));
+  w.clean_n = n;
+  return GS_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Device view of a caller input array: the pointer itself, or a staged copy.
+gs_status stage_in(const float* src, float* staging, size_t n3, cudaStream_t st, const float** dev, bool* host) {
+  if (!src) {
+    *dev = nullptr;
+    return GS_OK;
+  }
+  if (is_device_ptr(src)) {
+    *dev = src;
+    return GS_OK;
+  }
+  GS_CUDA(cudaMemcpyAsync(staging, src, n3 * sizeof(float), cudaMemcpyHostToDevice, st));
+  *dev = staging;
+  *host = true;
+  return GS_OK;
+}
+
+gs_status copy_out(float* dst, const float* src, size_t n3, cudaStream_t st, bool* host) {
+  if (!dst) return GS_OK;
+  const bool dev = is_device_ptr(dst);
+  if (!dev) *host = true;
+  GS_CUDA(cudaMemcpyAsync(dst, src, n3 * sizeof(float), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  return GS_OK;
+}
+
+// Read and clear the device status word (synchronises the stream).
+gs_status finish_sync(Workspace& w, cudaStream_t st) {
+  unsigned h = 0;
+  GS_CUDA(cudaMemcpyAsync(&h, w.status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  GS_CUDA(cudaStreamSynchronize(st));
+  if (h) {
+    cudaMemset(w.status, 0, sizeof(unsigned));
+    if (h & kErrTimeout) return fail(GS_ETIMEOUT, "a device-side wait expired");
+    if (h & kErrNonFinite) return fail(GS_ENONFINITE, "non-finite value in an input or intermediate");
+    return fail(GS_ECUDA, "device reported an inconsistent launch");
+  }
+  return GS_OK;
+}
+
+gs_status check_params(const gs_params* prm) {
+  if (!prm) return fail(GS_EINVAL, "params is NULL");
+  if (prm->N < 1 || prm->N > (1LL << 26)) return fail(GS_EINVAL, "N must be in [1, 2^26]");
+  if (prm->T < 1 || prm->T > 100000) return fail(GS_EINVAL, "T must be in [1, 100000]");
+  if (!(prm->sigma > 0.0) || !std::isfinite(prm->sigma)) return fail(GS_EINVAL, "sigma must be finite and > 0");
+  if (!(prm->lambda >= 0.0) || !std::isfinite(prm->lambda)) return fail(GS_EINVAL, "lambda must be finite and >= 0");
+  if (prm->ckpt_every < 0) return fail(GS_EINVAL, "ckpt_every must be >= 0");
+  return GS_OK;
+}
+
+// Enqueue the T forward steps (and, for kind 1, the loss and T reverse steps).
+gs_status enqueue_steps(Workspace& w, int kind, int n, int T, double sigma, double lambda, cudaStream_t st) {
+  const int npad = round_up(n, kPad);
+  const KernelScales sc = make_scales(sigma);
+  const PairConfig fc = choose_forward_config(npad, w.num_sms);
+  const PairConfig bc = choose_backward_config(npad, w.num_sms);
+  const double dt = 1.0 / T;
+  const size_t slot = static_cast<size_t>(w.cap_npad);
+  bool first_launch = true;
+  for (int k = 0; k < T; ++k) {
+    PairFwdArgs pa;
+    pa.q4 = w.traj_q + k * slot;
+    pa.p4 = w.traj_p + k * slot;
+    pa.part = w.part;
+    pa.npad = npad;
+    pa.split_len = fc.split_len;
+    pa.kappa = static_cast<float>(sc.kappa);
+    pa.status = w.status;
+    GS_CUDA(launch_pair_forward(fc, pa, st, !first_launch));
+    first_launch = false;
+    CombineFwdArgs ca;
+    std::memset(&ca, 0, sizeof(ca));
+    ca.part = w.part;
+    ca.splits = fc.splits;
+    ca.n = n;
+    ca.npad = npad;
+    ca.dt = dt;
+    ca.kq = sc.kq;
+    ca.q64 = w.q64;
+    ca.p64 = w.p64;
+    ca.q4_next = w.traj_q + (k + 1) * slot;
+    ca.p4_next = w.traj_p + (k + 1) * slot;
+    ca.first = (k == 0);
+    ca.hp0 = w.hp0;
+    ca.hq0 = w.hq0;
+    ca.last = (k == T - 1);
+    ca.with_loss = (kind == 1);
+    ca.t64 = w.t64;
+    ca.lambda = lambda;
+    ca.kappa = sc.kappa;
+    ca.a64 = w.a64;
+    ca.b64 = w.b64;
+    ca.a4 = w.adj_a;
+    ca.b4 = w.adj_b;
+    ca.red_h = w.red_h;
+    ca.red_m = w.red_m;
+    ca.ticket = w.ticket;
+    ca.scalars = w.scalars;
+    ca.status = w.status;
+    GS_CUDA(launch_combine_forward(ca, st, true, nullptr));
+  }
+  if (kind == 0) return GS_OK;
+  for (int k = T - 1; k >= 0; --k) {
+    PairBwdArgs pb;
+    pb.q4 = w.traj_q + k * slot;
+    pb.p4 = w.traj_p + k * slot;
+    pb.a4 = w.adj_a;
+    pb.b4 = w.adj_b;
+    pb.part = w.part;
+    pb.npad = npad;
+    pb.split_len = bc.split_len;
+    pb.kq = static_cast<float>(sc.kq);
+    pb.kappa = static_cast<float>(sc.kappa);
+    pb.status = w.status;
+    GS_CUDA(launch_pair_backward(bc, pb, st, true));
+    CombineBwdArgs cb;
+    std::memset(&cb, 0, sizeof(cb));
+    cb.part = w.part;
+    cb.splits = bc.splits;
+    cb.n = n;
+    cb.npad = npad;
+    cb.dt = dt;
+    cb.kappa = sc.kappa;
+    cb.a64 = w.a64;
+    cb.b64 = w.b64;
+    cb.a4 = w.adj_a;
+    cb.b4 = w.adj_b;
+    cb.first = (k == 0);
+    cb.hp0 = w.hp0;
+    cb.hq0 = w.hq0;
+    cb.grad_p0 = w.out_a;
+    cb.grad_q0 = w.out_b;
+    cb.status = w.status;
+    GS_CUDA(launch_combine_backward(cb, st, true));
+  }
+  return GS_OK;
+}
+
+gs_status get_graph(Workspace& w, const GraphKey& key, cudaGraphExec_t* out) {
+  auto it = w.graphs.find(key);
+  if (it != w.graphs.end()) {
+    *out = it->second;
+    return GS_OK;
+  }
+  if (w.graphs.size() >= 16) w.drop_graphs();
+  cudaStream_t cs = w.capture_stream;
+  GS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  gs_status s = enqueue_steps(w, key.kind, key.n, key.T, key.sigma, key.lambda, cs);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &g);
+  if (s != GS_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  if (e != cudaSuccess) return fail(GS_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  cudaGraphExec_t ge = nullptr;
+  e = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(GS_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  w.graphs[key] = ge;
+  *out = ge;
+  return GS_OK;
+}
+
+// Common driver of shoot_forward / shoot_gradient.
+gs_status run_shoot(int kind, const gs_params* prm, const float* q0, const float* p0, const float* target,
+                    float* q1, float* p1, double* H0, double* loss, float* gp, float* gq, void* stream) {
+  gs_status s = check_params(prm);
+  if (s != GS_OK) return s;
+  if (!q0 || !p0 || (kind == 1 && !target)) return fail(GS_EINVAL, "q0, p0 (and target) must not be NULL");
+  if (prm->ckpt_every != 0 && prm->ckpt_every < prm->T)
+    return fail(GS_EINVAL, "trajectory checkpointing is not available in this build");
+  std::lock_guard<std::mutex> lk(g_mu);
+  Workspace* w = nullptr;
+  if ((s = get_workspace(&w)) != GS_OK) return s;
+  const int n = static_cast<int>(prm->N), T = prm->T;
+  const int npad = round_up(n, kPad);
+  const PairConfig fc = choose_forward_config(npad, w->num_sms);
+  const PairConfig bc = choose_backward_config(npad, w->num_sms);
+  if ((s = reserve(*w, npad, T, std::max(fc.splits, bc.splits))) != GS_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((s = ensure_clean(*w, n, st)) != GS_OK) return s;
+  const size_t n3 = 3 * static_cast<size_t>(n);
+  bool host = false;
+  const float *dq = nullptr, *dp = nullptr, *dt = nullptr;
+  if ((s = stage_in(q0, w->in_q, n3, st, &dq, &host)) != GS_OK) return s;
+  if ((s = stage_in(p0, w->in_p, n3, st, &dp, &host)) != GS_OK) return s;
+  if (kind == 1 && (s = stage_in(target, w->in_t, n3, st, &dt, &host)) != GS_OK) return s;
+  PackArgs pk;
+  pk.q = dq;
+  pk.p = dp;
+  pk.tgt = dt;
+  pk.q64 = w->q64;
+  pk.p64 = w->p64;
+  pk.t64 = kind == 1 ? w->t64 : nullptr;
+  pk.q4 = w->traj_q;
+  pk.p4 = w->traj_p;
+  pk.n = n;
+  pk.kq = make_scales(prm->sigma).kq;
+  pk.status = w->status;
+  GS_CUDA(launch_pack(pk, st));
+  cudaGraphExec_t ge = nullptr;
+  const GraphKey key{kind, n, T, prm->sigma, kind == 1 ? prm->lambda : 0.0};
+  if ((s = get_graph(*w, key, &ge)) != GS_OK) return s;
+  GS_CUDA(cudaGraphLaunch(ge, st));
+  bool want_sync = host;
+  if (kind == 0) {
+    if (q1) {
+      UnpackArgs u{w->q64, w->out_a, static_cast<int>(n3)};
+      GS_CUDA(launch_unpack(u, st));
+      if ((s = copy_out(q1, w->out_a, n3, st, &want_sync)) != GS_OK) return s;
+    }
+    if (p1) {
+      UnpackArgs u{w->p64, w->out_b, static_cast<int>(n3)};
+      GS_CUDA(launch_unpack(u, st));
+      if ((s = copy_out(p1, w->out_b, n3, st, &want_sync)) != GS_OK) return s;
+    }
+    if (H0) {
+      GS_CUDA(cudaMemcpyAsync(H0, w->scalars, sizeof(double), cudaMemcpyDeviceToHost, st));
+      want_sync = true;
+    }
+  } else {
+    if ((s = copy_out(gp, w->out_a, n3, st, &want_sync)) != GS_OK) return s;
+    if ((s = copy_out(gq, w->out_b, n3, st, &want_sync)) != GS_OK) return s;
+    if (loss) {
+      GS_CUDA(cudaMemcpyAsync(loss, w->scalars + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+      want_sync = true;
+    }
+  }
+  (void)bc;
+  if (want_sync) return finish_sync(*w, st);
+  return GS_OK;
+}
+
+gs_status run_step(int kind, int64_t N, double sigma, const float* q, const float* p, const float* alpha,
+                   const float* beta, float* out0, float* out1, void* stream) {
+  if (N < 1 || N > (1LL << 26)) return fail(GS_EINVAL, "N must be in [1, 2^26]");
+  if (!(sigma > 0.0) || !std::isfinite(sigma)) return fail(GS_EINVAL, "sigma must be finite and > 0");
+  if (!q || !p || !out0 || !out1 || (kind == 1 && (!alpha || !beta)))
+    return fail(GS_EINVAL, "array arguments must not be NULL");
+  std::lock_guard<std::mutex> lk(g_mu);
+  Workspace* w = nullptr;
+  gs_status s = get_workspace(&w);
+  if (s != GS_OK) return s;
+  const int n = static_cast<int>(N), npad = round_up(n, kPad);
+  const PairConfig c = kind == 0 ? choose_forward_config(npad, w->num_sms) : choose_backward_config(npad, w->num_sms);
+  if ((s = reserve(*w, npad, 1, c.splits)) != GS_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t n3 = 3 * static_cast<size_t>(n);
+  bool host = false;
+  const float *dq, *dp, *da = nullptr, *db = nullptr;
+  if ((s = stage_in(q, w->in_q, n3, st, &dq, &host)) != GS_OK) return s;
+  if ((s = stage_in(p, w->in_p, n3, st, &dp, &host)) != GS_OK) return s;
+  if (kind == 1) {
+    if ((s = stage_in(alpha, w->in_a, n3, st, &da, &host)) != GS_OK) return s;
+    if ((s = stage_in(beta, w->in_t, n3, st, &db, &host)) != GS_OK) return s;
+  }
+  const KernelScales sc = make_scales(sigma);
+  GS_CUDA(launch_to_float4(dq, w->traj_q, n, npad, sc.kq, w->status, st));
+  GS_CUDA(launch_to_float4(dp, w->traj_p, n, npad, 1.0, w->status, st));
+  if (kind == 0) {
+    PairFwdArgs a;
+    a.q4 = w->traj_q;
+    a.p4 = w->traj_p;
+    a.part = w->part;
+    a.npad = npad;
+    a.split_len = c.split_len;
+    a.kappa = static_cast<float>(sc.kappa);
+    a.status = w->status;
+    GS_CUDA(launch_pair_forward(c, a, st, false));
+  } else {
+    GS_CUDA(launch_to_float4(da, w->adj_a, n, npad, 1.0, w->status, st));
+    GS_CUDA(launch_to_float4(db, w->adj_b, n, npad, sc.kappa, w->status, st));
+    PairBwdArgs a;
+    a.q4 = w->traj_q;
+    a.p4 = w->traj_p;
+    a.a4 = w->adj_a;
+    a.b4 = w->adj_b;
+    a.part = w->part;
+    a.npad = npad;
+    a.split_len = c.split_len;
+    a.kq = static_cast<float>(sc.kq);
+    a.kappa = static_cast<float>(sc.kappa);
+    a.status = w->status;
+    GS_CUDA(launch_pair_backward(c, a, st, false));
+  }
+  // Partials hold (Hp, Hq) forward and (dalpha, dbeta) backward.
+  GS_CUDA(launch_partials_to_out(w->part, c.splits, n, npad, w->out_a, w->out_b, st));
+  w->clean_n = -1;  // traj slot 0 / adjoint arrays were overwritten
+  bool want_sync = host;
+  if (kind == 0) {
+    if ((s = copy_out(out1, w->out_a, n3, st, &want_sync)) != GS_OK) return s;  // Hp
+    if ((s = copy_out(out0, w->out_b, n3, st, &want_sync)) != GS_OK) return s;  // Hq
+  } else {
+    if ((s = copy_out(out0, w->out_a, n3, st, &want_sync)) != GS_OK) return s;  // dalpha
+    if ((s = copy_out(out1, w->out_b, n3, st, &want_sync)) != GS_OK) return s;  // dbeta
+  }
+  if (want_sync) return finish_sync(*w, st);
+  return GS_OK;
+}
+
+gs_status time_pair_kernels(const gs_params* prm, const float* q0, const float* p0, const float* target,
+                            int reps, double* fwd_ms, double* bwd_ms, int* launches, void* stream) {
+  if (reps < 1 || reps > 100000) return fail(GS_EINVAL, "reps must be in [1, 100000]");
+  double loss = 0.0;
+  gs_status s = run_shoot(1, prm, q0, p0, target, nullptr, nullptr, nullptr, &loss, nullptr, nullptr, stream);
+  if (s != GS_OK) return s;
+  std::lock_guard<std::mutex> lk(g_mu);
+  Workspace* w = nullptr;
+  if ((s = get_workspace(&w)) != GS_OK) return s;
+  const int n = static_cast<int>(prm->N), T = prm->T, npad = round_up(n, kPad);
+  const KernelScales sc = make_scales(prm->sigma);
+  const PairConfig fc = choose_forward_config(npad, w->num_sms);
+  const PairConfig bc = choose_backward_config(npad, w->num_sms);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t slot = static_cast<size_t>(w->cap_npad) * (T / 2);
+  cudaEvent_t e0, e1, e2;
+  GS_CUDA(cudaEventCreate(&e0));
+  GS_CUDA(cudaEventCreate(&e1));
+  GS_CUDA(cudaEventCreate(&e2));
+  PairFwdArgs pa;
+  pa.q4 = w->traj_q + slot;
+  pa.p4 = w->traj_p + slot;
+  pa.part = w->part;
+  pa.npad = npad;
+  pa.split_len = fc.split_len;
+  pa.kappa = static_cast<float>(sc.kappa);
+  pa.status = w->status;
+  PairBwdArgs pb;
+  pb.q4 = pa.q4;
+  pb.p4 = pa.p4;
+  pb.a4 = w->adj_a;
+  pb.b4 = w->adj_b;
+  pb.part = w->part;
+  pb.npad = npad;
+  pb.split_len = bc.split_len;
+  pb.kq = static_cast<float>(sc.kq);
+  pb.kappa = static_cast<float>(sc.kappa);
+  pb.status = w->status;
+  GS_CUDA(launch_pair_forward(fc, pa, st, false));  // warm-up
+  GS_CUDA(launch_pair_backward(bc, pb, st, false));
+  GS_CUDA(cudaEventRecord(e0, st));
+  for (int r = 0; r < reps; ++r) GS_CUDA(launch_pair_forward(fc, pa, st, false));
+  GS_CUDA(cudaEventRecord(e1, st));
+  for (int r = 0; r < reps; ++r) GS_CUDA(launch_pair_backward(bc, pb, st, false));
+  GS_CUDA(cudaEventRecord(e2, st));
+  GS_CUDA(cudaEventSynchronize(e2));
+  float m1 = 0.f, m2 = 0.f;
+  GS_CUDA(cudaEventElapsedTime(&m1, e0, e1));
+  GS_CUDA(cudaEventElapsedTime(&m2, e1, e2));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaEventDestroy(e2);
+  if (fwd_ms) *fwd_ms = m1 / reps;
+  if (bwd_ms) *bwd_ms = m2 / reps;
+  if (launches) *launches = 4 * T + 1;
+  return finish_sync(*w, st);
+}
+
+}  // namespace
+}  // namespace gs
+
+extern "C" {
+
+gs_status step_forward(int64_t N, double sigma, const float* q, const float* p, float* Hq, float* Hp, void* stream) {
+  gs::g_err.clear();
+  return gs::run_step(0, N, sigma, q, p, nullptr, nullptr, Hq, Hp, stream);
+}
+
+gs_status step_backward(int64_t N, double sigma, const float* q, const float* p, const float* alpha,
+                        const float* beta, float* dalpha, float* dbeta, void* stream) {
+  gs::g_err.clear();
+  return gs::run_step(1, N, sigma, q, p, alpha, beta, dalpha, dbeta, stream);
+}
+
+gs_status shoot_forward(const gs_params* prm, const float* q0, const float* p0, float* q1, float* p1, double* H0,
+                        void* stream) {
+  gs::g_err.clear();
+  return gs::run_shoot(0, prm, q0, p0, nullptr, q1, p1, H0, nullptr, nullptr, nullptr, stream);
+}
+
+gs_status shoot_gradient(const gs_params* prm, const float* q0, const float* p0, const float* target, double* loss,
+                         float* grad_p0, float* grad_q0, void* stream) {
+  gs::g_err.clear();
+  return gs::run_shoot(1, prm, q0, p0, target, nullptr, nullptr, nullptr, loss, grad_p0, grad_q0, stream);
+}
+
+gs_status gs_time_pair_kernels(const gs_params* prm, const float* q0, const float* p0, const float* target,
+                               int32_t reps, double* fwd_ms, double* bwd_ms, int32_t* launches_per_eval,
+                               void* stream) {
+  gs::g_err.clear();
+  int l = 0;
+  gs_status s = gs::time_pair_kernels(prm, q0, p0, target, reps, fwd_ms, bwd_ms, &l, stream);
+  if (launches_per_eval) *launches_per_eval = l;
+  return s;
+}
+
+const char* gs_last_error(void) { return gs::g_err.c_str(); }
+
+void gs_release_workspace(void) {
+  std::lock_guard<std::mutex> lk(gs::g_mu);
+  for (auto& kv : gs::g_ws) {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(kv.first);
+    kv.second->free_all();
+    if (kv.second->capture_stream) cudaStreamDestroy(kv.second->capture_stream);
+    delete kv.second;
+    cudaSetDevice(cur);
+  }
+  gs::g_ws.clear();
+}
+
+int32_t gs_version(void) { return 100; }
+
+}  // extern "C"

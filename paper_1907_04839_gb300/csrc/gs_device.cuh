@@ -1,0 +1,132 @@
+// Device-side building blocks for the gshoot kernels (sm_103a):
+// bulk-copy (TMA) staging into shared memory guarded by mbarriers with
+// bounded waits, the MUFU base-2 exponential, compensated FP32 arithmetic
+// (Kahan updates and double-single pairs), programmatic dependent launch.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gs_internal.h"
+
+namespace gs {
+
+// Iteration limit of every spin on an mbarrier phase.  One try_wait may
+// suspend the thread for a while, so this bounds a wait well below a second
+// for copies that normally complete in a few microseconds.
+constexpr long kSpinLimit = 1L << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;"
+               ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// Bulk global -> shared copy (TMA, non-tensor); completes `bytes` of
+// transaction count on `bar`.  dst, src 16-byte aligned, bytes % 16 == 0.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait on phase `parity` of `bar`.  Returns false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  const uint32_t addr = smem_u32(bar);
+  for (long it = 0; it < kSpinLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok) : "r"(addr), "r"(parity) : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// Programmatic dependent launch: wait for the preceding kernel's results /
+// allow the next kernel to be scheduled.  No-ops when launched without PDL.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// 2^x on the MUFU unit (flushes subnormal results to zero).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// ---------------------------------------------------------------- compensated FP32
+// The *_rn intrinsics are never contracted into FMAs, which keeps the error
+// terms exact.
+
+// Kahan step: (sum, c) absorbs x; the compensated value is sum - c.
+__device__ __forceinline__ void kahan_add(float& sum, float& c, float x) {
+  const float y = __fsub_rn(x, c);
+  const float t = __fadd_rn(sum, y);
+  c = __fsub_rn(__fsub_rn(t, sum), y);
+  sum = t;
+}
+
+// Error-free a + b = s + e (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Error-free a + b = s + e when |a| >= |b| (Dekker's FastTwoSum).
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// Double-single value hi + lo with |lo| <= ulp(hi)/2.
+struct ds {
+  float hi, lo;
+};
+
+__device__ __forceinline__ ds ds_from_kahan(float sum, float c) {
+  ds r;
+  fast_two_sum(sum, -c, r.hi, r.lo);
+  return r;
+}
+
+__device__ __forceinline__ ds ds_add(ds a, ds b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  ds r;
+  fast_two_sum(s, e, r.hi, r.lo);
+  return r;
+}
+
+// (hi + lo) * f for an FP32 constant f, error-free product of hi.
+__device__ __forceinline__ ds ds_mul_f(ds a, float f) {
+  const float p = __fmul_rn(a.hi, f);
+  float e = __fmaf_rn(a.hi, f, -p);
+  e = __fmaf_rn(a.lo, f, e);
+  ds r;
+  fast_two_sum(p, e, r.hi, r.lo);
+  return r;
+}
+
+__device__ __forceinline__ double ds_to_double(ds a) { return (double)a.hi + (double)a.lo; }
+
+}  // namespace gs

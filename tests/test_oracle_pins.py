@@ -70,6 +70,23 @@ def test_hq_hp_are_partial_derivatives_of_H():
     assert rel(Hq, fq) < 1e-8
 
 
+def test_row_restricted_steps_match_dense_products():
+    # The row-restricted entry points compute the same sums for the chosen
+    # targets: Hp rows against the dense K matvec (BLAS), and every row
+    # against the full-set sweep.
+    q, p = small_cloud(500, 30)
+    rng = np.random.default_rng(31)
+    a = rng.normal(size=q.shape); b = rng.normal(size=q.shape)
+    rows = np.array([0, 7, 499, 250, 7])
+    Hq, Hp = oracle.step_forward_rows(q, p, 0.2, rows)
+    assert rel(Hp, (dense_K(q, q, 0.2) @ p)[rows]) < 1e-13
+    Hq_all, Hp_all = oracle.step_forward(q, p, 0.2)
+    assert np.array_equal(Hq, Hq_all[rows]) and np.array_equal(Hp, Hp_all[rows])
+    da, db = oracle.step_backward_rows(q, p, a, b, 0.2, rows)
+    da_all, db_all = oracle.step_backward(q, p, a, b, 0.2)
+    assert np.array_equal(da, da_all[rows]) and np.array_equal(db, db_all[rows])
+
+
 def test_hamiltonian_matches_dense_quadratic_form():
     q, p = small_cloud(200, 3)
     assert abs(oracle.hamiltonian(q, p, 0.15) - H_dense(q, p, 0.15)) < 1e-12 * abs(H_dense(q, p, 0.15))

@@ -128,6 +128,38 @@ gs_status gs_time_pair_kernels(const gs_params* prm, const float* q0, const floa
                                const float* target, int32_t reps, double* fwd_ms,
                                double* bwd_ms, int32_t* launches_per_eval, void* stream);
 
+/*
+ * step_forward_noalloc — StepForward for callers that cannot allocate device
+ * memory.  The paper has no counterpart; it is a library-usage variant.
+ *
+ * The other entry points take their scratch from a workspace the library
+ * grows with cudaMalloc.  Some callers cannot accept that: a host program
+ * whose device memory is owned by another allocator under a fixed budget, or
+ * code for which a cudaMalloc (which can synchronise the whole device) is not
+ * acceptable.  This entry point computes the same Hq, Hp as step_forward, but
+ * uses a file-scope static device array of about 3.4 MB as its scratch.  It
+ * never calls cudaMalloc, cudaFree or any allocating routine.
+ *
+ * Limits: 1 <= N <= 8192.  Larger N is rejected with GS_EINVAL before any
+ *   work is enqueued.  q, p, Hq and Hp must be device arrays ((N,3) float32);
+ *   a host pointer is rejected with GS_EINVAL.
+ * Memory: every GPU that loads the library holds the static array until the
+ *   process exits.
+ * Set-up: the first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress, with that device current).  Make that first call
+ *   before any stream capture begins.
+ * Sharing: every call on a device uses the same array.  Each call clears the
+ *   status word and rewrites the rest of the scratch it reads.  Calls whose
+ *   work overlaps on the GPU (different streams or host threads) race on the
+ *   array; serialise them.
+ * Synchronises `stream` before returning, and reports GS_ENONFINITE or
+ * GS_ETIMEOUT from the device status word.  The sum order differs from
+ * step_forward (at most 8 source splits), so results agree to rounding,
+ * not bitwise.
+ */
+gs_status step_forward_noalloc(int64_t N, double sigma, const float* q, const float* p,
+                               float* Hq, float* Hp, void* stream);
+
 /* Message for the last error of the calling thread ("" if none). */
 const char* gs_last_error(void);
 

@@ -22,7 +22,8 @@ GS_STATUS = {
 # Every symbol the header declares; tests check the library exports them all.
 EXPORTS = [
     "step_forward", "step_backward", "shoot_forward", "shoot_gradient",
-    "gs_time_pair_kernels", "gs_last_error", "gs_release_workspace", "gs_version",
+    "gs_time_pair_kernels", "step_forward_noalloc", "gs_last_error", "gs_release_workspace",
+    "gs_version",
 ]
 
 
@@ -55,7 +56,9 @@ def _declare(lib):
     lib.shoot_forward.argtypes = [P, fp, fp, fp, fp, dp, vp]
     lib.shoot_gradient.argtypes = [P, fp, fp, fp, dp, fp, fp, vp]
     lib.gs_time_pair_kernels.argtypes = [P, fp, fp, fp, i32, dp, dp, ctypes.c_void_p, vp]
-    for name in ("step_forward", "step_backward", "shoot_forward", "shoot_gradient", "gs_time_pair_kernels"):
+    lib.step_forward_noalloc.argtypes = [i64, cd, fp, fp, fp, fp, vp]
+    for name in ("step_forward", "step_backward", "shoot_forward", "shoot_gradient", "gs_time_pair_kernels",
+                 "step_forward_noalloc"):
         getattr(lib, name).restype = ctypes.c_int
     lib.gs_last_error.restype = ctypes.c_char_p
     lib.gs_last_error.argtypes = []

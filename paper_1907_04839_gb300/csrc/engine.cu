@@ -540,6 +540,9 @@ gs_status time_pair_kernels(const gs_params* prm, const float* q0, const float* 
 }
 
 }  // namespace
+
+void set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
 }  // namespace gs
 
 extern "C" {

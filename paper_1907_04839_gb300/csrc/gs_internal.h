@@ -76,6 +76,11 @@ struct PairConfig {
 
 PairConfig choose_forward_config(int npad, int num_sms);
 PairConfig choose_backward_config(int npad, int num_sms);
+// Forward configuration with at most `max_splits` source splits.
+PairConfig choose_forward_config_capped(int npad, int num_sms, int max_splits);
+
+// Record the calling thread's error message (returned by gs_last_error).
+void set_last_error(const char* msg);
 
 cudaError_t launch_pair_forward(const PairConfig& cfg, const PairFwdArgs& a, cudaStream_t st, bool pdl);
 cudaError_t launch_pair_backward(const PairConfig& cfg, const PairBwdArgs& a, cudaStream_t st, bool pdl);

@@ -376,6 +376,17 @@ PairConfig choose_forward_config(int npad, int num_sms) {
   return make_config(npad, num_sms, kFwdNT, kFwdR, 8);
 }
 
+PairConfig choose_forward_config_capped(int npad, int num_sms, int max_splits) {
+  PairConfig c = make_config(npad, num_sms, kFwdNT, kFwdR, 8);
+  if (c.splits > max_splits) {
+    int len = (npad + max_splits - 1) / max_splits;
+    len = (len + kUnroll - 1) / kUnroll * kUnroll;
+    c.split_len = len;
+    c.splits = (npad + len - 1) / len;
+  }
+  return c;
+}
+
 PairConfig choose_backward_config(int npad, int num_sms) {
   return make_config(npad, num_sms, kBwdNT, kBwdR, 8);
 }

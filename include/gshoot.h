@@ -160,6 +160,38 @@ gs_status gs_time_pair_kernels(const gs_params* prm, const float* q0, const floa
 gs_status step_forward_noalloc(int64_t N, double sigma, const float* q, const float* p,
                                float* Hq, float* Hp, void* stream);
 
+/*
+ * gs_time_pair_config — tuning diagnostics (no counterpart in the paper):
+ * average device time of one launch of a pair-sum kernel variant.
+ * kind 0 = StepForward split-partial kernel (alpha, beta ignored, may be
+ *          NULL), 1 = StepBackward split-partial kernel;
+ * kind 2 = fused forward time-step kernel, 3 = fused reverse time-step
+ *          kernel, run in a mode that computes and reduces everything but
+ *          writes no state.
+ * threads, R select the variant (CTA size, targets per thread).  For kinds
+ * 0/1, splits > 0 forces the number of source splits and splits <= 0 lets the
+ * library balance them; for kinds 2/3, splits is the cluster size (1, 2, 4,
+ * 8 or 16).  Adding 16 to kind captures the `reps` launches into one CUDA
+ * graph (linked by programmatic dependent launch) and times its replay.
+ * The kernel runs `reps` times back to back on (q, p[, alpha,
+ * beta]) between two CUDA events on `stream`.  Out: *ms per launch,
+ * *splits_used (NULL to skip).  GS_EINVAL for an unknown variant.
+ * Synchronises `stream`.
+ */
+gs_status gs_time_pair_config(int32_t kind, int64_t N, double sigma, const float* q,
+                              const float* p, const float* alpha, const float* beta,
+                              int32_t threads, int32_t R, int32_t splits, int32_t reps,
+                              double* ms, int32_t* splits_used, void* stream);
+
+/*
+ * gs_set_step_config — tuning (no counterpart in the paper): override the
+ * fused time-step kernel configuration used by shoot_forward / shoot_gradient
+ * for kind 0 (forward) or 1 (reverse): CTA size, targets per thread and
+ * cluster size, as in gs_time_pair_config.  threads = 0 restores the built-in
+ * choice.  Clears the cached graphs.  GS_EINVAL for an unknown variant.
+ */
+gs_status gs_set_step_config(int32_t kind, int32_t threads, int32_t R, int32_t cluster);
+
 /* Message for the last error of the calling thread ("" if none). */
 const char* gs_last_error(void);
 

@@ -22,7 +22,9 @@ GS_STATUS = {
 # Every symbol the header declares; tests check the library exports them all.
 EXPORTS = [
     "step_forward", "step_backward", "shoot_forward", "shoot_gradient",
-    "gs_time_pair_kernels", "step_forward_noalloc", "gs_last_error", "gs_release_workspace",
+    "gs_time_pair_kernels", "gs_time_pair_config", "gs_set_step_config", "step_forward_noalloc",
+    "gs_last_error",
+    "gs_release_workspace",
     "gs_version",
 ]
 
@@ -57,8 +59,11 @@ def _declare(lib):
     lib.shoot_gradient.argtypes = [P, fp, fp, fp, dp, fp, fp, vp]
     lib.gs_time_pair_kernels.argtypes = [P, fp, fp, fp, i32, dp, dp, ctypes.c_void_p, vp]
     lib.step_forward_noalloc.argtypes = [i64, cd, fp, fp, fp, fp, vp]
+    lib.gs_set_step_config.argtypes = [i32, i32, i32, i32]
+    lib.gs_time_pair_config.argtypes = [i32, i64, cd, fp, fp, fp, fp, i32, i32, i32, i32, dp,
+                                        ctypes.c_void_p, vp]
     for name in ("step_forward", "step_backward", "shoot_forward", "shoot_gradient", "gs_time_pair_kernels",
-                 "step_forward_noalloc"):
+                 "step_forward_noalloc", "gs_time_pair_config", "gs_set_step_config"):
         getattr(lib, name).restype = ctypes.c_int
     lib.gs_last_error.restype = ctypes.c_char_p
     lib.gs_last_error.argtypes = []

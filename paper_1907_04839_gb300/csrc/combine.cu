@@ -1,18 +1,12 @@
-// O(N) kernels around the pair sums.  This file holds:
-//  * packing of the (N,3) inputs;
-//  * the split combine followed by the Euler update (Algorithm 1,
-//    lines 7-8 and 14-15);
-//  * the loss of Eq. 3 with the adjoint initialisation;
-//  * the gradient assembly.
+// O(N) kernels around the pair sums: packing the (N,3) caller arrays into
+// the FP64 master state and the prescaled FP32 float4 copies, unpacking
+// results, and summing split partials straight to (N,3) outputs for the
+// single-step entry points.
 //
-// Numerics.  Per target, the source-split partials are summed in
-// double-single FP32 arithmetic (TwoSum), in split order, so the result is
-// deterministic.  The combined value is then converted to FP64, and the
-// FP64 master state is updated.  The FP64 pipe of this part runs at about
-// 1/80 of the FP32 rate, so FP64 is kept to a few operations per landmark
-// coordinate and stays out of the S-way reduction.  The loss and H0 are
-// reduced in FP64 in a fixed order: a warp tree per CTA, then one warp over
-// the CTA partials, with the last CTA chosen by a ticket.
+// Split partials are summed in double-single FP32 arithmetic (TwoSum).
+// Eight lanes share a landmark: each sums a lane-strided subset of the
+// splits, then a fixed xor-butterfly joins them.  The order is fixed, so the
+// result is deterministic.
 #include <cmath>
 
 #include "gs_device.cuh"
@@ -23,31 +17,8 @@ namespace gs {
 namespace {
 
 constexpr int kThreads = 128;
+constexpr int kGroup = 8;  // lanes that share one landmark's split partials
 
-__device__ __forceinline__ bool finite64(double x) { return isfinite(x); }
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Sum over the CTA in a fixed order; result valid in thread 0.
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-  v = warp_sum(v);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) sh[w] = v;
-  __syncthreads();
-  double r = 0.0;
-  if (w == 0) {
-    r = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
-    r = warp_sum(r);
-  }
-  __syncthreads();
-  return r;
-}
-
-__device__ __forceinline__ ds load_ds(float2 v) { return ds{v.x, v.y}; }
 
 __global__ void __launch_bounds__(kThreads) k_pack(PackArgs a) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -64,98 +35,36 @@ __global__ void __launch_bounds__(kThreads) k_pack(PackArgs a) {
   reinterpret_cast<float*>(a.p4)[4 * i + k] = p;
 }
 
-__global__ void __launch_bounds__(kThreads) k_combine_forward(CombineFwdArgs a) {
-  __shared__ double sh[kThreads / 32];
-  __shared__ int am_last;
-  pdl_wait();  // the pair-sum partials of this step must be complete
-  pdl_launch_dependents();
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  double hc = 0.0, mc = 0.0;
-  if (t < 3 * a.n) {
-    const int i = t / 3, k = t - 3 * i;
-    ds hp{0.f, 0.f}, hq{0.f, 0.f};
-    const Partial* pp = a.part + i;
-    for (int s = 0; s < a.splits; ++s) {
-      const float2* c = pp[static_cast<size_t>(s) * a.npad].c;
-      hp = ds_add(hp, load_ds(c[k]));
-      hq = ds_add(hq, load_ds(c[3 + k]));
-    }
-    const double Hp = ds_to_double(hp), Hq = ds_to_double(hq);
-    const double p_old = a.p64[t];
-    const double q = a.q64[t] + a.dt * Hp;
-    const double p = p_old - a.dt * Hq;
-    if (!finite64(q) || !finite64(p)) atomicOr(a.status, kErrNonFinite);
-    if (a.first) {
-      a.hp0[t] = Hp;
-      a.hq0[t] = Hq;
-      hc = 0.5 * p_old * Hp;
-    }
-    a.q64[t] = q;
-    a.p64[t] = p;
-    reinterpret_cast<float*>(a.q4_next)[4 * i + k] = (float)(a.kq * q);
-    reinterpret_cast<float*>(a.p4_next)[4 * i + k] = (float)p;
-    if (a.last && a.with_loss) {
-      const double r = q - a.t64[t];
-      mc = r * r;
-      const double al = 2.0 * a.lambda * r;
-      a.a64[t] = al;
-      a.b64[t] = 0.0;
-      reinterpret_cast<float*>(a.a4)[4 * i + k] = (float)al;
-      reinterpret_cast<float*>(a.b4)[4 * i + k] = 0.f;
+// Sum the split partials of landmark i over a group of kGroup lanes: lane l
+// takes splits l, l + kGroup, ..., then a fixed xor-butterfly combines the
+// lanes.  Every lane of the group ends with the same six sums (TwoSum is
+// commutative), and the result does not depend on timing.
+__device__ __forceinline__ void group_partials(const Partial* part, int splits, int npad, int i, bool valid,
+                                               int lane, ds acc[6]) {
+#pragma unroll
+  for (int c = 0; c < 6; ++c) acc[c] = ds{0.f, 0.f};
+  if (valid) {
+    const Partial* pp = part + i;
+#pragma unroll 4
+    for (int s = lane; s < splits; s += kGroup) {
+      const float4* v = reinterpret_cast<const float4*>(pp + static_cast<size_t>(s) * npad);
+      const float4 x = v[0], y = v[1], z = v[2];
+      acc[0] = ds_add(acc[0], ds{x.x, x.y});
+      acc[1] = ds_add(acc[1], ds{x.z, x.w});
+      acc[2] = ds_add(acc[2], ds{y.x, y.y});
+      acc[3] = ds_add(acc[3], ds{y.z, y.w});
+      acc[4] = ds_add(acc[4], ds{z.x, z.y});
+      acc[5] = ds_add(acc[5], ds{z.z, z.w});
     }
   }
-  const bool reduce_h = a.first != 0;
-  const bool reduce_m = a.last && a.with_loss;
-  if (!reduce_h && !reduce_m) return;  // uniform across the grid
-  const double bh = block_sum(hc, sh);
-  const double bm = block_sum(mc, sh);
-  if (threadIdx.x == 0) {
-    a.red_h[blockIdx.x] = bh;
-    a.red_m[blockIdx.x] = bm;
-    __threadfence();
-    const unsigned tk = atomicAdd(a.ticket, 1u);
-    am_last = (tk == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!am_last || threadIdx.x >= 32) return;
-  __threadfence();
-  double h = 0.0, m = 0.0;
-  for (unsigned b = threadIdx.x; b < gridDim.x; b += 32) {
-    h += *((volatile double*)&a.red_h[b]);
-    m += *((volatile double*)&a.red_m[b]);
-  }
-  h = warp_sum(h);
-  m = warp_sum(m);
-  if (threadIdx.x == 0) {
-    if (reduce_h) a.scalars[0] = h;
-    if (reduce_m) a.scalars[1] = (reduce_h ? h : a.scalars[0]) + a.lambda * m;
-    *a.ticket = 0u;
-  }
-}
-
-__global__ void __launch_bounds__(kThreads) k_combine_backward(CombineBwdArgs a) {
-  pdl_wait();
-  pdl_launch_dependents();
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 3 * a.n) return;
-  const int i = t / 3, k = t - 3 * i;
-  ds da{0.f, 0.f}, db{0.f, 0.f};
-  const Partial* pp = a.part + i;
-  for (int s = 0; s < a.splits; ++s) {
-    const float2* c = pp[static_cast<size_t>(s) * a.npad].c;
-    da = ds_add(da, load_ds(c[k]));
-    db = ds_add(db, load_ds(c[3 + k]));
-  }
-  const double al = a.a64[t] + a.dt * ds_to_double(da);
-  const double be = a.b64[t] + a.dt * ds_to_double(db);
-  if (!finite64(al) || !finite64(be)) atomicOr(a.status, kErrNonFinite);
-  a.a64[t] = al;
-  a.b64[t] = be;
-  reinterpret_cast<float*>(a.a4)[4 * i + k] = (float)al;
-  reinterpret_cast<float*>(a.b4)[4 * i + k] = (float)(a.kappa * be);
-  if (a.first) {
-    if (a.grad_p0) a.grad_p0[t] = (float)(be + a.hp0[t]);
-    if (a.grad_q0) a.grad_q0[t] = (float)(al + a.hq0[t]);
+#pragma unroll
+  for (int o = kGroup / 2; o > 0; o >>= 1) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const float hi = __shfl_xor_sync(0xffffffffu, acc[c].hi, o);
+      const float lo = __shfl_xor_sync(0xffffffffu, acc[c].lo, o);
+      acc[c] = ds_add(acc[c], ds{hi, lo});
+    }
   }
 }
 
@@ -166,17 +75,15 @@ __global__ void __launch_bounds__(kThreads) k_unpack(UnpackArgs a) {
 
 __global__ void __launch_bounds__(kThreads) k_partials_to_out(const Partial* part, int splits, int n, int npad,
                                                               float* out_a, float* out_b) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 3 * n) return;
-  const int i = t / 3, k = t - 3 * i;
-  ds x{0.f, 0.f}, y{0.f, 0.f};
-  for (int s = 0; s < splits; ++s) {
-    const float2* c = part[static_cast<size_t>(s) * npad + i].c;
-    x = ds_add(x, load_ds(c[k]));
-    y = ds_add(y, load_ds(c[3 + k]));
-  }
-  out_a[t] = (float)ds_to_double(x);
-  out_b[t] = (float)ds_to_double(y);
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = gt / kGroup, lane = gt % kGroup;
+  const bool valid = i < n;
+  ds acc[6];
+  group_partials(part, splits, npad, i, valid, lane, acc);
+  if (!valid || lane >= 6) return;
+  const int k = lane % 3;
+  if (lane < 3) out_a[3 * i + k] = (float)ds_to_double(acc[k]);
+  else out_b[3 * i + k] = (float)ds_to_double(acc[3 + k]);
 }
 
 __global__ void __launch_bounds__(kThreads) k_to_float4(const float* x, float4* x4, int n, int npad,
@@ -219,21 +126,12 @@ KernelScales make_scales(double sigma) {
 }
 
 int combine_threads() { return kThreads; }
+int combine_group() { return kGroup; }
 
 cudaError_t launch_pack(const PackArgs& a, cudaStream_t st) {
   if (a.n <= 0) return cudaSuccess;
   k_pack<<<blocks_for(3LL * a.n), kThreads, 0, st>>>(a);
   return cudaGetLastError();
-}
-
-cudaError_t launch_combine_forward(const CombineFwdArgs& a, cudaStream_t st, bool pdl, int* grid_out) {
-  const int grid = blocks_for(3LL * a.n);
-  if (grid_out) *grid_out = grid;
-  return launch_ex(k_combine_forward, grid, a, st, pdl);
-}
-
-cudaError_t launch_combine_backward(const CombineBwdArgs& a, cudaStream_t st, bool pdl) {
-  return launch_ex(k_combine_backward, blocks_for(3LL * a.n), a, st, pdl);
 }
 
 cudaError_t launch_unpack(const UnpackArgs& a, cudaStream_t st) {
@@ -244,7 +142,7 @@ cudaError_t launch_unpack(const UnpackArgs& a, cudaStream_t st) {
 
 cudaError_t launch_partials_to_out(const Partial* part, int splits, int n, int npad,
                                    float* out_a, float* out_b, cudaStream_t st) {
-  k_partials_to_out<<<blocks_for(3LL * n), kThreads, 0, st>>>(part, splits, n, npad, out_a, out_b);
+  k_partials_to_out<<<blocks_for((long long)kGroup * n), kThreads, 0, st>>>(part, splits, n, npad, out_a, out_b);
   return cudaGetLastError();
 }
 

@@ -65,7 +65,7 @@ struct Workspace {
   std::vector<void*> allocs;
   float4* traj_q = nullptr;  // (cap_T + 1) * cap_npad
   float4* traj_p = nullptr;
-  float4* adj_a = nullptr;   // cap_npad
+  float4* adj_a = nullptr;   // 2 * cap_npad: reverse steps alternate buffers
   float4* adj_b = nullptr;
   double *q64 = nullptr, *p64 = nullptr, *a64 = nullptr, *b64 = nullptr, *t64 = nullptr;
   double *hp0 = nullptr, *hq0 = nullptr;
@@ -122,7 +122,9 @@ gs_status get_workspace(Workspace** out) {
 
 // Make room for npad landmarks, T steps and the given split counts.
 gs_status reserve(Workspace& w, int npad, int T, int splits) {
-  const int red = (3 * npad + combine_threads() - 1) / combine_threads() + 1;
+  // per-CTA reduction slots: at most Npad/4 fused-step CTAs (tiles of >= 64
+  // targets, clusters of <= 16)
+  const int red = npad + 64;
   if (npad <= w.cap_npad && T <= w.cap_T && splits <= w.cap_splits && red <= w.cap_red) return GS_OK;
   const int cn = std::max(npad, w.cap_npad), cT = std::max(T, w.cap_T);
   const int cs = std::max(splits, w.cap_splits), cr = std::max(red, w.cap_red);
@@ -130,8 +132,8 @@ gs_status reserve(Workspace& w, int npad, int T, int splits) {
   const size_t n3 = 3 * static_cast<size_t>(cn);
   GS_CUDA(dalloc(w, &w.traj_q, static_cast<size_t>(cT + 1) * cn));
   GS_CUDA(dalloc(w, &w.traj_p, static_cast<size_t>(cT + 1) * cn));
-  GS_CUDA(dalloc(w, &w.adj_a, cn));
-  GS_CUDA(dalloc(w, &w.adj_b, cn));
+  GS_CUDA(dalloc(w, &w.adj_a, 2 * static_cast<size_t>(cn)));
+  GS_CUDA(dalloc(w, &w.adj_b, 2 * static_cast<size_t>(cn)));
   GS_CUDA(dalloc(w, &w.q64, n3));
   GS_CUDA(dalloc(w, &w.p64, n3));
   GS_CUDA(dalloc(w, &w.a64, n3));
@@ -167,8 +169,8 @@ gs_status ensure_clean(Workspace& w, int n, cudaStream_t st) {
   if (w.clean_n == n) return GS_OK;
   GS_CUDA(cudaMemsetAsync(w.traj_q, 0, sizeof(float4) * (w.cap_T + 1) * static_cast<size_t>(w.cap_npad), st));
   GS_CUDA(cudaMemsetAsync(w.traj_p, 0, sizeof(float4) * (w.cap_T + 1) * static_cast<size_t>(w.cap_npad), st));
-  GS_CUDA(cudaMemsetAsync(w.adj_a, 0, sizeof(float4) * w.cap_npad, st));
-  GS_CUDA(cudaMemsetAsync(w.adj_b, 0, sizeof(float4) * w.cap_npad, st));
+  GS_CUDA(cudaMemsetAsync(w.adj_a, 0, 2 * sizeof(float4) * w.cap_npad, st));
+  GS_CUDA(cudaMemsetAsync(w.adj_b, 0, 2 * sizeof(float4) * w.cap_npad, st));
   w.clean_n = n;
   return GS_OK;
 }
@@ -230,90 +232,93 @@ gs_status check_params(const gs_params* prm) {
   return GS_OK;
 }
 
-// Enqueue the T forward steps (and, for kind 1, the loss and T reverse steps).
-gs_status enqueue_steps(Workspace& w, int kind, int n, int T, double sigma, double lambda, cudaStream_t st) {
+// Arguments of fused forward step k (kind 1: the last step also forms the
+// loss and the adjoint initialisation).
+StepFwdArgs forward_step_args(Workspace& w, const StepConfig& c, int kind, int n, int T, int k, double sigma,
+                              double lambda) {
   const int npad = round_up(n, kPad);
   const KernelScales sc = make_scales(sigma);
-  const PairConfig fc = choose_forward_config(npad, w.num_sms);
-  const PairConfig bc = choose_backward_config(npad, w.num_sms);
-  const double dt = 1.0 / T;
   const size_t slot = static_cast<size_t>(w.cap_npad);
-  bool first_launch = true;
+  StepFwdArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.q4 = w.traj_q + k * slot;
+  a.p4 = w.traj_p + k * slot;
+  a.q4_next = w.traj_q + (k + 1) * slot;
+  a.p4_next = w.traj_p + (k + 1) * slot;
+  a.n = n;
+  a.npad = npad;
+  a.split_len = c.split_len;
+  a.kappa = static_cast<float>(sc.kappa);
+  a.dt = 1.0 / T;
+  a.kq = sc.kq;
+  a.q64 = w.q64;
+  a.p64 = w.p64;
+  a.first = (k == 0);
+  a.hp0 = w.hp0;
+  a.hq0 = w.hq0;
+  a.last = (k == T - 1);
+  a.with_loss = (kind == 1);
+  a.t64 = w.t64;
+  a.lambda = lambda;
+  a.a64 = w.a64;
+  a.b64 = w.b64;
+  a.a4 = w.adj_a;  // buffer 0: read by the first reverse step
+  a.b4 = w.adj_b;
+  a.red_h = w.red_h;
+  a.red_m = w.red_m;
+  a.ticket = w.ticket;
+  a.scalars = w.scalars;
+  a.status = w.status;
+  return a;
+}
+
+// Arguments of fused reverse step number s = 0..T-1 (time step k = T-1-s).
+StepBwdArgs backward_step_args(Workspace& w, const StepConfig& c, int n, int T, int s, double sigma) {
+  const int npad = round_up(n, kPad);
+  const KernelScales sc = make_scales(sigma);
+  const size_t slot = static_cast<size_t>(w.cap_npad);
+  const int k = T - 1 - s;
+  StepBwdArgs b;
+  std::memset(&b, 0, sizeof(b));
+  b.q4 = w.traj_q + k * slot;
+  b.p4 = w.traj_p + k * slot;
+  b.a4 = w.adj_a + (s & 1) * slot;
+  b.b4 = w.adj_b + (s & 1) * slot;
+  b.a4_next = w.adj_a + ((s + 1) & 1) * slot;
+  b.b4_next = w.adj_b + ((s + 1) & 1) * slot;
+  b.n = n;
+  b.npad = npad;
+  b.split_len = c.split_len;
+  b.kq = static_cast<float>(sc.kq);
+  b.kappa = static_cast<float>(sc.kappa);
+  b.dt = 1.0 / T;
+  b.kappa64 = sc.kappa;
+  b.a64 = w.a64;
+  b.b64 = w.b64;
+  b.first = (k == 0);
+  b.hp0 = w.hp0;
+  b.hq0 = w.hq0;
+  b.grad_p0 = w.out_a;
+  b.grad_q0 = w.out_b;
+  b.status = w.status;
+  return b;
+}
+
+// Enqueue the T forward steps (and, for kind 1, the loss and T reverse
+// steps): one fused cluster kernel per time step.
+gs_status enqueue_steps(Workspace& w, int kind, int n, int T, double sigma, double lambda, cudaStream_t st) {
+  const int npad = round_up(n, kPad);
+  const StepConfig fc = choose_step_config(0, npad, w.num_sms);
+  const StepConfig bc = choose_step_config(1, npad, w.num_sms);
+  if (fc.threads == 0 || bc.threads == 0) return fail(GS_EINVAL, "no step kernel configuration");
   for (int k = 0; k < T; ++k) {
-    PairFwdArgs pa;
-    pa.q4 = w.traj_q + k * slot;
-    pa.p4 = w.traj_p + k * slot;
-    pa.part = w.part;
-    pa.npad = npad;
-    pa.split_len = fc.split_len;
-    pa.kappa = static_cast<float>(sc.kappa);
-    pa.status = w.status;
-    GS_CUDA(launch_pair_forward(fc, pa, st, !first_launch));
-    first_launch = false;
-    CombineFwdArgs ca;
-    std::memset(&ca, 0, sizeof(ca));
-    ca.part = w.part;
-    ca.splits = fc.splits;
-    ca.n = n;
-    ca.npad = npad;
-    ca.dt = dt;
-    ca.kq = sc.kq;
-    ca.q64 = w.q64;
-    ca.p64 = w.p64;
-    ca.q4_next = w.traj_q + (k + 1) * slot;
-    ca.p4_next = w.traj_p + (k + 1) * slot;
-    ca.first = (k == 0);
-    ca.hp0 = w.hp0;
-    ca.hq0 = w.hq0;
-    ca.last = (k == T - 1);
-    ca.with_loss = (kind == 1);
-    ca.t64 = w.t64;
-    ca.lambda = lambda;
-    ca.kappa = sc.kappa;
-    ca.a64 = w.a64;
-    ca.b64 = w.b64;
-    ca.a4 = w.adj_a;
-    ca.b4 = w.adj_b;
-    ca.red_h = w.red_h;
-    ca.red_m = w.red_m;
-    ca.ticket = w.ticket;
-    ca.scalars = w.scalars;
-    ca.status = w.status;
-    GS_CUDA(launch_combine_forward(ca, st, true, nullptr));
+    const StepFwdArgs a = forward_step_args(w, fc, kind, n, T, k, sigma, lambda);
+    GS_CUDA(launch_step_forward(fc, a, st, k > 0));
   }
   if (kind == 0) return GS_OK;
-  for (int k = T - 1; k >= 0; --k) {
-    PairBwdArgs pb;
-    pb.q4 = w.traj_q + k * slot;
-    pb.p4 = w.traj_p + k * slot;
-    pb.a4 = w.adj_a;
-    pb.b4 = w.adj_b;
-    pb.part = w.part;
-    pb.npad = npad;
-    pb.split_len = bc.split_len;
-    pb.kq = static_cast<float>(sc.kq);
-    pb.kappa = static_cast<float>(sc.kappa);
-    pb.status = w.status;
-    GS_CUDA(launch_pair_backward(bc, pb, st, true));
-    CombineBwdArgs cb;
-    std::memset(&cb, 0, sizeof(cb));
-    cb.part = w.part;
-    cb.splits = bc.splits;
-    cb.n = n;
-    cb.npad = npad;
-    cb.dt = dt;
-    cb.kappa = sc.kappa;
-    cb.a64 = w.a64;
-    cb.b64 = w.b64;
-    cb.a4 = w.adj_a;
-    cb.b4 = w.adj_b;
-    cb.first = (k == 0);
-    cb.hp0 = w.hp0;
-    cb.hq0 = w.hq0;
-    cb.grad_p0 = w.out_a;
-    cb.grad_q0 = w.out_b;
-    cb.status = w.status;
-    GS_CUDA(launch_combine_backward(cb, st, true));
+  for (int s = 0; s < T; ++s) {
+    const StepBwdArgs b = backward_step_args(w, bc, n, T, s, sigma);
+    GS_CUDA(launch_step_backward(bc, b, st, true));
   }
   return GS_OK;
 }
@@ -357,9 +362,7 @@ gs_status run_shoot(int kind, const gs_params* prm, const float* q0, const float
   if ((s = get_workspace(&w)) != GS_OK) return s;
   const int n = static_cast<int>(prm->N), T = prm->T;
   const int npad = round_up(n, kPad);
-  const PairConfig fc = choose_forward_config(npad, w->num_sms);
-  const PairConfig bc = choose_backward_config(npad, w->num_sms);
-  if ((s = reserve(*w, npad, T, std::max(fc.splits, bc.splits))) != GS_OK) return s;
+  if ((s = reserve(*w, npad, T, 1)) != GS_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if ((s = ensure_clean(*w, n, st)) != GS_OK) return s;
   const size_t n3 = 3 * static_cast<size_t>(n);
@@ -409,7 +412,6 @@ gs_status run_shoot(int kind, const gs_params* prm, const float* q0, const float
       want_sync = true;
     }
   }
-  (void)bc;
   if (want_sync) return finish_sync(*w, st);
   return GS_OK;
 }
@@ -491,40 +493,24 @@ gs_status time_pair_kernels(const gs_params* prm, const float* q0, const float* 
   Workspace* w = nullptr;
   if ((s = get_workspace(&w)) != GS_OK) return s;
   const int n = static_cast<int>(prm->N), T = prm->T, npad = round_up(n, kPad);
-  const KernelScales sc = make_scales(prm->sigma);
-  const PairConfig fc = choose_forward_config(npad, w->num_sms);
-  const PairConfig bc = choose_backward_config(npad, w->num_sms);
+  const StepConfig fc = choose_step_config(0, npad, w->num_sms);
+  const StepConfig bc = choose_step_config(1, npad, w->num_sms);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const size_t slot = static_cast<size_t>(w->cap_npad) * (T / 2);
+  // Middle time step of the trajectory just computed; dry runs change no state.
+  StepFwdArgs fa = forward_step_args(*w, fc, 1, n, T, T / 2, prm->sigma, prm->lambda);
+  fa.dry = 1;
+  StepBwdArgs ba = backward_step_args(*w, bc, n, T, T - 1 - T / 2, prm->sigma);
+  ba.dry = 1;
   cudaEvent_t e0, e1, e2;
   GS_CUDA(cudaEventCreate(&e0));
   GS_CUDA(cudaEventCreate(&e1));
   GS_CUDA(cudaEventCreate(&e2));
-  PairFwdArgs pa;
-  pa.q4 = w->traj_q + slot;
-  pa.p4 = w->traj_p + slot;
-  pa.part = w->part;
-  pa.npad = npad;
-  pa.split_len = fc.split_len;
-  pa.kappa = static_cast<float>(sc.kappa);
-  pa.status = w->status;
-  PairBwdArgs pb;
-  pb.q4 = pa.q4;
-  pb.p4 = pa.p4;
-  pb.a4 = w->adj_a;
-  pb.b4 = w->adj_b;
-  pb.part = w->part;
-  pb.npad = npad;
-  pb.split_len = bc.split_len;
-  pb.kq = static_cast<float>(sc.kq);
-  pb.kappa = static_cast<float>(sc.kappa);
-  pb.status = w->status;
-  GS_CUDA(launch_pair_forward(fc, pa, st, false));  // warm-up
-  GS_CUDA(launch_pair_backward(bc, pb, st, false));
+  GS_CUDA(launch_step_forward(fc, fa, st, false));  // warm-up
+  GS_CUDA(launch_step_backward(bc, ba, st, false));
   GS_CUDA(cudaEventRecord(e0, st));
-  for (int r = 0; r < reps; ++r) GS_CUDA(launch_pair_forward(fc, pa, st, false));
+  for (int r = 0; r < reps; ++r) GS_CUDA(launch_step_forward(fc, fa, st, false));
   GS_CUDA(cudaEventRecord(e1, st));
-  for (int r = 0; r < reps; ++r) GS_CUDA(launch_pair_backward(bc, pb, st, false));
+  for (int r = 0; r < reps; ++r) GS_CUDA(launch_step_backward(bc, ba, st, false));
   GS_CUDA(cudaEventRecord(e2, st));
   GS_CUDA(cudaEventSynchronize(e2));
   float m1 = 0.f, m2 = 0.f;
@@ -535,7 +521,122 @@ gs_status time_pair_kernels(const gs_params* prm, const float* q0, const float* 
   cudaEventDestroy(e2);
   if (fwd_ms) *fwd_ms = m1 / reps;
   if (bwd_ms) *bwd_ms = m2 / reps;
-  if (launches) *launches = 4 * T + 1;
+  if (launches) *launches = 2 * T + 1;
+  return finish_sync(*w, st);
+}
+
+gs_status time_pair_config(int kind_in, int64_t N, double sigma, const float* q, const float* p,
+                           const float* alpha, const float* beta, int threads, int R, int splits, int reps, double* ms,
+                           int* used, void* stream) {
+  const bool graph = (kind_in & 16) != 0;
+  const int kind = kind_in & ~16;
+  if (kind < 0 || kind > 3) return fail(GS_EINVAL, "kind must be 0..3 (+16 for graph replay)");
+  if (N < 1 || N > (1LL << 26)) return fail(GS_EINVAL, "N must be in [1, 2^26]");
+  if (!(sigma > 0.0) || !std::isfinite(sigma)) return fail(GS_EINVAL, "sigma must be finite and > 0");
+  if (reps < 1 || reps > 100000) return fail(GS_EINVAL, "reps must be in [1, 100000]");
+  const bool bwd = (kind == 1 || kind == 3);
+  if (!q || !p || (bwd && (!alpha || !beta))) return fail(GS_EINVAL, "array arguments must not be NULL");
+  std::lock_guard<std::mutex> lk(g_mu);
+  Workspace* w = nullptr;
+  gs_status s = get_workspace(&w);
+  if (s != GS_OK) return s;
+  const int n = static_cast<int>(N), npad = round_up(n, kPad);
+  PairConfig c{};
+  StepConfig sc{};
+  if (kind < 2) {
+    c = kind == 0 ? forward_config_for(npad, w->num_sms, threads, R, splits)
+                  : backward_config_for(npad, w->num_sms, threads, R, splits);
+    if (c.threads == 0) return fail(GS_EINVAL, "no such kernel variant");
+  } else {
+    sc = step_config_for(kind - 2, npad, threads, R, splits);
+    if (sc.threads == 0) return fail(GS_EINVAL, "no such step kernel variant / cluster size");
+  }
+  if ((s = reserve(*w, npad, 1, kind < 2 ? c.splits : 1)) != GS_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t n3 = 3 * static_cast<size_t>(n);
+  bool host = false;
+  const float *dq, *dp, *da = nullptr, *db = nullptr;
+  if ((s = stage_in(q, w->in_q, n3, st, &dq, &host)) != GS_OK) return s;
+  if ((s = stage_in(p, w->in_p, n3, st, &dp, &host)) != GS_OK) return s;
+  if (bwd) {
+    if ((s = stage_in(alpha, w->in_a, n3, st, &da, &host)) != GS_OK) return s;
+    if ((s = stage_in(beta, w->in_t, n3, st, &db, &host)) != GS_OK) return s;
+  }
+  const KernelScales ks = make_scales(sigma);
+  GS_CUDA(launch_to_float4(dq, w->traj_q, n, npad, ks.kq, w->status, st));
+  GS_CUDA(launch_to_float4(dp, w->traj_p, n, npad, 1.0, w->status, st));
+  if (bwd) {
+    GS_CUDA(launch_to_float4(da, w->adj_a, n, npad, 1.0, w->status, st));
+    GS_CUDA(launch_to_float4(db, w->adj_b, n, npad, ks.kappa, w->status, st));
+  }
+  w->clean_n = -1;
+  PairFwdArgs fa;
+  fa.q4 = w->traj_q;
+  fa.p4 = w->traj_p;
+  fa.part = w->part;
+  fa.npad = npad;
+  fa.split_len = c.split_len;
+  fa.kappa = static_cast<float>(ks.kappa);
+  fa.status = w->status;
+  PairBwdArgs ba;
+  ba.q4 = w->traj_q;
+  ba.p4 = w->traj_p;
+  ba.a4 = w->adj_a;
+  ba.b4 = w->adj_b;
+  ba.part = w->part;
+  ba.npad = npad;
+  ba.split_len = c.split_len;
+  ba.kq = static_cast<float>(ks.kq);
+  ba.kappa = static_cast<float>(ks.kappa);
+  ba.status = w->status;
+  StepFwdArgs sfa = forward_step_args(*w, sc, 1, n, 1, 0, sigma, 1.0);
+  sfa.dry = 1;
+  StepBwdArgs sba = backward_step_args(*w, sc, n, 1, 0, sigma);
+  sba.dry = 1;
+  auto once = [&](cudaStream_t s, bool pdl) {
+    switch (kind) {
+      case 0: return launch_pair_forward(c, fa, s, pdl);
+      case 1: return launch_pair_backward(c, ba, s, pdl);
+      case 2: return launch_step_forward(sc, sfa, s, pdl);
+      default: return launch_step_backward(sc, sba, s, pdl);
+    }
+  };
+  GS_CUDA(once(st, false));  // warm-up
+  cudaGraphExec_t ge = nullptr;
+  if (graph) {  // the reps launches as one graph, linked by programmatic dependent launch
+    cudaStream_t cs = w->capture_stream;
+    GS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = once(cs, r > 0);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return fail(GS_ECUDA, std::string("capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(GS_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+    GS_CUDA(cudaGraphLaunch(ge, st));  // warm-up replay
+  }
+  cudaEvent_t e0, e1;
+  GS_CUDA(cudaEventCreate(&e0));
+  GS_CUDA(cudaEventCreate(&e1));
+  GS_CUDA(cudaEventRecord(e0, st));
+  if (graph) {
+    GS_CUDA(cudaGraphLaunch(ge, st));
+  } else {
+    for (int r = 0; r < reps; ++r) GS_CUDA(once(st, false));
+  }
+  GS_CUDA(cudaEventRecord(e1, st));
+  GS_CUDA(cudaEventSynchronize(e1));
+  float t = 0.f;
+  GS_CUDA(cudaEventElapsedTime(&t, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (ge) cudaGraphExecDestroy(ge);
+  if (ms) *ms = t / reps;
+  if (used) *used = kind < 2 ? c.splits : sc.cluster;
   return finish_sync(*w, st);
 }
 
@@ -578,6 +679,31 @@ gs_status gs_time_pair_kernels(const gs_params* prm, const float* q0, const floa
   gs_status s = gs::time_pair_kernels(prm, q0, p0, target, reps, fwd_ms, bwd_ms, &l, stream);
   if (launches_per_eval) *launches_per_eval = l;
   return s;
+}
+
+gs_status gs_time_pair_config(int32_t kind, int64_t N, double sigma, const float* q, const float* p,
+                              const float* alpha, const float* beta, int32_t threads, int32_t R, int32_t splits,
+                              int32_t reps, double* ms, int32_t* splits_used, void* stream) {
+  gs::g_err.clear();
+  int used = 0;
+  gs_status s = gs::time_pair_config(kind, N, sigma, q, p, alpha, beta, threads, R, splits, reps, ms, &used, stream);
+  if (splits_used) *splits_used = used;
+  return s;
+}
+
+gs_status gs_set_step_config(int32_t kind, int32_t threads, int32_t R, int32_t cluster) {
+  gs::g_err.clear();
+  if (kind != 0 && kind != 1) {
+    gs::set_last_error("kind must be 0 (forward) or 1 (reverse)");
+    return GS_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(gs::g_mu);
+  if (!gs::set_step_override(kind, threads, R, cluster)) {
+    gs::set_last_error("no such step kernel variant / cluster size");
+    return GS_EINVAL;
+  }
+  for (auto& kv : gs::g_ws) kv.second->drop_graphs();
+  return GS_OK;
 }
 
 const char* gs_last_error(void) { return gs::g_err.c_str(); }

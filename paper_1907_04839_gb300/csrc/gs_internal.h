@@ -4,8 +4,8 @@
 // multiple of kPad, padded landmarks stay exactly zero):
 //   traj_q[k]  float4[Npad]  kq * q^k (xyz, w = 0), the prescaled positions
 //   traj_p[k]  float4[Npad]  p^k (xyz, w = 0)
-//   adj_a      float4[Npad]  alpha (adjoint of q) of the current reverse step
-//   adj_b      float4[Npad]  kappa * beta (adjoint of p, prescaled)
+//   adj_a[2]   float4[Npad]  alpha (adjoint of q), two buffers: a reverse step
+//   adj_b[2]   float4[Npad]  reads one and writes the other; b holds kappa*beta
 //   q64, p64, a64, b64       double[N*3], FP64 master state, (N,3) row-major
 //   part       Partial[S][Npad], per source split: six double-single sums
 // with kq = sqrt(log2(e) / 2) / sigma (so g = 2^-(|kq d|^2)),
@@ -75,6 +75,10 @@ struct PairConfig {
 };
 
 PairConfig choose_forward_config(int npad, int num_sms);
+// A given kernel variant (threads per CTA, targets per thread); splits <= 0
+// picks the balanced split count.  threads == 0 in the result: no such variant.
+PairConfig forward_config_for(int npad, int num_sms, int threads, int R, int splits);
+PairConfig backward_config_for(int npad, int num_sms, int threads, int R, int splits);
 PairConfig choose_backward_config(int npad, int num_sms);
 // Forward configuration with at most `max_splits` source splits.
 PairConfig choose_forward_config_capped(int npad, int num_sms, int max_splits);
@@ -84,6 +88,77 @@ void set_last_error(const char* msg);
 
 cudaError_t launch_pair_forward(const PairConfig& cfg, const PairFwdArgs& a, cudaStream_t st, bool pdl);
 cudaError_t launch_pair_backward(const PairConfig& cfg, const PairBwdArgs& a, cudaStream_t st, bool pdl);
+
+// ---------------------------------------------------------------- fused step kernels
+// One kernel per time step: a thread-block cluster of C CTAs owns a tile of
+// targets; CTA rank r sums sources [r*split_len, (r+1)*split_len).  The C
+// partial sums meet in distributed shared memory, and each CTA finishes the
+// Euler (or adjoint) update for 1/C of the tile.
+struct StepConfig {
+  int threads;    // CTA size
+  int R;          // targets per thread
+  int cluster;    // C, CTAs per cluster = source splits
+  int tiles;      // clusters = ceil(Npad / (threads * R))
+  int split_len;  // sources per CTA (multiple of 8)
+};
+
+struct StepFwdArgs {
+  const float4* q4;    // traj_q[k]
+  const float4* p4;    // traj_p[k]
+  float4* q4_next;     // traj_q[k+1]
+  float4* p4_next;     // traj_p[k+1]
+  int n, npad, split_len;
+  float kappa;
+  double dt, kq;
+  double* q64;
+  double* p64;
+  int first;           // keep Hp, Hq of step 0 and reduce H0
+  double* hp0;
+  double* hq0;
+  int last;            // last step of a gradient: loss terms and adjoint init
+  int with_loss;
+  const double* t64;
+  double lambda;
+  double* a64;
+  double* b64;
+  float4* a4;          // adjoint buffer the first reverse step reads
+  float4* b4;
+  double* red_h;       // per-CTA partial sums (grid-sized)
+  double* red_m;
+  unsigned* ticket;
+  double* scalars;     // [0] = H0, [1] = loss
+  int dry;             // tuning: compute everything, write nothing
+  unsigned* status;
+};
+
+struct StepBwdArgs {
+  const float4* q4;    // traj_q[k]
+  const float4* p4;    // traj_p[k]
+  const float4* a4;    // alpha of step k+1
+  const float4* b4;    // kappa * beta of step k+1
+  float4* a4_next;     // alpha of step k (the other buffer)
+  float4* b4_next;
+  int n, npad, split_len;
+  float kq, kappa;
+  double dt, kappa64;
+  double* a64;
+  double* b64;
+  int first;           // k == 0: write the gradient
+  const double* hp0;
+  const double* hq0;
+  float* grad_p0;
+  float* grad_q0;
+  int dry;
+  unsigned* status;
+};
+
+StepConfig step_config_for(int kind, int npad, int threads, int R, int cluster);
+StepConfig choose_step_config(int kind, int npad, int num_sms);
+// Override the fused step configuration of `kind` (threads == 0 restores the
+// built-in choice).  Returns false for an unknown variant.
+bool set_step_override(int kind, int threads, int R, int cluster);
+cudaError_t launch_step_forward(const StepConfig& cfg, const StepFwdArgs& a, cudaStream_t st, bool pdl);
+cudaError_t launch_step_backward(const StepConfig& cfg, const StepBwdArgs& a, cudaStream_t st, bool pdl);
 
 // ---------------------------------------------------------------- combine kernels
 struct PackArgs {
@@ -100,58 +175,6 @@ struct PackArgs {
   unsigned* status;
 };
 
-struct CombineFwdArgs {
-  const Partial* part;
-  int splits;
-  int n, npad;
-  double dt;
-  double kq;
-  double* q64;
-  double* p64;
-  float4* q4_next;     // traj_q[k+1]
-  float4* p4_next;     // traj_p[k+1]
-  // step 0: keep Hp(q0,p0), Hq(q0,p0) and reduce H0 = 1/2 sum p0 . Hp
-  int first;
-  double* hp0;
-  double* hq0;
-  // last step: loss = H0 + lambda |q - t|^2, alpha = 2 lambda (q - t), beta = 0
-  int last;
-  int with_loss;
-  const double* t64;
-  double lambda;
-  double kappa;
-  double* a64;
-  double* b64;
-  float4* a4;
-  float4* b4;
-  // deterministic grid reduction: per-CTA partials + ticket; scalars[0] = H0,
-  // scalars[1] = loss
-  double* red_h;
-  double* red_m;
-  unsigned* ticket;
-  double* scalars;
-  unsigned* status;
-};
-
-struct CombineBwdArgs {
-  const Partial* part;
-  int splits;
-  int n, npad;
-  double dt;
-  double kappa;
-  double* a64;
-  double* b64;
-  float4* a4;
-  float4* b4;
-  // step 0: gradient assembly
-  int first;
-  const double* hp0;
-  const double* hq0;
-  float* grad_p0;      // (N,3) float32, may be null
-  float* grad_q0;
-  unsigned* status;
-};
-
 struct UnpackArgs {
   const double* x64;
   float* out;
@@ -159,8 +182,6 @@ struct UnpackArgs {
 };
 
 cudaError_t launch_pack(const PackArgs& a, cudaStream_t st);
-cudaError_t launch_combine_forward(const CombineFwdArgs& a, cudaStream_t st, bool pdl, int* grid_out);
-cudaError_t launch_combine_backward(const CombineBwdArgs& a, cudaStream_t st, bool pdl);
 cudaError_t launch_unpack(const UnpackArgs& a, cudaStream_t st);
 // Hq, Hp straight from one split-partial set (step_forward entry point).
 cudaError_t launch_partials_to_out(const Partial* part, int splits, int n, int npad,
@@ -170,5 +191,6 @@ cudaError_t launch_to_float4(const float* x, float4* x4, int n, int npad, double
                              unsigned* status, cudaStream_t st);
 
 int combine_threads();
+int combine_group();  // lanes per landmark in the combine kernels
 
 }  // namespace gs

@@ -1,0 +1,351 @@
+// Fused time-step kernels: StepForward plus the Euler update (Algorithm 1,
+// lines 6-8), and StepBackward plus the adjoint update (lines 13-15).  Each
+// runs as one launch per time step.
+//
+// Work split.  A thread-block cluster of C CTAs owns a tile of M = NT*R
+// targets.  CTA rank r sums the pair terms of every target in the tile
+// against one contiguous split of the sources (pair_tile.cuh).  The C splits
+// together cover all N sources.  The split sums then meet in distributed
+// shared memory: each CTA writes its tile partials to its own shared memory,
+// and after a cluster barrier CTA r adds the C partials of targets
+// [r*M/C, (r+1)*M/C) in rank order, in double-single arithmetic.  It then
+// applies the FP64 update to those targets.  The reduction order is fixed,
+// so results are deterministic.  No split partials go through global
+// memory, and no second kernel is needed.  This plays the role of the
+// paper's shared-memory reduction (Section 2.5), spread over up to 16 SMs.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <mutex>
+#include <set>
+
+#include "pair_tile.cuh"
+
+namespace gs {
+
+namespace {
+
+// Grid-wide deterministic sum of per-CTA values: each CTA stores its value
+// at red[cta]; the last CTA to take a ticket adds them with one warp in a
+// fixed order.  Returns true in the threads of the finishing warp; their
+// *out holds the total.
+__device__ __forceinline__ bool grid_sum2(double vh, double vm, double* red_h, double* red_m, unsigned* ticket,
+                                          double* sh, int* am_last, double* out_h, double* out_m) {
+  const double bh = block_sum_f64(vh, sh);
+  const double bm = block_sum_f64(vm, sh);
+  const unsigned cta = blockIdx.y * gridDim.x + blockIdx.x;
+  const unsigned ncta = gridDim.x * gridDim.y;
+  if (threadIdx.x == 0) {
+    red_h[cta] = bh;
+    red_m[cta] = bm;
+    __threadfence();
+    const unsigned tk = atomicAdd(ticket, 1u);
+    *am_last = (tk == ncta - 1);
+  }
+  __syncthreads();
+  if (!*am_last || threadIdx.x >= 32) return false;
+  __threadfence();
+  double h = 0.0, m = 0.0;
+  for (unsigned b = threadIdx.x; b < ncta; b += 32) {
+    h += *((volatile double*)&red_h[b]);
+    m += *((volatile double*)&red_m[b]);
+  }
+  *out_h = warp_sum_f64(h);
+  *out_m = warp_sum_f64(m);
+  return true;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- forward step
+template <int NT, int R>
+__global__ void __launch_bounds__(NT) k_step_forward(StepFwdArgs a) {
+  constexpr int M = NT * R;
+  union Smem {
+    StageBuf<2> st;
+    float4 red[M][3];  // Hp (hi,lo) x3 then Hq (hi,lo) x3 per target
+  };
+  __shared__ __align__(128) Smem sm;
+  __shared__ __align__(8) uint64_t full[2];
+  __shared__ double shred[NT / 32];
+  __shared__ int am_last;
+
+  const unsigned rank = cluster_rank(), C = cluster_size();
+  const int tile = blockIdx.y;
+  const int j0 = min(static_cast<int>(rank) * a.split_len, a.npad);
+  const int j1 = min(j0 + a.split_len, a.npad);
+  if (threadIdx.x == 0) stage_init(full);
+  __syncthreads();
+  pdl_wait();  // the previous step's state must be complete
+  pdl_launch_dependents();
+
+  const int base = tile * M + threadIdx.x;
+  FwdTile<R> t;
+  t.load(a.q4, a.p4, base, NT, a.npad);
+  const float4* src[2] = {a.q4, a.p4};
+  stream_sources<2>(sm.st, full, src, j0, j1, t, a.status);  // ends with a CTA barrier
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    ds v[6];
+    t.result(r, a.kappa, v);
+    const int lt = threadIdx.x + r * NT;
+    sm.red[lt][0] = make_float4(v[0].hi, v[0].lo, v[1].hi, v[1].lo);
+    sm.red[lt][1] = make_float4(v[2].hi, v[2].lo, v[3].hi, v[3].lo);
+    sm.red[lt][2] = make_float4(v[4].hi, v[4].lo, v[5].hi, v[5].lo);
+  }
+  cluster_sync();  // every CTA's tile partials are visible to the cluster
+
+  const int slice = M / static_cast<int>(C);
+  double hc = 0.0, mc = 0.0;
+  for (int item = threadIdx.x; item < slice * 3; item += NT) {
+    const int lt = static_cast<int>(rank) * slice + item / 3;
+    const int k = item % 3;
+    const int i = tile * M + lt;
+    if (i >= a.n) continue;
+    const uint32_t lp = smem_u32(&sm.red[lt][0]);
+    ds hp{0.f, 0.f}, hq{0.f, 0.f};
+#pragma unroll 4
+    for (unsigned rr = 0; rr < C; ++rr) {
+      const uint32_t rp = dsmem_addr(lp, rr);
+      const float2 x = ld_dsmem_f2(rp + 8u * k);
+      const float2 y = ld_dsmem_f2(rp + 24u + 8u * k);
+      hp = ds_add(hp, ds{x.x, x.y});
+      hq = ds_add(hq, ds{y.x, y.y});
+    }
+    if (a.dry) {  // timing only: keep the reduction, touch no state
+      hc += ds_to_double(hp) + ds_to_double(hq);
+      continue;
+    }
+    const int tt = 3 * i + k;
+    const double Hp = ds_to_double(hp), Hq = ds_to_double(hq);
+    const double p_old = a.p64[tt];
+    const double q = a.q64[tt] + a.dt * Hp;
+    const double p = p_old - a.dt * Hq;
+    if (!isfinite(q) || !isfinite(p)) atomicOr(a.status, kErrNonFinite);
+    if (a.first) hc += 0.5 * p_old * Hp;  // H0 = 1/2 sum_i p0_i . Hp_i(q0, p0)
+    double r = 0.0;
+    if (a.last && a.with_loss) {
+      r = q - a.t64[tt];
+      mc += r * r;
+    }
+    if (a.first) {
+      a.hp0[tt] = Hp;
+      a.hq0[tt] = Hq;
+    }
+    a.q64[tt] = q;
+    a.p64[tt] = p;
+    reinterpret_cast<float*>(a.q4_next)[4 * i + k] = (float)(a.kq * q);
+    reinterpret_cast<float*>(a.p4_next)[4 * i + k] = (float)p;
+    if (a.last && a.with_loss) {
+      const double al = 2.0 * a.lambda * r;
+      a.a64[tt] = al;
+      a.b64[tt] = 0.0;
+      reinterpret_cast<float*>(a.a4)[4 * i + k] = (float)al;
+      reinterpret_cast<float*>(a.b4)[4 * i + k] = 0.f;
+    }
+  }
+  cluster_sync();  // peers may still be reading this CTA's partials
+
+  const bool reduce_h = a.first != 0;
+  const bool reduce_m = a.last && a.with_loss;
+  if ((!reduce_h && !reduce_m) || a.dry) return;  // uniform across the grid
+  double h, m;
+  if (grid_sum2(hc, mc, a.red_h, a.red_m, a.ticket, shred, &am_last, &h, &m) && threadIdx.x == 0) {
+    if (reduce_h) a.scalars[0] = h;
+    if (reduce_m) a.scalars[1] = (reduce_h ? h : a.scalars[0]) + a.lambda * m;
+    *a.ticket = 0u;
+  }
+}
+
+// ---------------------------------------------------------------- backward step
+template <int NT, int R>
+__global__ void __launch_bounds__(NT) k_step_backward(StepBwdArgs a) {
+  constexpr int M = NT * R;
+  union Smem {
+    StageBuf<4> st;
+    float4 red[M][3];  // dalpha (hi,lo) x3 then dbeta (hi,lo) x3 per target
+  };
+  __shared__ __align__(128) Smem sm;
+  __shared__ __align__(8) uint64_t full[2];
+
+  const unsigned rank = cluster_rank(), C = cluster_size();
+  const int tile = blockIdx.y;
+  const int j0 = min(static_cast<int>(rank) * a.split_len, a.npad);
+  const int j1 = min(j0 + a.split_len, a.npad);
+  if (threadIdx.x == 0) stage_init(full);
+  __syncthreads();
+  pdl_wait();
+  pdl_launch_dependents();
+
+  const int base = tile * M + threadIdx.x;
+  BwdTile<R> t;
+  t.load(a.q4, a.p4, a.a4, a.b4, base, NT, a.npad);
+  const float4* src[4] = {a.q4, a.p4, a.a4, a.b4};
+  stream_sources<4>(sm.st, full, src, j0, j1, t, a.status);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    ds v[6];
+    t.result(r, a.kq, a.kappa, v);
+    const int lt = threadIdx.x + r * NT;
+    sm.red[lt][0] = make_float4(v[0].hi, v[0].lo, v[1].hi, v[1].lo);
+    sm.red[lt][1] = make_float4(v[2].hi, v[2].lo, v[3].hi, v[3].lo);
+    sm.red[lt][2] = make_float4(v[4].hi, v[4].lo, v[5].hi, v[5].lo);
+  }
+  cluster_sync();
+
+  const int slice = M / static_cast<int>(C);
+  for (int item = threadIdx.x; item < slice * 3; item += NT) {
+    const int lt = static_cast<int>(rank) * slice + item / 3;
+    const int k = item % 3;
+    const int i = tile * M + lt;
+    if (i >= a.n) continue;
+    const uint32_t lp = smem_u32(&sm.red[lt][0]);
+    ds da{0.f, 0.f}, db{0.f, 0.f};
+#pragma unroll 4
+    for (unsigned rr = 0; rr < C; ++rr) {
+      const uint32_t rp = dsmem_addr(lp, rr);
+      const float2 x = ld_dsmem_f2(rp + 8u * k);
+      const float2 y = ld_dsmem_f2(rp + 24u + 8u * k);
+      da = ds_add(da, ds{x.x, x.y});
+      db = ds_add(db, ds{y.x, y.y});
+    }
+    if (a.dry) {
+      if (!isfinite(da.hi + db.hi)) atomicOr(a.status, kErrNonFinite);
+      continue;
+    }
+    const int tt = 3 * i + k;
+    const double al = a.a64[tt] + a.dt * ds_to_double(da);
+    const double be = a.b64[tt] + a.dt * ds_to_double(db);
+    if (!isfinite(al) || !isfinite(be)) atomicOr(a.status, kErrNonFinite);
+    a.a64[tt] = al;
+    a.b64[tt] = be;
+    reinterpret_cast<float*>(a.a4_next)[4 * i + k] = (float)al;
+    reinterpret_cast<float*>(a.b4_next)[4 * i + k] = (float)(a.kappa64 * be);
+    if (a.first) {
+      if (a.grad_p0) a.grad_p0[tt] = (float)(be + a.hp0[tt]);
+      if (a.grad_q0) a.grad_q0[tt] = (float)(al + a.hq0[tt]);
+    }
+  }
+  cluster_sync();
+}
+
+// ---------------------------------------------------------------- host side
+
+namespace {
+
+struct Variant {
+  int threads, R;
+};
+#define GS_STEP_FWD_CASES(X) X(64, 2) X(64, 4) X(128, 1) X(128, 2) X(128, 4) X(256, 1) X(256, 2)
+#define GS_STEP_BWD_CASES(X) X(64, 1) X(64, 2) X(128, 1) X(128, 2) X(256, 1)
+
+std::mutex g_attr_mu;
+std::set<const void*> g_attr_done;  // kernels allowed clusters of up to 16 CTAs
+
+template <typename K, typename A>
+cudaError_t launch_cluster(K kern, const StepConfig& c, const A& args, cudaStream_t st, bool pdl) {
+  {
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    const void* key = reinterpret_cast<const void*>(kern);
+    if (!g_attr_done.count(key)) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+      g_attr_done.insert(key);
+    }
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(c.cluster, c.tiles);
+  cfg.blockDim = dim3(c.threads);
+  cfg.stream = st;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = c.cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 2 : 1;
+  return cudaLaunchKernelEx(&cfg, kern, args);
+}
+
+bool valid_variant(int kind, int threads, int R) {
+#define X(T_, R_) \
+  if (threads == T_ && R == R_) return true;
+  if (kind == 0) {
+    GS_STEP_FWD_CASES(X)
+  } else {
+    GS_STEP_BWD_CASES(X)
+  }
+#undef X
+  return false;
+}
+
+}  // namespace
+
+StepConfig step_config_for(int kind, int npad, int threads, int R, int cluster) {
+  StepConfig c{};
+  if (!valid_variant(kind, threads, R)) return c;
+  const int M = threads * R;
+  if (cluster < 1 || cluster > 16 || (cluster & (cluster - 1)) != 0 || cluster > M) return c;
+  c.threads = threads;
+  c.R = R;
+  c.cluster = cluster;
+  c.tiles = (npad + M - 1) / M;
+  int len = (npad + cluster - 1) / cluster;
+  c.split_len = (len + kUnroll - 1) / kUnroll * kUnroll;
+  return c;
+}
+
+namespace {
+int g_override[2][3] = {{0, 0, 0}, {0, 0, 0}};  // threads, R, cluster per kind
+}
+
+bool set_step_override(int kind, int threads, int R, int cluster) {
+  if (threads == 0) {
+    g_override[kind][0] = g_override[kind][1] = g_override[kind][2] = 0;
+    return true;
+  }
+  if (step_config_for(kind, 1 << 16, threads, R, cluster).threads == 0) return false;
+  g_override[kind][0] = threads;
+  g_override[kind][1] = R;
+  g_override[kind][2] = cluster;
+  return true;
+}
+
+// Default configuration per problem size, from sweeps on GB300 (152 SMs).
+StepConfig choose_step_config(int kind, int npad, int num_sms) {
+  (void)num_sms;
+  if (g_override[kind][0]) {
+    const StepConfig c = step_config_for(kind, npad, g_override[kind][0], g_override[kind][1],
+                                         std::min(g_override[kind][2], std::max(1, npad / kUnroll)));
+    if (c.threads) return c;
+  }
+  // Measured on GB300 (in-graph replay of the fused kernels, landmark
+  // counts 1024..65536): 128-thread CTAs with one target per thread forward,
+  // 64-thread CTAs backward, clusters of 16 up to 16k landmarks and of 8
+  // beyond.
+  const int cl = std::min(npad >= 32768 ? 8 : 16, std::max(1, npad / kUnroll));
+  int c = 1;
+  while (c * 2 <= cl) c *= 2;
+  if (kind == 0) return step_config_for(0, npad, 128, 1, c);
+  return step_config_for(1, npad, 64, 1, c);
+}
+
+cudaError_t launch_step_forward(const StepConfig& c, const StepFwdArgs& a, cudaStream_t st, bool pdl) {
+#define X(T_, R_) \
+  if (c.threads == T_ && c.R == R_) return launch_cluster(k_step_forward<T_, R_>, c, a, st, pdl);
+  GS_STEP_FWD_CASES(X)
+#undef X
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_step_backward(const StepConfig& c, const StepBwdArgs& a, cudaStream_t st, bool pdl) {
+#define X(T_, R_) \
+  if (c.threads == T_ && c.R == R_) return launch_cluster(k_step_backward<T_, R_>, c, a, st, pdl);
+  GS_STEP_BWD_CASES(X)
+#undef X
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace gs

@@ -137,7 +137,7 @@ gs_status gs_time_pair_kernels(const gs_params* prm, const float* q0, const floa
  * whose device memory is owned by another allocator under a fixed budget, or
  * code for which a cudaMalloc (which can synchronise the whole device) is not
  * acceptable.  This entry point computes the same Hq, Hp as step_forward, but
- * uses a file-scope static device array of about 3.4 MB as its scratch.  It
+ * uses a file-scope static device array of about 3.3 MB as its scratch.  It
  * never calls cudaMalloc, cudaFree or any allocating routine.
  *
  * Limits: 1 <= N <= 8192.  Larger N is rejected with GS_EINVAL before any

@@ -31,8 +31,9 @@ __global__ void __launch_bounds__(kThreads) k_pack(PackArgs a) {
   a.q64[t] = q;
   a.p64[t] = p;
   if (a.t64) a.t64[t] = tg;
-  reinterpret_cast<float*>(a.q4)[4 * i + k] = (float)(a.kq * (double)q);
-  reinterpret_cast<float*>(a.p4)[4 * i + k] = p;
+  float* r = reinterpret_cast<float*>(a.qp + (i >> 1) * kRecF4) + 2 * k + (i & 1);
+  r[0] = -(float)(a.kq * (double)q);
+  r[6] = p;
 }
 
 // Sum the split partials of landmark i over a group of kGroup lanes: lane l
@@ -86,17 +87,23 @@ __global__ void __launch_bounds__(kThreads) k_partials_to_out(const Partial* par
   else out_b[3 * i + k] = (float)ds_to_double(acc[3 + k]);
 }
 
-__global__ void __launch_bounds__(kThreads) k_to_float4(const float* x, float4* x4, int n, int npad,
-                                                        double scale, unsigned* status) {
+// One thread per landmark slot i < npad (padding written as zeros).
+__global__ void __launch_bounds__(kThreads) k_to_records(const float* x, const float* y, float4* rec, int n, int npad,
+                                                         double sx, double sy, int ab_layout, unsigned* status) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= npad) return;
-  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (i < n) {
-    const float a = x[3 * i], b = x[3 * i + 1], c = x[3 * i + 2];
-    if (!isfinite(a) || !isfinite(b) || !isfinite(c)) atomicOr(status, kErrNonFinite);
-    v = make_float4((float)(scale * a), (float)(scale * b), (float)(scale * c), 0.f);
+  float* r = reinterpret_cast<float*>(rec + (i >> 1) * kRecF4) + (i & 1);
+  const float fx = ab_layout ? 1.f : -1.f, fy = ab_layout ? -1.f : 1.f;
+  for (int k = 0; k < 3; ++k) {
+    float a = 0.f, b = 0.f;
+    if (i < n) {
+      a = x[3 * i + k];
+      b = y[3 * i + k];
+      if (!isfinite(a) || !isfinite(b)) atomicOr(status, kErrNonFinite);
+    }
+    r[2 * k] = fx * (float)(sx * a);
+    r[6 + 2 * k] = fy * (float)(sy * b);
   }
-  x4[i] = v;
 }
 
 inline int blocks_for(long long n) { return static_cast<int>((n + kThreads - 1) / kThreads); }
@@ -146,9 +153,9 @@ cudaError_t launch_partials_to_out(const Partial* part, int splits, int n, int n
   return cudaGetLastError();
 }
 
-cudaError_t launch_to_float4(const float* x, float4* x4, int n, int npad, double scale,
-                             unsigned* status, cudaStream_t st) {
-  k_to_float4<<<blocks_for(npad), kThreads, 0, st>>>(x, x4, n, npad, scale, status);
+cudaError_t launch_to_records(const float* a, const float* b, float4* rec, int n, int npad, double sa, double sb,
+                              int ab_layout, unsigned* status, cudaStream_t st) {
+  k_to_records<<<blocks_for(npad), kThreads, 0, st>>>(a, b, rec, n, npad, sa, sb, ab_layout, status);
   return cudaGetLastError();
 }
 

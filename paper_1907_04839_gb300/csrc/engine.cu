@@ -63,10 +63,9 @@ struct Workspace {
   int cap_npad = 0, cap_T = 0, cap_splits = 0;
   int cap_red = 0;
   std::vector<void*> allocs;
-  float4* traj_q = nullptr;  // (cap_T + 1) * cap_npad
-  float4* traj_p = nullptr;
-  float4* adj_a = nullptr;   // 2 * cap_npad: reverse steps alternate buffers
-  float4* adj_b = nullptr;
+  float4* traj = nullptr;  // (cap_T + 1) slots of QP pair records
+  float4* adj = nullptr;   // 2 slots of AB pair records: reverse steps alternate
+  size_t slot() const { return static_cast<size_t>(kRecF4) * (cap_npad / 2); }  // float4 per slot
   double *q64 = nullptr, *p64 = nullptr, *a64 = nullptr, *b64 = nullptr, *t64 = nullptr;
   double *hp0 = nullptr, *hq0 = nullptr;
   Partial* part = nullptr;   // cap_splits * cap_npad
@@ -130,10 +129,9 @@ gs_status reserve(Workspace& w, int npad, int T, int splits) {
   const int cs = std::max(splits, w.cap_splits), cr = std::max(red, w.cap_red);
   w.free_all();
   const size_t n3 = 3 * static_cast<size_t>(cn);
-  GS_CUDA(dalloc(w, &w.traj_q, static_cast<size_t>(cT + 1) * cn));
-  GS_CUDA(dalloc(w, &w.traj_p, static_cast<size_t>(cT + 1) * cn));
-  GS_CUDA(dalloc(w, &w.adj_a, 2 * static_cast<size_t>(cn)));
-  GS_CUDA(dalloc(w, &w.adj_b, 2 * static_cast<size_t>(cn)));
+  const size_t slot = static_cast<size_t>(kRecF4) * (cn / 2);
+  GS_CUDA(dalloc(w, &w.traj, static_cast<size_t>(cT + 1) * slot));
+  GS_CUDA(dalloc(w, &w.adj, 2 * slot));
   GS_CUDA(dalloc(w, &w.q64, n3));
   GS_CUDA(dalloc(w, &w.p64, n3));
   GS_CUDA(dalloc(w, &w.a64, n3));
@@ -167,10 +165,8 @@ gs_status reserve(Workspace& w, int npad, int T, int splits) {
 // changes: padded entries must be exactly zero (they are never written).
 gs_status ensure_clean(Workspace& w, int n, cudaStream_t st) {
   if (w.clean_n == n) return GS_OK;
-  GS_CUDA(cudaMemsetAsync(w.traj_q, 0, sizeof(float4) * (w.cap_T + 1) * static_cast<size_t>(w.cap_npad), st));
-  GS_CUDA(cudaMemsetAsync(w.traj_p, 0, sizeof(float4) * (w.cap_T + 1) * static_cast<size_t>(w.cap_npad), st));
-  GS_CUDA(cudaMemsetAsync(w.adj_a, 0, 2 * sizeof(float4) * w.cap_npad, st));
-  GS_CUDA(cudaMemsetAsync(w.adj_b, 0, 2 * sizeof(float4) * w.cap_npad, st));
+  GS_CUDA(cudaMemsetAsync(w.traj, 0, sizeof(float4) * (w.cap_T + 1) * w.slot(), st));
+  GS_CUDA(cudaMemsetAsync(w.adj, 0, 2 * sizeof(float4) * w.slot(), st));
   w.clean_n = n;
   return GS_OK;
 }
@@ -238,13 +234,11 @@ StepFwdArgs forward_step_args(Workspace& w, const StepConfig& c, int kind, int n
                               double lambda) {
   const int npad = round_up(n, kPad);
   const KernelScales sc = make_scales(sigma);
-  const size_t slot = static_cast<size_t>(w.cap_npad);
+  const size_t slot = w.slot();
   StepFwdArgs a;
   std::memset(&a, 0, sizeof(a));
-  a.q4 = w.traj_q + k * slot;
-  a.p4 = w.traj_p + k * slot;
-  a.q4_next = w.traj_q + (k + 1) * slot;
-  a.p4_next = w.traj_p + (k + 1) * slot;
+  a.qp = w.traj + k * slot;
+  a.qp_next = w.traj + (k + 1) * slot;
   a.n = n;
   a.npad = npad;
   a.split_len = c.split_len;
@@ -262,8 +256,8 @@ StepFwdArgs forward_step_args(Workspace& w, const StepConfig& c, int kind, int n
   a.lambda = lambda;
   a.a64 = w.a64;
   a.b64 = w.b64;
-  a.a4 = w.adj_a;  // buffer 0: read by the first reverse step
-  a.b4 = w.adj_b;
+  a.ab = w.adj;  // buffer 0: read by the first reverse step
+  a.kappa64 = sc.kappa;
   a.red_h = w.red_h;
   a.red_m = w.red_m;
   a.ticket = w.ticket;
@@ -276,16 +270,13 @@ StepFwdArgs forward_step_args(Workspace& w, const StepConfig& c, int kind, int n
 StepBwdArgs backward_step_args(Workspace& w, const StepConfig& c, int n, int T, int s, double sigma) {
   const int npad = round_up(n, kPad);
   const KernelScales sc = make_scales(sigma);
-  const size_t slot = static_cast<size_t>(w.cap_npad);
+  const size_t slot = w.slot();
   const int k = T - 1 - s;
   StepBwdArgs b;
   std::memset(&b, 0, sizeof(b));
-  b.q4 = w.traj_q + k * slot;
-  b.p4 = w.traj_p + k * slot;
-  b.a4 = w.adj_a + (s & 1) * slot;
-  b.b4 = w.adj_b + (s & 1) * slot;
-  b.a4_next = w.adj_a + ((s + 1) & 1) * slot;
-  b.b4_next = w.adj_b + ((s + 1) & 1) * slot;
+  b.qp = w.traj + k * slot;
+  b.ab = w.adj + (s & 1) * slot;
+  b.ab_next = w.adj + ((s + 1) & 1) * slot;
   b.n = n;
   b.npad = npad;
   b.split_len = c.split_len;
@@ -378,8 +369,7 @@ gs_status run_shoot(int kind, const gs_params* prm, const float* q0, const float
   pk.q64 = w->q64;
   pk.p64 = w->p64;
   pk.t64 = kind == 1 ? w->t64 : nullptr;
-  pk.q4 = w->traj_q;
-  pk.p4 = w->traj_p;
+  pk.qp = w->traj;
   pk.n = n;
   pk.kq = make_scales(prm->sigma).kq;
   pk.status = w->status;
@@ -440,12 +430,10 @@ gs_status run_step(int kind, int64_t N, double sigma, const float* q, const floa
     if ((s = stage_in(beta, w->in_t, n3, st, &db, &host)) != GS_OK) return s;
   }
   const KernelScales sc = make_scales(sigma);
-  GS_CUDA(launch_to_float4(dq, w->traj_q, n, npad, sc.kq, w->status, st));
-  GS_CUDA(launch_to_float4(dp, w->traj_p, n, npad, 1.0, w->status, st));
+  GS_CUDA(launch_to_records(dq, dp, w->traj, n, npad, sc.kq, 1.0, 0, w->status, st));
   if (kind == 0) {
     PairFwdArgs a;
-    a.q4 = w->traj_q;
-    a.p4 = w->traj_p;
+    a.qp = w->traj;
     a.part = w->part;
     a.npad = npad;
     a.split_len = c.split_len;
@@ -453,13 +441,10 @@ gs_status run_step(int kind, int64_t N, double sigma, const float* q, const floa
     a.status = w->status;
     GS_CUDA(launch_pair_forward(c, a, st, false));
   } else {
-    GS_CUDA(launch_to_float4(da, w->adj_a, n, npad, 1.0, w->status, st));
-    GS_CUDA(launch_to_float4(db, w->adj_b, n, npad, sc.kappa, w->status, st));
+    GS_CUDA(launch_to_records(da, db, w->adj, n, npad, 1.0, sc.kappa, 1, w->status, st));
     PairBwdArgs a;
-    a.q4 = w->traj_q;
-    a.p4 = w->traj_p;
-    a.a4 = w->adj_a;
-    a.b4 = w->adj_b;
+    a.qp = w->traj;
+    a.ab = w->adj;
     a.part = w->part;
     a.npad = npad;
     a.split_len = c.split_len;
@@ -563,26 +548,19 @@ gs_status time_pair_config(int kind_in, int64_t N, double sigma, const float* q,
     if ((s = stage_in(beta, w->in_t, n3, st, &db, &host)) != GS_OK) return s;
   }
   const KernelScales ks = make_scales(sigma);
-  GS_CUDA(launch_to_float4(dq, w->traj_q, n, npad, ks.kq, w->status, st));
-  GS_CUDA(launch_to_float4(dp, w->traj_p, n, npad, 1.0, w->status, st));
-  if (bwd) {
-    GS_CUDA(launch_to_float4(da, w->adj_a, n, npad, 1.0, w->status, st));
-    GS_CUDA(launch_to_float4(db, w->adj_b, n, npad, ks.kappa, w->status, st));
-  }
+  GS_CUDA(launch_to_records(dq, dp, w->traj, n, npad, ks.kq, 1.0, 0, w->status, st));
+  if (bwd) GS_CUDA(launch_to_records(da, db, w->adj, n, npad, 1.0, ks.kappa, 1, w->status, st));
   w->clean_n = -1;
   PairFwdArgs fa;
-  fa.q4 = w->traj_q;
-  fa.p4 = w->traj_p;
+  fa.qp = w->traj;
   fa.part = w->part;
   fa.npad = npad;
   fa.split_len = c.split_len;
   fa.kappa = static_cast<float>(ks.kappa);
   fa.status = w->status;
   PairBwdArgs ba;
-  ba.q4 = w->traj_q;
-  ba.p4 = w->traj_p;
-  ba.a4 = w->adj_a;
-  ba.b4 = w->adj_b;
+  ba.qp = w->traj;
+  ba.ab = w->adj;
   ba.part = w->part;
   ba.npad = npad;
   ba.split_len = c.split_len;

@@ -1,15 +1,19 @@
 // Internal interfaces between the gshoot kernels and the host engine.
 //
 // Device data layout (one workspace per device; Npad = N rounded up to a
-// multiple of kPad, padded landmarks stay exactly zero):
-//   traj_q[k]  float4[Npad]  kq * q^k (xyz, w = 0), the prescaled positions
-//   traj_p[k]  float4[Npad]  p^k (xyz, w = 0)
-//   adj_a[2]   float4[Npad]  alpha (adjoint of q), two buffers: a reverse step
-//   adj_b[2]   float4[Npad]  reads one and writes the other; b holds kappa*beta
-//   q64, p64, a64, b64       double[N*3], FP64 master state, (N,3) row-major
-//   part       Partial[S][Npad], per source split: six double-single sums
-// with kq = sqrt(log2(e) / 2) / sigma (so g = 2^-(|kq d|^2)),
-// s = 1/sigma^2 and kappa = s / kq.
+// multiple of kPad; padded landmarks stay exactly zero):
+//   traj[k]   QP pair records, Npad/2 x 3 float4: landmarks 2g and 2g+1
+//             interleaved per coordinate, positions prescaled and negated:
+//               {-q~x0, -q~x1, -q~y0, -q~y1} {-q~z0, -q~z1, px0, px1}
+//               {py0, py1, pz0, pz1}
+//   adj[2]    AB pair records, same shape, two buffers (a reverse step reads
+//             one and writes the other):
+//               {ax0, ax1, ay0, ay1} {az0, az1, -b~x0, -b~x1}
+//               {-b~y0, -b~y1, -b~z0, -b~z1}
+//   q64, p64, a64, b64   double[N*3], FP64 master state, (N,3) row-major
+//   part      Partial[S][Npad], per source split: six double-single sums
+// with q~ = kq q, b~ = kappa beta, kq = sqrt(log2(e) / 2) / sigma (so the
+// Gaussian is 2^-|q~_i - q~_j|^2), s = 1/sigma^2 and kappa = s / kq.
 #pragma once
 
 #include <cstdint>
@@ -26,6 +30,8 @@ enum : unsigned {
 
 constexpr int kPad = 64;      // landmark padding granule = source sub-block
 constexpr int kChunk = 256;   // sources staged in shared memory per bulk copy
+constexpr int kRecF4 = 3;     // float4 per pair record (two landmarks)
+constexpr int kRecBytes = 48;
 
 // Six double-single sums for one target and one source split:
 // forward  c[0..2] = Hp, c[3..5] = Hq
@@ -43,8 +49,7 @@ struct KernelScales {
 KernelScales make_scales(double sigma);
 
 struct PairFwdArgs {
-  const float4* q4;   // traj_q slot, Npad
-  const float4* p4;   // traj_p slot, Npad
+  const float4* qp;   // QP records of the state
   Partial* part;      // [S][Npad]
   int npad;
   int split_len;      // sources per split (multiple of kPad)
@@ -53,10 +58,8 @@ struct PairFwdArgs {
 };
 
 struct PairBwdArgs {
-  const float4* q4;
-  const float4* p4;
-  const float4* a4;   // alpha
-  const float4* b4;   // kappa * beta
+  const float4* qp;   // QP records of the state
+  const float4* ab;   // AB records of the adjoint
   Partial* part;
   int npad;
   int split_len;
@@ -103,10 +106,8 @@ struct StepConfig {
 };
 
 struct StepFwdArgs {
-  const float4* q4;    // traj_q[k]
-  const float4* p4;    // traj_p[k]
-  float4* q4_next;     // traj_q[k+1]
-  float4* p4_next;     // traj_p[k+1]
+  const float4* qp;    // traj[k]
+  float4* qp_next;     // traj[k+1]
   int n, npad, split_len;
   float kappa;
   double dt, kq;
@@ -121,8 +122,8 @@ struct StepFwdArgs {
   double lambda;
   double* a64;
   double* b64;
-  float4* a4;          // adjoint buffer the first reverse step reads
-  float4* b4;
+  float4* ab;          // adjoint buffer the first reverse step reads
+  double kappa64;
   double* red_h;       // per-CTA partial sums (grid-sized)
   double* red_m;
   unsigned* ticket;
@@ -132,12 +133,9 @@ struct StepFwdArgs {
 };
 
 struct StepBwdArgs {
-  const float4* q4;    // traj_q[k]
-  const float4* p4;    // traj_p[k]
-  const float4* a4;    // alpha of step k+1
-  const float4* b4;    // kappa * beta of step k+1
-  float4* a4_next;     // alpha of step k (the other buffer)
-  float4* b4_next;
+  const float4* qp;    // traj[k]
+  const float4* ab;    // adjoint of step k+1
+  float4* ab_next;     // adjoint of step k (the other buffer)
   int n, npad, split_len;
   float kq, kappa;
   double dt, kappa64;
@@ -168,8 +166,7 @@ struct PackArgs {
   double* q64;
   double* p64;
   double* t64;         // may be null
-  float4* q4;          // traj_q[0]
-  float4* p4;          // traj_p[0]
+  float4* qp;          // traj[0]
   int n;
   double kq;
   unsigned* status;
@@ -186,9 +183,10 @@ cudaError_t launch_unpack(const UnpackArgs& a, cudaStream_t st);
 // Hq, Hp straight from one split-partial set (step_forward entry point).
 cudaError_t launch_partials_to_out(const Partial* part, int splits, int n, int npad,
                                    float* out_a, float* out_b, cudaStream_t st);
-// (N,3) float32 -> prescaled float4 (scale * x), zero-padded to npad.
-cudaError_t launch_to_float4(const float* x, float4* x4, int n, int npad, double scale,
-                             unsigned* status, cudaStream_t st);
+// Two (N,3) float32 arrays -> pair records {-sa * a, sb * b} (QP: a = q,
+// b = p) or {sa * a, -sb * b} (AB: a = alpha, b = beta), zero-padded to npad.
+cudaError_t launch_to_records(const float* a, const float* b, float4* rec, int n, int npad, double sa, double sb,
+                              int ab_layout, unsigned* status, cudaStream_t st);
 
 int combine_threads();
 int combine_group();  // lanes per landmark in the combine kernels

@@ -30,13 +30,12 @@ constexpr int kMaxSplits = 8;
 constexpr int kMaxDevices = 64;
 
 constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
-constexpr size_t kOffQ4 = 0;
-constexpr size_t kOffP4 = align256(kOffQ4 + sizeof(float4) * kMaxN);
-constexpr size_t kOffPart = align256(kOffP4 + sizeof(float4) * kMaxN);
+constexpr size_t kOffQP = 0;
+constexpr size_t kOffPart = align256(kOffQP + sizeof(float4) * kRecF4 * (kMaxN / 2));
 constexpr size_t kOffStatus = align256(kOffPart + sizeof(Partial) * kMaxSplits * kMaxN);
-constexpr size_t kScratchBytes = align256(kOffStatus + 4 * sizeof(unsigned));  // about 3.4 MB
+constexpr size_t kScratchBytes = align256(kOffStatus + 4 * sizeof(unsigned));  // about 3.3 MB
 
-// The scratch for every call on a device.  It holds the float4 copies of q
+// The scratch for every call on a device.  It holds the pair records of q
 // and p, the split partials, and the device status word.  The pointer that
 // host code passes to kernels comes from cudaGetSymbolAddress, because the
 // array's name in host code does not give a device address.
@@ -118,8 +117,7 @@ extern "C" gs_status step_forward_noalloc(int64_t N, double sigma, const float* 
   int num_sms = 0;
   gs_status s = scratch_for_current_device(&base, &num_sms);
   if (s != GS_OK) return s;
-  float4* q4 = reinterpret_cast<float4*>(base + kOffQ4);
-  float4* p4 = reinterpret_cast<float4*>(base + kOffP4);
+  float4* qp = reinterpret_cast<float4*>(base + kOffQP);
   Partial* part = reinterpret_cast<Partial*>(base + kOffPart);
   unsigned* status = reinterpret_cast<unsigned*>(base + kOffStatus);
 
@@ -132,15 +130,13 @@ extern "C" gs_status step_forward_noalloc(int64_t N, double sigma, const float* 
     return GS_EINVAL;
   }
   const KernelScales sc = make_scales(sigma);
-  // The status word keeps the previous call's value: clear it.  The float4
-  // copies (padding included) and the partials are fully rewritten below.
+  // The status word keeps the previous call's value: clear it.  The pair
+  // records (padding included) and the partials are fully rewritten below.
   cudaError_t e = cudaMemsetAsync(status, 0, 4 * sizeof(unsigned), st);
   if (e != cudaSuccess) return cuda_fail(e);
-  if ((e = launch_to_float4(q, q4, n, npad, sc.kq, status, st)) != cudaSuccess) return cuda_fail(e);
-  if ((e = launch_to_float4(p, p4, n, npad, 1.0, status, st)) != cudaSuccess) return cuda_fail(e);
+  if ((e = launch_to_records(q, p, qp, n, npad, sc.kq, 1.0, 0, status, st)) != cudaSuccess) return cuda_fail(e);
   PairFwdArgs a;
-  a.q4 = q4;
-  a.p4 = p4;
+  a.qp = qp;
   a.part = part;
   a.npad = npad;
   a.split_len = cfg.split_len;

@@ -9,6 +9,8 @@
 //    buffer, and each buffer is guarded by an mbarrier.
 //  * Every warp reads the same source at the same time, so the shared-memory
 //    read is a broadcast.
+//  * Sources are stored as pair records of two landmarks, and paired FP32
+//    instructions work on both at once (pair_tile.cuh).
 //  * Each thread accumulates plain FP32 over a sub-block of at most 64
 //    sources, then folds the sub-block sum into a Kahan (sum, compensation)
 //    pair.  This is the compensated accumulation that the paper's accuracy
@@ -33,7 +35,7 @@ namespace gs {
 // sources of split y; it writes one double-single Partial per target.
 template <int NT, int R>
 __global__ void __launch_bounds__(NT) k_pair_forward(PairFwdArgs a) {
-  __shared__ __align__(128) StageBuf<2> st;
+  __shared__ __align__(128) StageBuf<1> st;
   __shared__ __align__(8) uint64_t full[2];
   const int j0 = blockIdx.y * a.split_len;
   const int j1 = min(j0 + a.split_len, a.npad);
@@ -43,9 +45,9 @@ __global__ void __launch_bounds__(NT) k_pair_forward(PairFwdArgs a) {
   pdl_launch_dependents();
   const int base = blockIdx.x * (NT * R) + threadIdx.x;
   FwdTile<R> tile;
-  tile.load(a.q4, a.p4, base, NT, a.npad);
-  const float4* src[2] = {a.q4, a.p4};
-  if (!stream_sources<2>(st, full, src, j0, j1, tile, a.status)) return;
+  tile.load(a.qp, base, NT, a.npad);
+  const float4* src[1] = {a.qp};
+  if (!stream_sources<1>(st, full, src, j0, j1, tile, a.status)) return;
   Partial* out = a.part + static_cast<size_t>(blockIdx.y) * a.npad;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -62,7 +64,7 @@ __global__ void __launch_bounds__(NT) k_pair_forward(PairFwdArgs a) {
 
 template <int NT, int R>
 __global__ void __launch_bounds__(NT) k_pair_backward(PairBwdArgs a) {
-  __shared__ __align__(128) StageBuf<4> st;
+  __shared__ __align__(128) StageBuf<2> st;
   __shared__ __align__(8) uint64_t full[2];
   const int j0 = blockIdx.y * a.split_len;
   const int j1 = min(j0 + a.split_len, a.npad);
@@ -72,9 +74,9 @@ __global__ void __launch_bounds__(NT) k_pair_backward(PairBwdArgs a) {
   pdl_launch_dependents();
   const int base = blockIdx.x * (NT * R) + threadIdx.x;
   BwdTile<R> tile;
-  tile.load(a.q4, a.p4, a.a4, a.b4, base, NT, a.npad);
-  const float4* src[4] = {a.q4, a.p4, a.a4, a.b4};
-  if (!stream_sources<4>(st, full, src, j0, j1, tile, a.status)) return;
+  tile.load(a.qp, a.ab, base, NT, a.npad);
+  const float4* src[2] = {a.qp, a.ab};
+  if (!stream_sources<2>(st, full, src, j0, j1, tile, a.status)) return;
   Partial* out = a.part + static_cast<size_t>(blockIdx.y) * a.npad;
 #pragma unroll
   for (int r = 0; r < R; ++r) {

@@ -3,12 +3,19 @@
 // Both the split-partial kernels (pair_kernels.cu) and the fused step kernels
 // (step_kernels.cu) are built from these pieces.
 //
-// A thread holds R targets in registers.  The targets of one CTA are
-// tid + r*NT, r < R.  For each source staged in shared memory, every thread
-// updates all of its R targets.  All threads of a warp read the same source
-// at the same time, so the shared-memory load is a broadcast.  Sums are
-// plain FP32 over a sub-block of at most kSub sources, then folded into a
-// Kahan (sum, compensation) pair.
+// Packed arithmetic.  Sources sit in memory as pair records: two landmarks
+// interleaved per coordinate (layout in gs_internal.h).  The inner loop uses
+// the sm_100+ paired FP32 instructions (__fadd2_rn, __fmul2_rn, __ffma2_rn).
+// Each instruction applies one target to two sources, which halves the issue
+// slots spent on FP32 work.  Positions are stored negated, so q_i - q_j is a
+// single paired add.  The Gaussian is one MUFU ex2 per pair, on prescaled
+// coordinates.
+//
+// A thread holds R targets in registers; the targets of a CTA are
+// base + r*NT, r < R.  The whole warp reads the same source record, so the
+// shared-memory load is a broadcast.  Sums are plain FP32 over a sub-block of
+// at most kSub sources, then the two halves of each paired accumulator are
+// added and folded into a Kahan (sum, compensation) pair.
 #pragma once
 
 #include "gs_device.cuh"
@@ -19,11 +26,12 @@ namespace gs {
 constexpr int kSub = 64;    // sources per plain-FP32 sub-block before a Kahan fold
 constexpr int kUnroll = 8;  // split lengths are multiples of this
 
-// Two chunk buffers for NA source arrays.  The mbarriers live outside, so
-// this memory can be reused once the last chunk has been consumed.
+// Two chunk buffers for NA record arrays (kChunk sources = kChunk/2 records
+// of 3 float4 each).  The mbarriers live outside, so the memory can be reused
+// once the last chunk has been consumed.
 template <int NA>
 struct StageBuf {
-  float4 buf[2][NA][kChunk];
+  float4 buf[2][NA][kRecF4 * kChunk / 2];
 };
 
 __device__ __forceinline__ void stage_init(uint64_t* full) {
@@ -32,17 +40,18 @@ __device__ __forceinline__ void stage_init(uint64_t* full) {
   fence_mbar_init();
 }
 
-// Issue the bulk copies of chunk c (NA arrays) into buffer c & 1.
+// Issue the bulk copies of chunk c (NA record arrays) into buffer c & 1.
+// Source offsets and lengths are even, so records are copied whole.
 template <int NA>
 __device__ __forceinline__ void issue_chunk(StageBuf<NA>& st, uint64_t* full, const float4* const* src, int j0,
                                             int j1, int c) {
   const int off = j0 + c * kChunk;
   const int len = min(kChunk, j1 - off);
-  const unsigned bytes = static_cast<unsigned>(len) * sizeof(float4);
+  const unsigned bytes = static_cast<unsigned>(len) * (kRecBytes / 2);
   uint64_t* bar = &full[c & 1];
   mbar_arrive_expect_tx(bar, NA * bytes);
 #pragma unroll
-  for (int a = 0; a < NA; ++a) bulk_g2s(&st.buf[c & 1][a][0], src[a] + off, bytes, bar);
+  for (int a = 0; a < NA; ++a) bulk_g2s(&st.buf[c & 1][a][0], src[a] + (off / 2) * kRecF4, bytes, bar);
 }
 
 // Stream sources [j0, j1) through the double buffer and feed each chunk to
@@ -91,25 +100,44 @@ __device__ bool stream_sources(StageBuf<NA>& st, uint64_t* full, const float4* c
   return true;
 }
 
+__device__ __forceinline__ float2 dup(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+
+// Gaussian of two pairs at once from their squared prescaled distances.
+__device__ __forceinline__ float2 gauss2(float2 r2) {
+  return make_float2(ex2_approx(-r2.x), ex2_approx(-r2.y));
+}
+
+// Coordinate k (0..2) of landmark i from a pair-record array; field f selects
+// the first (0) or second (1) quantity of the record.
+__device__ __forceinline__ float rec_get(const float4* rec, int i, int f, int k) {
+  const float* r = reinterpret_cast<const float*>(rec + (i >> 1) * kRecF4);
+  return __ldcg(r + 6 * f + 2 * k + (i & 1));
+}
+
 // ---------------------------------------------------------------- StepForward tile
 // Per target i:  Hp_i = sum_j g_ij p_j  and  G~_i = sum_j c_ij g_ij (q~_i - q~_j),
 // with Hq_i = -kappa G~_i.
 template <int R>
 struct FwdTile {
-  float qx[R], qy[R], qz[R], px[R], py[R], pz[R];
+  float2 qx[R], qy[R], qz[R], px[R], py[R], pz[R];  // target, duplicated
   float sF[R][3], cF[R][3], sG[R][3], cG[R][3];
 
-  __device__ __forceinline__ void load(const float4* q4, const float4* p4, int base, int stride, int npad) {
+  __device__ __forceinline__ void load(const float4* qp, int base, int stride, int npad) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int i = base + r * stride;
-      float4 qi = make_float4(0.f, 0.f, 0.f, 0.f), pi = qi;
+      float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       if (i < npad) {
-        qi = q4[i];
-        pi = p4[i];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          v[k] = -rec_get(qp, i, 0, k);
+          v[3 + k] = rec_get(qp, i, 1, k);
+        }
       }
-      qx[r] = qi.x; qy[r] = qi.y; qz[r] = qi.z;
-      px[r] = pi.x; py[r] = pi.y; pz[r] = pi.z;
+      qx[r] = dup(v[0]); qy[r] = dup(v[1]); qz[r] = dup(v[2]);
+      px[r] = dup(v[3]); py[r] = dup(v[4]); pz[r] = dup(v[5]);
 #pragma unroll
       for (int k = 0; k < 3; ++k) sF[r][k] = cF[r][k] = sG[r][k] = cG[r][k] = 0.f;
     }
@@ -117,32 +145,39 @@ struct FwdTile {
 
   __device__ __forceinline__ void consume(const float4* const* bufs, int len) {
     const float4* Q = bufs[0];
-    const float4* P = bufs[1];
     for (int sb = 0; sb < len; sb += kSub) {
       const int sl = min(kSub, len - sb);
-      float aF[R][3], aG[R][3];
+      float2 aF[R][3], aG[R][3];
 #pragma unroll
       for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) aF[r][k] = aG[r][k] = 0.f;
+        for (int k = 0; k < 3; ++k) aF[r][k] = aG[r][k] = make_float2(0.f, 0.f);
       for (int jj = 0; jj < sl; jj += kUnroll) {
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-          const float4 qj = Q[sb + jj + u];
-          const float4 pj = P[sb + jj + u];
+        for (int u = 0; u < kUnroll / 2; ++u) {
+          const float4* rec = Q + ((sb + jj) / 2 + u) * kRecF4;
+          const float4 A = rec[0], B = rec[1], C = rec[2];
+          const float2 nqx = lo2(A), nqy = hi2(A), nqz = lo2(B);
+          const float2 pjx = hi2(B), pjy = lo2(C), pjz = hi2(C);
 #pragma unroll
           for (int r = 0; r < R; ++r) {
-            const float dx = qx[r] - qj.x, dy = qy[r] - qj.y, dz = qz[r] - qj.z;
-            const float nr = fmaf(-dz, dz, fmaf(-dy, dy, -dx * dx));
-            const float g = ex2_approx(nr);
-            const float cc = fmaf(pz[r], pj.z, fmaf(py[r], pj.y, px[r] * pj.x));
-            const float w = g * cc;
-            aF[r][0] = fmaf(g, pj.x, aF[r][0]);
-            aF[r][1] = fmaf(g, pj.y, aF[r][1]);
-            aF[r][2] = fmaf(g, pj.z, aF[r][2]);
-            aG[r][0] = fmaf(w, dx, aG[r][0]);
-            aG[r][1] = fmaf(w, dy, aG[r][1]);
-            aG[r][2] = fmaf(w, dz, aG[r][2]);
+            const float2 dx = __fadd2_rn(qx[r], nqx);
+            const float2 dy = __fadd2_rn(qy[r], nqy);
+            const float2 dz = __fadd2_rn(qz[r], nqz);
+            float2 r2 = __fmul2_rn(dx, dx);
+            r2 = __ffma2_rn(dy, dy, r2);
+            r2 = __ffma2_rn(dz, dz, r2);
+            const float2 g = gauss2(r2);
+            float2 cc = __fmul2_rn(px[r], pjx);
+            cc = __ffma2_rn(py[r], pjy, cc);
+            cc = __ffma2_rn(pz[r], pjz, cc);
+            const float2 w = __fmul2_rn(g, cc);
+            aF[r][0] = __ffma2_rn(g, pjx, aF[r][0]);
+            aF[r][1] = __ffma2_rn(g, pjy, aF[r][1]);
+            aF[r][2] = __ffma2_rn(g, pjz, aF[r][2]);
+            aG[r][0] = __ffma2_rn(w, dx, aG[r][0]);
+            aG[r][1] = __ffma2_rn(w, dy, aG[r][1]);
+            aG[r][2] = __ffma2_rn(w, dz, aG[r][2]);
           }
         }
       }
@@ -150,8 +185,8 @@ struct FwdTile {
       for (int r = 0; r < R; ++r)
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-          kahan_add(sF[r][k], cF[r][k], aF[r][k]);
-          kahan_add(sG[r][k], cG[r][k], aG[r][k]);
+          kahan_add(sF[r][k], cF[r][k], __fadd_rn(aF[r][k].x, aF[r][k].y));
+          kahan_add(sG[r][k], cG[r][k], __fadd_rn(aG[r][k].x, aG[r][k].y));
         }
     }
   }
@@ -167,32 +202,37 @@ struct FwdTile {
 };
 
 // ---------------------------------------------------------------- StepBackward tile
-// Sources carry q~ = kq q, p, alpha and b~ = kappa beta.  Per pair:
+// Sources carry q~ = kq q, p (QP records) and alpha, b~ = kappa beta (AB
+// records).  Per pair:
 //   d~ = q~_i - q~_j, g = 2^-|d~|^2, c = p_i.p_j, e~ = b~_i - b~_j,
 //   t = e~.d~ (= s e.d), u = alpha_i.p_j + alpha_j.p_i, h = u + c t,
 //   A1 += g c e~,  A2 += g h d~,  B += g (alpha_j + t p_j);
 // dalpha = kq A1 - kappa A2 and dbeta = B.
 template <int R>
 struct BwdTile {
-  float qx[R], qy[R], qz[R], px[R], py[R], pz[R], ax[R], ay[R], az[R], bx[R], by[R], bz[R];
+  float2 qx[R], qy[R], qz[R], px[R], py[R], pz[R], ax[R], ay[R], az[R], bx[R], by[R], bz[R];
   float s1[R][3], c1[R][3], s2[R][3], c2[R][3], sB[R][3], cB[R][3];
 
-  __device__ __forceinline__ void load(const float4* q4, const float4* p4, const float4* a4, const float4* b4,
-                                       int base, int stride, int npad) {
+  __device__ __forceinline__ void load(const float4* qp, const float4* ab, int base, int stride, int npad) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int i = base + r * stride;
-      float4 qi = make_float4(0.f, 0.f, 0.f, 0.f), pi = qi, ai = qi, bi = qi;
+      float v[12];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) v[k] = 0.f;
       if (i < npad) {
-        qi = q4[i];
-        pi = p4[i];
-        ai = a4[i];
-        bi = b4[i];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          v[k] = -rec_get(qp, i, 0, k);
+          v[3 + k] = rec_get(qp, i, 1, k);
+          v[6 + k] = rec_get(ab, i, 0, k);
+          v[9 + k] = -rec_get(ab, i, 1, k);
+        }
       }
-      qx[r] = qi.x; qy[r] = qi.y; qz[r] = qi.z;
-      px[r] = pi.x; py[r] = pi.y; pz[r] = pi.z;
-      ax[r] = ai.x; ay[r] = ai.y; az[r] = ai.z;
-      bx[r] = bi.x; by[r] = bi.y; bz[r] = bi.z;
+      qx[r] = dup(v[0]); qy[r] = dup(v[1]); qz[r] = dup(v[2]);
+      px[r] = dup(v[3]); py[r] = dup(v[4]); pz[r] = dup(v[5]);
+      ax[r] = dup(v[6]); ay[r] = dup(v[7]); az[r] = dup(v[8]);
+      bx[r] = dup(v[9]); by[r] = dup(v[10]); bz[r] = dup(v[11]);
 #pragma unroll
       for (int k = 0; k < 3; ++k) s1[r][k] = c1[r][k] = s2[r][k] = c2[r][k] = sB[r][k] = cB[r][k] = 0.f;
     }
@@ -200,49 +240,60 @@ struct BwdTile {
 
   __device__ __forceinline__ void consume(const float4* const* bufs, int len) {
     const float4* Q = bufs[0];
-    const float4* P = bufs[1];
-    const float4* A = bufs[2];
-    const float4* B = bufs[3];
+    const float4* Ab = bufs[1];
     for (int sb = 0; sb < len; sb += kSub) {
       const int sl = min(kSub, len - sb);
-      float a1[R][3], a2[R][3], bb[R][3];
+      float2 a1[R][3], a2[R][3], bb[R][3];
 #pragma unroll
       for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) a1[r][k] = a2[r][k] = bb[r][k] = 0.f;
+        for (int k = 0; k < 3; ++k) a1[r][k] = a2[r][k] = bb[r][k] = make_float2(0.f, 0.f);
       for (int jj = 0; jj < sl; jj += kUnroll) {
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-          const float4 qj = Q[sb + jj + u];
-          const float4 pj = P[sb + jj + u];
-          const float4 aj = A[sb + jj + u];
-          const float4 bj = B[sb + jj + u];
+        for (int u = 0; u < kUnroll / 2; ++u) {
+          const int ri = ((sb + jj) / 2 + u) * kRecF4;
+          const float4 A = Q[ri], B = Q[ri + 1], C = Q[ri + 2];
+          const float4 D = Ab[ri], E = Ab[ri + 1], F = Ab[ri + 2];
+          const float2 nqx = lo2(A), nqy = hi2(A), nqz = lo2(B);
+          const float2 pjx = hi2(B), pjy = lo2(C), pjz = hi2(C);
+          const float2 ajx = lo2(D), ajy = hi2(D), ajz = lo2(E);
+          const float2 nbx = hi2(E), nby = lo2(F), nbz = hi2(F);
 #pragma unroll
           for (int r = 0; r < R; ++r) {
-            const float dx = qx[r] - qj.x, dy = qy[r] - qj.y, dz = qz[r] - qj.z;
-            const float nr = fmaf(-dz, dz, fmaf(-dy, dy, -dx * dx));
-            const float g = ex2_approx(nr);
-            const float cc = fmaf(pz[r], pj.z, fmaf(py[r], pj.y, px[r] * pj.x));
-            const float ex = bx[r] - bj.x, ey = by[r] - bj.y, ez = bz[r] - bj.z;
-            const float t = fmaf(ez, dz, fmaf(ey, dy, ex * dx));
-            float uu = ax[r] * pj.x;
-            uu = fmaf(ay[r], pj.y, uu);
-            uu = fmaf(az[r], pj.z, uu);
-            uu = fmaf(aj.x, px[r], uu);
-            uu = fmaf(aj.y, py[r], uu);
-            uu = fmaf(aj.z, pz[r], uu);
-            const float h = fmaf(cc, t, uu);
-            const float gc = g * cc;
-            const float gh = g * h;
-            a1[r][0] = fmaf(gc, ex, a1[r][0]);
-            a1[r][1] = fmaf(gc, ey, a1[r][1]);
-            a1[r][2] = fmaf(gc, ez, a1[r][2]);
-            a2[r][0] = fmaf(gh, dx, a2[r][0]);
-            a2[r][1] = fmaf(gh, dy, a2[r][1]);
-            a2[r][2] = fmaf(gh, dz, a2[r][2]);
-            bb[r][0] = fmaf(g, fmaf(t, pj.x, aj.x), bb[r][0]);
-            bb[r][1] = fmaf(g, fmaf(t, pj.y, aj.y), bb[r][1]);
-            bb[r][2] = fmaf(g, fmaf(t, pj.z, aj.z), bb[r][2]);
+            const float2 dx = __fadd2_rn(qx[r], nqx);
+            const float2 dy = __fadd2_rn(qy[r], nqy);
+            const float2 dz = __fadd2_rn(qz[r], nqz);
+            float2 r2 = __fmul2_rn(dx, dx);
+            r2 = __ffma2_rn(dy, dy, r2);
+            r2 = __ffma2_rn(dz, dz, r2);
+            const float2 g = gauss2(r2);
+            float2 cc = __fmul2_rn(px[r], pjx);
+            cc = __ffma2_rn(py[r], pjy, cc);
+            cc = __ffma2_rn(pz[r], pjz, cc);
+            const float2 ex = __fadd2_rn(bx[r], nbx);
+            const float2 ey = __fadd2_rn(by[r], nby);
+            const float2 ez = __fadd2_rn(bz[r], nbz);
+            float2 t = __fmul2_rn(ex, dx);
+            t = __ffma2_rn(ey, dy, t);
+            t = __ffma2_rn(ez, dz, t);
+            float2 uu = __fmul2_rn(ax[r], pjx);
+            uu = __ffma2_rn(ay[r], pjy, uu);
+            uu = __ffma2_rn(az[r], pjz, uu);
+            uu = __ffma2_rn(ajx, px[r], uu);
+            uu = __ffma2_rn(ajy, py[r], uu);
+            uu = __ffma2_rn(ajz, pz[r], uu);
+            const float2 h = __ffma2_rn(cc, t, uu);
+            const float2 gc = __fmul2_rn(g, cc);
+            const float2 gh = __fmul2_rn(g, h);
+            a1[r][0] = __ffma2_rn(gc, ex, a1[r][0]);
+            a1[r][1] = __ffma2_rn(gc, ey, a1[r][1]);
+            a1[r][2] = __ffma2_rn(gc, ez, a1[r][2]);
+            a2[r][0] = __ffma2_rn(gh, dx, a2[r][0]);
+            a2[r][1] = __ffma2_rn(gh, dy, a2[r][1]);
+            a2[r][2] = __ffma2_rn(gh, dz, a2[r][2]);
+            bb[r][0] = __ffma2_rn(g, __ffma2_rn(t, pjx, ajx), bb[r][0]);
+            bb[r][1] = __ffma2_rn(g, __ffma2_rn(t, pjy, ajy), bb[r][1]);
+            bb[r][2] = __ffma2_rn(g, __ffma2_rn(t, pjz, ajz), bb[r][2]);
           }
         }
       }
@@ -250,9 +301,9 @@ struct BwdTile {
       for (int r = 0; r < R; ++r)
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-          kahan_add(s1[r][k], c1[r][k], a1[r][k]);
-          kahan_add(s2[r][k], c2[r][k], a2[r][k]);
-          kahan_add(sB[r][k], cB[r][k], bb[r][k]);
+          kahan_add(s1[r][k], c1[r][k], __fadd_rn(a1[r][k].x, a1[r][k].y));
+          kahan_add(s2[r][k], c2[r][k], __fadd_rn(a2[r][k].x, a2[r][k].y));
+          kahan_add(sB[r][k], cB[r][k], __fadd_rn(bb[r][k].x, bb[r][k].y));
         }
     }
   }

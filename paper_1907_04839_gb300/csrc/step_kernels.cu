@@ -62,7 +62,7 @@ template <int NT, int R>
 __global__ void __launch_bounds__(NT) k_step_forward(StepFwdArgs a) {
   constexpr int M = NT * R;
   union Smem {
-    StageBuf<2> st;
+    StageBuf<1> st;
     float4 red[M][3];  // Hp (hi,lo) x3 then Hq (hi,lo) x3 per target
   };
   __shared__ __align__(128) Smem sm;
@@ -81,9 +81,9 @@ __global__ void __launch_bounds__(NT) k_step_forward(StepFwdArgs a) {
 
   const int base = tile * M + threadIdx.x;
   FwdTile<R> t;
-  t.load(a.q4, a.p4, base, NT, a.npad);
-  const float4* src[2] = {a.q4, a.p4};
-  stream_sources<2>(sm.st, full, src, j0, j1, t, a.status);  // ends with a CTA barrier
+  t.load(a.qp, base, NT, a.npad);
+  const float4* src[1] = {a.qp};
+  stream_sources<1>(sm.st, full, src, j0, j1, t, a.status);  // ends with a CTA barrier
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     ds v[6];
@@ -134,14 +134,16 @@ __global__ void __launch_bounds__(NT) k_step_forward(StepFwdArgs a) {
     }
     a.q64[tt] = q;
     a.p64[tt] = p;
-    reinterpret_cast<float*>(a.q4_next)[4 * i + k] = (float)(a.kq * q);
-    reinterpret_cast<float*>(a.p4_next)[4 * i + k] = (float)p;
+    float* qn = reinterpret_cast<float*>(a.qp_next + (i >> 1) * kRecF4) + 2 * k + (i & 1);
+    qn[0] = -(float)(a.kq * q);
+    qn[6] = (float)p;
     if (a.last && a.with_loss) {
       const double al = 2.0 * a.lambda * r;
       a.a64[tt] = al;
       a.b64[tt] = 0.0;
-      reinterpret_cast<float*>(a.a4)[4 * i + k] = (float)al;
-      reinterpret_cast<float*>(a.b4)[4 * i + k] = 0.f;
+      float* an = reinterpret_cast<float*>(a.ab + (i >> 1) * kRecF4) + 2 * k + (i & 1);
+      an[0] = (float)al;
+      an[6] = 0.f;
     }
   }
   cluster_sync();  // peers may still be reading this CTA's partials
@@ -162,7 +164,7 @@ template <int NT, int R>
 __global__ void __launch_bounds__(NT) k_step_backward(StepBwdArgs a) {
   constexpr int M = NT * R;
   union Smem {
-    StageBuf<4> st;
+    StageBuf<2> st;
     float4 red[M][3];  // dalpha (hi,lo) x3 then dbeta (hi,lo) x3 per target
   };
   __shared__ __align__(128) Smem sm;
@@ -179,9 +181,9 @@ __global__ void __launch_bounds__(NT) k_step_backward(StepBwdArgs a) {
 
   const int base = tile * M + threadIdx.x;
   BwdTile<R> t;
-  t.load(a.q4, a.p4, a.a4, a.b4, base, NT, a.npad);
-  const float4* src[4] = {a.q4, a.p4, a.a4, a.b4};
-  stream_sources<4>(sm.st, full, src, j0, j1, t, a.status);
+  t.load(a.qp, a.ab, base, NT, a.npad);
+  const float4* src[2] = {a.qp, a.ab};
+  stream_sources<2>(sm.st, full, src, j0, j1, t, a.status);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     ds v[6];
@@ -219,8 +221,9 @@ __global__ void __launch_bounds__(NT) k_step_backward(StepBwdArgs a) {
     if (!isfinite(al) || !isfinite(be)) atomicOr(a.status, kErrNonFinite);
     a.a64[tt] = al;
     a.b64[tt] = be;
-    reinterpret_cast<float*>(a.a4_next)[4 * i + k] = (float)al;
-    reinterpret_cast<float*>(a.b4_next)[4 * i + k] = (float)(a.kappa64 * be);
+    float* an = reinterpret_cast<float*>(a.ab_next + (i >> 1) * kRecF4) + 2 * k + (i & 1);
+    an[0] = (float)al;
+    an[6] = -(float)(a.kappa64 * be);
     if (a.first) {
       if (a.grad_p0) a.grad_p0[tt] = (float)(be + a.hp0[tt]);
       if (a.grad_q0) a.grad_q0[tt] = (float)(al + a.hq0[tt]);

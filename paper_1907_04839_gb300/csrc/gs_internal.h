@@ -29,7 +29,8 @@ enum : unsigned {
 };
 
 constexpr int kPad = 64;      // landmark padding granule = source sub-block
-constexpr int kChunk = 256;   // sources staged in shared memory per bulk copy
+constexpr int kChunk = 128;   // sources staged in shared memory per bulk copy
+constexpr int kStages = 4;    // chunk buffers in flight per CTA
 constexpr int kRecF4 = 3;     // float4 per pair record (two landmarks)
 constexpr int kRecBytes = 48;
 

@@ -36,10 +36,10 @@ namespace gs {
 template <int NT, int R>
 __global__ void __launch_bounds__(NT) k_pair_forward(PairFwdArgs a) {
   __shared__ __align__(128) StageBuf<1> st;
-  __shared__ __align__(8) uint64_t full[2];
+  __shared__ __align__(8) Pipe pp;
   const int j0 = blockIdx.y * a.split_len;
   const int j1 = min(j0 + a.split_len, a.npad);
-  if (threadIdx.x == 0) stage_init(full);
+  if (threadIdx.x == 0) pipe_init(pp, NT / 32);
   __syncthreads();
   pdl_wait();  // the previous step's state must be complete
   pdl_launch_dependents();
@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(NT) k_pair_forward(PairFwdArgs a) {
   FwdTile<R> tile;
   tile.load(a.qp, base, NT, a.npad);
   const float4* src[1] = {a.qp};
-  if (!stream_sources<1>(st, full, src, j0, j1, tile, a.status)) return;
+  if (!stream_sources<1>(st, pp, src, j0, j1, tile, a.status)) return;
   Partial* out = a.part + static_cast<size_t>(blockIdx.y) * a.npad;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -65,10 +65,10 @@ __global__ void __launch_bounds__(NT) k_pair_forward(PairFwdArgs a) {
 template <int NT, int R>
 __global__ void __launch_bounds__(NT) k_pair_backward(PairBwdArgs a) {
   __shared__ __align__(128) StageBuf<2> st;
-  __shared__ __align__(8) uint64_t full[2];
+  __shared__ __align__(8) Pipe pp;
   const int j0 = blockIdx.y * a.split_len;
   const int j1 = min(j0 + a.split_len, a.npad);
-  if (threadIdx.x == 0) stage_init(full);
+  if (threadIdx.x == 0) pipe_init(pp, NT / 32);
   __syncthreads();
   pdl_wait();
   pdl_launch_dependents();
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(NT) k_pair_backward(PairBwdArgs a) {
   BwdTile<R> tile;
   tile.load(a.qp, a.ab, base, NT, a.npad);
   const float4* src[2] = {a.qp, a.ab};
-  if (!stream_sources<2>(st, full, src, j0, j1, tile, a.status)) return;
+  if (!stream_sources<2>(st, pp, src, j0, j1, tile, a.status)) return;
   Partial* out = a.part + static_cast<size_t>(blockIdx.y) * a.npad;
 #pragma unroll
   for (int r = 0; r < R; ++r) {

@@ -26,73 +26,98 @@ namespace gs {
 constexpr int kSub = 64;    // sources per plain-FP32 sub-block before a Kahan fold
 constexpr int kUnroll = 8;  // split lengths are multiples of this
 
-// Two chunk buffers for NA record arrays (kChunk sources = kChunk/2 records
-// of 3 float4 each).  The mbarriers live outside, so the memory can be reused
-// once the last chunk has been consumed.
+// kStages chunk buffers for NA record arrays (kChunk sources = kChunk/2
+// records of 3 float4 each).  The mbarriers live outside (struct Pipe), so
+// this memory can be reused once the last chunk has been consumed.
 template <int NA>
 struct StageBuf {
-  float4 buf[2][NA][kRecF4 * kChunk / 2];
+  float4 buf[kStages][NA][kRecF4 * kChunk / 2];
 };
 
-__device__ __forceinline__ void stage_init(uint64_t* full) {
-  mbar_init(&full[0], 1);
-  mbar_init(&full[1], 1);
+// full[s]: the bulk copies of the chunk in stage s have landed (transaction
+// count).  empty[s]: every warp has finished reading stage s (one arrival per
+// warp).  abort: set by a thread whose wait expired.
+struct Pipe {
+  uint64_t full[kStages];
+  uint64_t empty[kStages];
+  int abort;
+};
+
+__device__ __forceinline__ void pipe_init(Pipe& p, int warps) {
+#pragma unroll
+  for (int s = 0; s < kStages; ++s) {
+    mbar_init(&p.full[s], 1);
+    mbar_init(&p.empty[s], warps);
+  }
+  p.abort = 0;
   fence_mbar_init();
 }
 
-// Issue the bulk copies of chunk c (NA record arrays) into buffer c & 1.
+// Issue the bulk copies of chunk c (NA record arrays) into stage c % kStages.
 // Source offsets and lengths are even, so records are copied whole.
 template <int NA>
-__device__ __forceinline__ void issue_chunk(StageBuf<NA>& st, uint64_t* full, const float4* const* src, int j0,
-                                            int j1, int c) {
+__device__ __forceinline__ void issue_chunk(StageBuf<NA>& st, Pipe& pp, const float4* const* src, int j0, int j1,
+                                            int c) {
   const int off = j0 + c * kChunk;
   const int len = min(kChunk, j1 - off);
   const unsigned bytes = static_cast<unsigned>(len) * (kRecBytes / 2);
-  uint64_t* bar = &full[c & 1];
+  const int s = c % kStages;
+  uint64_t* bar = &pp.full[s];
   mbar_arrive_expect_tx(bar, NA * bytes);
 #pragma unroll
-  for (int a = 0; a < NA; ++a) bulk_g2s(&st.buf[c & 1][a][0], src[a] + (off / 2) * kRecF4, bytes, bar);
+  for (int a = 0; a < NA; ++a) bulk_g2s(&st.buf[s][a][0], src[a] + (off / 2) * kRecF4, bytes, bar);
 }
 
-// Stream sources [j0, j1) through the double buffer and feed each chunk to
-// tile.consume(buffers, len).  The whole CTA calls this.  Returns false in
-// every thread if a wait expired; the expiry is recorded in *status, and
-// every copy still in flight has been waited for (bounded) before return.
+// Stream sources [j0, j1) through the stage ring and feed each chunk to
+// tile.consume(buffers, len).  The whole CTA calls this; thread 0 issues the
+// copies.  Warps move on to the next chunk as soon as it has landed: a warp
+// releases a stage through empty[s], and thread 0 refills a stage only after
+// every warp has released it.  Returns false in every thread if a wait
+// expired; the expiry is recorded in *status, and every copy still in flight
+// has been waited for (bounded) before return.  Ends with a CTA barrier.
 template <int NA, class Tile>
-__device__ bool stream_sources(StageBuf<NA>& st, uint64_t* full, const float4* const* src, int j0, int j1,
-                               Tile& tile, unsigned* status) {
+__device__ bool stream_sources(StageBuf<NA>& st, Pipe& pp, const float4* const* src, int j0, int j1, Tile& tile,
+                               unsigned* status) {
   const int tid = threadIdx.x;
-  const int nch = (j1 - j0 + kChunk - 1) / kChunk;
+  const int nch = j1 > j0 ? (j1 - j0 + kChunk - 1) / kChunk : 0;
   int issued = 0;
-  if (tid == 0 && nch > 0) {
-    issue_chunk<NA>(st, full, src, j0, j1, 0);
-    issued = 1;
-    if (nch > 1) {
-      issue_chunk<NA>(st, full, src, j0, j1, 1);
-      issued = 2;
-    }
+  if (tid == 0) {
+    for (; issued < nch && issued < kStages; ++issued) issue_chunk<NA>(st, pp, src, j0, j1, issued);
   }
-  int c = 0;
-  for (; c < nch; ++c) {
-    const int b = c & 1;
-    const bool ok = mbar_wait(&full[b], (c >> 1) & 1);
-    const int len = min(kChunk, j1 - (j0 + c * kChunk));
+  volatile int* abort = &pp.abort;
+  for (int c = 0; c < nch; ++c) {
+    const int s = c % kStages;
+    if (*abort) break;
+    if (!mbar_wait(&pp.full[s], (c / kStages) & 1)) {
+      *abort = 1;
+      break;
+    }
     const float4* bufs[NA];
 #pragma unroll
-    for (int a = 0; a < NA; ++a) bufs[a] = st.buf[b][a];
-    tile.consume(bufs, len);
-    // Every thread is done with buffer b; a uniform vote on the wait result.
-    if (__syncthreads_or(!ok)) break;
-    if (tid == 0 && c + 2 < nch) {
-      fence_proxy_async_smem();
-      issue_chunk<NA>(st, full, src, j0, j1, c + 2);
-      issued = c + 3;
+    for (int a = 0; a < NA; ++a) bufs[a] = st.buf[s][a];
+    tile.consume(bufs, min(kChunk, j1 - (j0 + c * kChunk)));
+    __syncwarp();
+    if ((tid & 31) == 0) mbar_arrive(&pp.empty[s]);
+    if (tid == 0 && c + kStages < nch) {
+      // Refill stage s with chunk c + kStages once every warp has released it.
+      if (mbar_wait(&pp.empty[s], (c / kStages) & 1)) {
+        fence_proxy_async_smem();
+        issue_chunk<NA>(st, pp, src, j0, j1, c + kStages);
+        issued = c + kStages + 1;
+      } else {
+        *abort = 1;
+      }
     }
   }
-  if (c < nch) {
+  __syncthreads();
+  if (*abort) {
     if (tid == 0) {
       atomicOr(status, kErrTimeout);
-      for (int d = c; d < issued; ++d) (void)mbar_wait(&full[d & 1], (d >> 1) & 1);
+      // Let every copy that was issued land before the CTA reuses or leaves
+      // this memory: the last kStages chunks issued are the only ones that
+      // can still be in flight.
+      for (int d = max(0, issued - kStages); d < issued; ++d)
+        (void)mbar_wait(&pp.full[d % kStages], (d / kStages) & 1);
     }
     __syncthreads();
     return false;

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(NT) k_step_forward(StepFwdArgs a) {
     float4 red[M][3];  // Hp (hi,lo) x3 then Hq (hi,lo) x3 per target
   };
   __shared__ __align__(128) Smem sm;
-  __shared__ __align__(8) uint64_t full[2];
+  __shared__ __align__(8) Pipe pp;
   __shared__ double shred[NT / 32];
   __shared__ int am_last;
 
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(NT) k_step_forward(StepFwdArgs a) {
   const int tile = blockIdx.y;
   const int j0 = min(static_cast<int>(rank) * a.split_len, a.npad);
   const int j1 = min(j0 + a.split_len, a.npad);
-  if (threadIdx.x == 0) stage_init(full);
+  if (threadIdx.x == 0) pipe_init(pp, NT / 32);
   __syncthreads();
   pdl_wait();  // the previous step's state must be complete
   pdl_launch_dependents();
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(NT) k_step_forward(StepFwdArgs a) {
   FwdTile<R> t;
   t.load(a.qp, base, NT, a.npad);
   const float4* src[1] = {a.qp};
-  stream_sources<1>(sm.st, full, src, j0, j1, t, a.status);  // ends with a CTA barrier
+  stream_sources<1>(sm.st, pp, src, j0, j1, t, a.status);  // ends with a CTA barrier
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     ds v[6];
@@ -168,13 +168,13 @@ __global__ void __launch_bounds__(NT) k_step_backward(StepBwdArgs a) {
     float4 red[M][3];  // dalpha (hi,lo) x3 then dbeta (hi,lo) x3 per target
   };
   __shared__ __align__(128) Smem sm;
-  __shared__ __align__(8) uint64_t full[2];
+  __shared__ __align__(8) Pipe pp;
 
   const unsigned rank = cluster_rank(), C = cluster_size();
   const int tile = blockIdx.y;
   const int j0 = min(static_cast<int>(rank) * a.split_len, a.npad);
   const int j1 = min(j0 + a.split_len, a.npad);
-  if (threadIdx.x == 0) stage_init(full);
+  if (threadIdx.x == 0) pipe_init(pp, NT / 32);
   __syncthreads();
   pdl_wait();
   pdl_launch_dependents();
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(NT) k_step_backward(StepBwdArgs a) {
   BwdTile<R> t;
   t.load(a.qp, a.ab, base, NT, a.npad);
   const float4* src[2] = {a.qp, a.ab};
-  stream_sources<2>(sm.st, full, src, j0, j1, t, a.status);
+  stream_sources<2>(sm.st, pp, src, j0, j1, t, a.status);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     ds v[6];

@@ -57,6 +57,13 @@ def _load():
             lib.orc_shoot_gradient.restype = cd
             lib.orc_velocity.argtypes = [i64, _D, i64, _D, _D, cd, _D]
             _I = ctypes.POINTER(ctypes.c_int64)
+            IP = ctypes.POINTER(ctypes.c_int)
+            lib.orc_lbfgs_quadratic.argtypes = [i64, _D, _D, _D, cint, cint, cd, _D, IP, IP]
+            lib.orc_lbfgs_quadratic.restype = cint
+            lib.orc_lbfgs_rosenbrock.argtypes = [i64, _D, cint, cint, cd, _D, IP, IP]
+            lib.orc_lbfgs_rosenbrock.restype = cint
+            lib.orc_register.argtypes = [i64, cint, cd, cd, cint, cint, cd, _D, _D, _D, _D, IP, IP, _D]
+            lib.orc_register.restype = cint
             lib.orc_step_forward_rows.argtypes = [i64, cd, _D, _D, i64, _I, _D, _D]
             lib.orc_step_backward_rows.argtypes = [i64, cd, _D, _D, _D, _D, i64, _I, _D, _D]
             _lib = lib
@@ -169,3 +176,43 @@ def velocity(x, q, p, sigma):
     v = np.empty_like(x)
     _load().orc_velocity(x.shape[0], _p(x), q.shape[0], _p(q), _p(p), float(sigma), _p(v))
     return v
+
+
+def _lbfgs_out(status, f, iters, evals, x, trace=None):
+    out = dict(status=int(status), f=float(f.value), iters=int(iters.value), evals=int(evals.value), x=x)
+    if trace is not None:
+        out["trace"] = trace[: out["iters"] + 1].copy()
+    return out
+
+
+def lbfgs_quadratic(A, b, x0, m=10, max_iter=200, grad_tol=1e-12):
+    """L-BFGS on 1/2 x^T A x - b^T x (pin helper)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64).ravel()
+    x = np.ascontiguousarray(x0, dtype=np.float64).ravel().copy()
+    f = ctypes.c_double(0); it = ctypes.c_int(0); ev = ctypes.c_int(0)
+    st = _load().orc_lbfgs_quadratic(x.size, _p(A), _p(b), _p(x), int(m), int(max_iter), float(grad_tol),
+                                     ctypes.byref(f), ctypes.byref(it), ctypes.byref(ev))
+    return _lbfgs_out(st, f, it, ev, x)
+
+
+def lbfgs_rosenbrock(x0, m=10, max_iter=500, grad_tol=1e-10):
+    """L-BFGS on the extended Rosenbrock function (pin helper)."""
+    x = np.ascontiguousarray(x0, dtype=np.float64).ravel().copy()
+    f = ctypes.c_double(0); it = ctypes.c_int(0); ev = ctypes.c_int(0)
+    st = _load().orc_lbfgs_rosenbrock(x.size, _p(x), int(m), int(max_iter), float(grad_tol),
+                                      ctypes.byref(f), ctypes.byref(it), ctypes.byref(ev))
+    return _lbfgs_out(st, f, it, ev, x)
+
+
+def register(q0, target, T, sigma, lam, p0=None, m=10, max_iter=50, grad_tol=1e-5):
+    """Algorithm 1 (lines 18-19): L-BFGS over p0 of the Eq. 3 loss.  Returns
+    dict(status, f, iters, evals, x=p0 (N,3), trace=loss per iterate)."""
+    q0 = _in(q0); n = q0.shape[0]; target = _in(target, n)
+    x = np.zeros((n, 3)) if p0 is None else _in(p0, n).copy()
+    trace = np.zeros(max_iter + 1)
+    f = ctypes.c_double(0); it = ctypes.c_int(0); ev = ctypes.c_int(0)
+    st = _load().orc_register(n, int(T), float(sigma), float(lam), int(m), int(max_iter), float(grad_tol),
+                              _p(q0), _p(target), _p(x), ctypes.byref(f), ctypes.byref(it), ctypes.byref(ev),
+                              _p(trace))
+    return _lbfgs_out(st, f, it, ev, x, trace)

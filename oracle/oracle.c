@@ -322,3 +322,239 @@ void orc_velocity(int64_t m, const double* x, int64_t n, const double* q, const 
         for (int k = 0; k < 3; ++k) v[3 * i + k] = acc[k];
     }
 }
+
+/* ------------------------------------------------------------------ L-BFGS
+ * Limited-memory BFGS over x (Section 2.1 uses VNL's L-BFGS; its settings are
+ * not stated, so this follows the reading written down for both paths):
+ *   - memory m pairs (s_k, y_k), two-loop recursion, initial scaling
+ *     gamma = s.y / y.y of the newest pair;
+ *   - first direction -g with a first trial step 1/||g0||, later trials 1;
+ *   - strong-Wolfe line search (c1 = 1e-4, c2 = 0.9) by bracketing and zoom
+ *     with safeguarded cubic interpolation, at most 20 evaluations;
+ *   - a pair is stored only if s.y > 1e-12 s.s^(1/2) y.y^(1/2);
+ *   - stop when ||g|| <= grad_tol ||g0|| or after max_iter iterations.
+ * fg(ctx, x, g) returns f(x) and writes its gradient. */
+typedef double (*orc_fg_fn)(void* ctx, const double* x, double* g);
+
+static double vdot(int64_t n, const double* a, const double* b) {
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+    return s;
+}
+
+/* Minimiser of the cubic through (a, fa, da) and (b, fb, db); NAN if none. */
+static double cubic_min(double a, double fa, double da, double b, double fb, double db) {
+    const double d1 = da + db - 3.0 * (fa - fb) / (a - b);
+    const double disc = d1 * d1 - da * db;
+    if (!(disc >= 0.0)) return NAN;
+    const double d2 = (b > a ? 1.0 : -1.0) * sqrt(disc);
+    const double den = db - da + 2.0 * d2;
+    if (den == 0.0) return NAN;
+    return b - (b - a) * (db + d2 - d1) / den;
+}
+
+typedef struct {
+    int64_t n;
+    orc_fg_fn fg;
+    void* ctx;
+    const double* x;
+    const double* d;
+    double* xt;
+    double* gt;
+    int evals;
+} ls_ctx;
+
+static double ls_eval(ls_ctx* c, double a, double* dphi) {
+    for (int64_t i = 0; i < c->n; ++i) c->xt[i] = c->x[i] + a * c->d[i];
+    const double f = c->fg(c->ctx, c->xt, c->gt);
+    c->evals++;
+    *dphi = vdot(c->n, c->gt, c->d);
+    return f;
+}
+
+/* Strong-Wolfe line search; returns the accepted step (xt, gt hold its point
+ * and gradient, *f_out its value) or 0 on failure. */
+static double line_search(ls_ctx* c, double f0, double dphi0, double a1, double* f_out) {
+    const double c1 = 1e-4, c2 = 0.9;
+    const int max_evals = 20;
+    double a_prev = 0.0, f_prev = f0, d_prev = dphi0;
+    double a = a1;
+    const int start = c->evals;
+    for (int it = 0; c->evals - start < max_evals; ++it) {
+        double da;
+        const double fa = ls_eval(c, a, &da);
+        int zoom = 0;
+        double lo = 0, flo = 0, dlo = 0, hi = 0, fhi = 0, dhi = 0;
+        if (!(fa <= f0 + c1 * a * dphi0) || (it > 0 && fa >= f_prev)) {
+            zoom = 1; lo = a_prev; flo = f_prev; dlo = d_prev; hi = a; fhi = fa; dhi = da;
+        } else if (fabs(da) <= -c2 * dphi0) {
+            *f_out = fa;
+            return a;
+        } else if (da >= 0.0) {
+            zoom = 1; lo = a; flo = fa; dlo = da; hi = a_prev; fhi = f_prev; dhi = d_prev;
+        }
+        if (zoom) {
+            while (c->evals - start < max_evals) {
+                double aj = cubic_min(lo, flo, dlo, hi, fhi, dhi);
+                const double w = hi - lo;
+                const double lo_b = (w > 0 ? lo + 0.1 * w : hi - 0.1 * w);
+                const double hi_b = (w > 0 ? hi - 0.1 * w : lo + 0.1 * w);
+                const double mn = lo_b < hi_b ? lo_b : hi_b, mx = lo_b < hi_b ? hi_b : lo_b;
+                if (!(aj >= mn && aj <= mx)) aj = 0.5 * (lo + hi);
+                double dj;
+                const double fj = ls_eval(c, aj, &dj);
+                if (!(fj <= f0 + c1 * aj * dphi0) || fj >= flo) {
+                    hi = aj; fhi = fj; dhi = dj;
+                } else {
+                    if (fabs(dj) <= -c2 * dphi0) {
+                        *f_out = fj;
+                        return aj;
+                    }
+                    if (dj * (hi - lo) >= 0.0) { hi = lo; fhi = flo; dhi = dlo; }
+                    lo = aj; flo = fj; dlo = dj;
+                }
+            }
+            return 0.0;
+        }
+        a_prev = a; f_prev = fa; d_prev = da;
+        a = 2.0 * a;
+    }
+    return 0.0;
+}
+
+/* Returns 0 when the gradient tolerance was met, 1 at max_iter, -1 when a line
+ * search failed.  trace (optional, max_iter+1 entries) receives f per iterate. */
+int orc_lbfgs(int64_t n, double* x, orc_fg_fn fg, void* ctx, int m, int max_iter, double grad_tol,
+              double* f_out, int* iters_out, int* evals_out, double* trace) {
+    double* g = malloc(n * sizeof(double));
+    double* d = malloc(n * sizeof(double));
+    double* xt = malloc(n * sizeof(double));
+    double* gt = malloc(n * sizeof(double));
+    double* S = malloc((size_t)m * n * sizeof(double));
+    double* Y = malloc((size_t)m * n * sizeof(double));
+    double* rho = malloc(m * sizeof(double));
+    double* alpha = malloc(m * sizeof(double));
+    int stored = 0, head = 0, status = 1, it = 0;
+    ls_ctx c = {n, fg, ctx, x, d, xt, gt, 0};
+    double f = fg(ctx, x, g);
+    c.evals = 1;
+    const double g0 = sqrt(vdot(n, g, g));
+    if (trace) trace[0] = f;
+    if (g0 == 0.0) status = 0;
+    for (it = 0; status == 1 && it < max_iter; ++it) {
+        /* two-loop recursion: d = -H g */
+        for (int64_t i = 0; i < n; ++i) d[i] = g[i];
+        for (int k = 0; k < stored; ++k) {
+            const int j = (head - 1 - k + m) % m;
+            alpha[j] = rho[j] * vdot(n, S + (size_t)j * n, d);
+            for (int64_t i = 0; i < n; ++i) d[i] -= alpha[j] * Y[(size_t)j * n + i];
+        }
+        if (stored > 0) {
+            const int j = (head - 1 + m) % m;
+            const double gamma = vdot(n, S + (size_t)j * n, Y + (size_t)j * n) /
+                                 vdot(n, Y + (size_t)j * n, Y + (size_t)j * n);
+            for (int64_t i = 0; i < n; ++i) d[i] *= gamma;
+        }
+        for (int k = stored - 1; k >= 0; --k) {
+            const int j = (head - 1 - k + m) % m;
+            const double b = rho[j] * vdot(n, Y + (size_t)j * n, d);
+            for (int64_t i = 0; i < n; ++i) d[i] += (alpha[j] - b) * S[(size_t)j * n + i];
+        }
+        for (int64_t i = 0; i < n; ++i) d[i] = -d[i];
+        double dphi0 = vdot(n, g, d);
+        if (!(dphi0 < 0.0)) { /* not a descent direction: restart from -g */
+            for (int64_t i = 0; i < n; ++i) d[i] = -g[i];
+            dphi0 = -vdot(n, g, g);
+            stored = 0;
+        }
+        const double a1 = (it == 0) ? 1.0 / g0 : 1.0;
+        double fn = 0.0;
+        const double a = line_search(&c, f, dphi0, a1, &fn);
+        if (a == 0.0) { status = -1; break; }
+        /* s = a d, y = gt - g */
+        double* s = S + (size_t)head * n;
+        double* y = Y + (size_t)head * n;
+        for (int64_t i = 0; i < n; ++i) {
+            s[i] = a * d[i];
+            y[i] = gt[i] - g[i];
+        }
+        const double sy = vdot(n, s, y);
+        if (sy > 1e-12 * sqrt(vdot(n, s, s) * vdot(n, y, y))) {
+            rho[head] = 1.0 / sy;
+            head = (head + 1) % m;
+            if (stored < m) ++stored;
+        }
+        memcpy(x, xt, n * sizeof(double));
+        memcpy(g, gt, n * sizeof(double));
+        f = fn;
+        if (trace) trace[it + 1] = f;
+        if (sqrt(vdot(n, g, g)) <= grad_tol * g0) { status = 0; ++it; break; }
+    }
+    if (f_out) *f_out = f;
+    if (iters_out) *iters_out = it;
+    if (evals_out) *evals_out = c.evals;
+    free(g); free(d); free(xt); free(gt); free(S); free(Y); free(rho); free(alpha);
+    return status;
+}
+
+/* Pin helpers: a convex quadratic 1/2 x^T A x - b^T x (A dense, n x n) and the
+ * extended Rosenbrock function. */
+typedef struct { int64_t n; const double* A; const double* b; } quad_ctx;
+
+static double quad_fg(void* p, const double* x, double* g) {
+    const quad_ctx* q = p;
+    double f = 0.0;
+    for (int64_t i = 0; i < q->n; ++i) {
+        double ax = 0.0;
+        for (int64_t j = 0; j < q->n; ++j) ax += q->A[i * q->n + j] * x[j];
+        g[i] = ax - q->b[i];
+        f += 0.5 * x[i] * ax - q->b[i] * x[i];
+    }
+    return f;
+}
+
+int orc_lbfgs_quadratic(int64_t n, const double* A, const double* b, double* x, int m, int max_iter,
+                        double grad_tol, double* f_out, int* iters, int* evals) {
+    quad_ctx q = {n, A, b};
+    return orc_lbfgs(n, x, quad_fg, &q, m, max_iter, grad_tol, f_out, iters, evals, NULL);
+}
+
+static double rosen_fg(void* p, const double* x, double* g) {
+    const int64_t n = *(const int64_t*)p;
+    double f = 0.0;
+    for (int64_t i = 0; i < n; ++i) g[i] = 0.0;
+    for (int64_t i = 0; i + 1 < n; ++i) {
+        const double a = x[i + 1] - x[i] * x[i], b = 1.0 - x[i];
+        f += 100.0 * a * a + b * b;
+        g[i] += -400.0 * x[i] * a - 2.0 * b;
+        g[i + 1] += 200.0 * a;
+    }
+    return f;
+}
+
+int orc_lbfgs_rosenbrock(int64_t n, double* x, int m, int max_iter, double grad_tol, double* f_out, int* iters,
+                         int* evals) {
+    return orc_lbfgs(n, x, rosen_fg, &n, m, max_iter, grad_tol, f_out, iters, evals, NULL);
+}
+
+/* register: minimise the Eq. 3 loss over p0 from p0_inout (Algorithm 1,
+ * lines 18-19).  Returns the orc_lbfgs status. */
+typedef struct {
+    int64_t n;
+    int T;
+    double sigma, lambda;
+    const double* q0;
+    const double* target;
+} reg_ctx;
+
+static double reg_fg(void* p, const double* x, double* g) {
+    const reg_ctx* r = p;
+    return orc_shoot_gradient(r->n, r->T, r->sigma, r->lambda, r->q0, x, r->target, g, NULL, NULL, NULL, NULL);
+}
+
+int orc_register(int64_t n, int T, double sigma, double lambda, int m, int max_iter, double grad_tol,
+                 const double* q0, const double* target, double* p0, double* loss, int* iters, int* evals,
+                 double* trace) {
+    reg_ctx r = {n, T, sigma, lambda, q0, target};
+    return orc_lbfgs(3 * n, p0, reg_fg, &r, m, max_iter, grad_tol, loss, iters, evals, trace);
+}

@@ -315,3 +315,41 @@ def test_golden_regression_fixture():
     assert rel(r["grad_p0"], vals["grad_p0"].reshape(-1, 3)) < 1e-12
     assert rel(r["grad_q0"], vals["grad_q0"].reshape(-1, 3)) < 1e-12
     assert rel(r["q1"], vals["q1"].reshape(-1, 3)) < 1e-13
+
+
+# ---------------------------------------------------------------- L-BFGS
+
+def test_lbfgs_solves_convex_quadratic():
+    # The minimiser of 1/2 x^T A x - b^T x is A^{-1} b (numpy solve).
+    rng = np.random.default_rng(40)
+    n = 30
+    M = rng.normal(size=(n, n))
+    A = M @ M.T + n * np.eye(n)
+    b = rng.normal(size=n)
+    # ||g|| <= 3e-9 ||g0||: much further and the line search meets the FP64
+    # resolution of f for this problem
+    r = oracle.lbfgs_quadratic(A, b, np.zeros(n), m=10, max_iter=200, grad_tol=3e-9)
+    assert r["status"] == 0
+    assert rel(r["x"], np.linalg.solve(A, b)) < 1e-8
+
+
+def test_lbfgs_rosenbrock_reaches_ones():
+    x0 = np.array([-1.2, 1.0] * 5)
+    r = oracle.lbfgs_rosenbrock(x0, m=10, max_iter=1000, grad_tol=1e-9)
+    assert r["status"] == 0
+    assert np.abs(r["x"] - 1.0).max() < 1e-6
+
+
+def test_register_decreases_loss_and_first_step_follows_gradient():
+    pr = ls.ellipsoid_pair(64, seed=4, n_bumps=4)
+    T, sigma, lam = 5, 0.25, 10.0
+    r = oracle.register(pr.q0, pr.target, T, sigma, lam, max_iter=15, grad_tol=1e-8)
+    tr = r["trace"]
+    assert np.all(np.diff(tr) < 0)  # Armijo: every accepted step lowers the loss
+    assert tr[-1] < 0.2 * tr[0]
+    assert abs(oracle.loss(pr.q0, r["x"], pr.target, T, sigma, lam) - r["f"]) < 1e-12 * r["f"]
+    # the first iterate lies on the ray p0 = -a g0 of the closed-form gradient
+    r1 = oracle.register(pr.q0, pr.target, T, sigma, lam, max_iter=1, grad_tol=0.0)
+    g0 = 2 * lam * dense_K(pr.q0, pr.q0, sigma) @ (pr.q0 - pr.target)
+    a = -np.sum(r1["x"] * g0) / np.sum(g0 * g0)
+    assert a > 0 and rel(r1["x"], -a * g0) < 1e-12

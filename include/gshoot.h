@@ -113,6 +113,40 @@ gs_status shoot_gradient(const gs_params* prm, const float* q0, const float* p0,
                          const float* target, double* loss,
                          float* grad_p0, float* grad_q0, void* stream);
 
+/* Result of register_landmarks (all fields written when the pointer is set). */
+typedef struct gs_register_info {
+    double loss;        /* loss of Eq. 3 at the returned p0 */
+    double grad_norm0;  /* ||dL/dp0|| at the initial p0 */
+    double grad_norm;   /* ||dL/dp0|| at the returned p0 */
+    double avg_dist;    /* AverageDist(q(1), target) of Section 3.1 */
+    double max_dist;    /* MaxDist(q(1), target) of Section 3.1 */
+    int32_t iters;      /* L-BFGS iterations taken */
+    int32_t evals;      /* gradient evaluations (ComputeGradient calls) */
+    int32_t status;     /* 0: ||g|| <= grad_tol ||g0||; 1: max_iter reached;
+                           2: the line search found no step meeting the
+                              Wolfe conditions (rounding-noise floor) */
+    int32_t reserved;
+} gs_register_info;
+
+/*
+ * register_landmarks — Algorithm 1, lines 18-19: L-BFGS over the initial
+ * momentum p0 of the loss L(p0) = H(p0, q0) + lambda ||q(1) - target||^2
+ * (Eq. 3), each function evaluation being one ComputeGradient.  Settings
+ * (the paper used VNL's L-BFGS without stating them): memory prm->lbfgs_m
+ * (1..64), two-loop recursion with s.y / y.y scaling, first step -g scaled to
+ * 1/||g0||, strong-Wolfe line search (c1 = 1e-4, c2 = 0.9, at most 20
+ * evaluations), stop when ||g|| <= prm->grad_tol ||g0|| or after
+ * prm->max_iter iterations.  Vectors are FP64 on the device.
+ * In: prm (N, T, sigma, lambda, lbfgs_m, max_iter, grad_tol), q0, target,
+ *     p0_inout = starting momenta (zeros for the default start).
+ * Out: p0_inout = final momenta; *info (NULL to skip).
+ * Returns GS_OK when the gradient tolerance was met (or info is NULL), and
+ * GS_NOT_CONVERGED (> 0, outputs valid) when it stopped at max_iter or at the
+ * noise floor (info->status).  Synchronises `stream`.
+ */
+gs_status register_landmarks(const gs_params* prm, const float* q0, const float* target,
+                             float* p0_inout, gs_register_info* info, void* stream);
+
 /*
  * gs_time_pair_kernels — diagnostics (no counterpart in the paper): the
  * average device time of one launch of each pair-sum kernel, StepForward and

@@ -16,10 +16,10 @@ import ctypes
 
 import numpy as np
 
-from ._lib import EXPORTS, GShootError, GsParams, check, load
+from ._lib import EXPORTS, GShootError, GsParams, GsRegisterInfo, check, load
 
 __all__ = [
-    "step_forward", "step_backward", "shoot_forward", "shoot_gradient",
+    "step_forward", "step_backward", "shoot_forward", "shoot_gradient", "register",
     "release_workspace", "version", "GShootError", "GsParams", "EXPORTS",
 ]
 
@@ -132,6 +132,29 @@ def shoot_gradient(q0, p0, target, T, sigma, lam, ckpt_every=0):
     loss = ctypes.c_double(0.0)
     check(load().shoot_gradient(ctypes.byref(prm), pq, pp, pt, ctypes.byref(loss), og, oq, m.stream))
     return loss.value, gp, gq
+
+
+def register(q0, target, T, sigma, lam, p0=None, m=10, max_iter=100, grad_tol=1e-5):
+    """Algorithm 1 (lines 18-19): L-BFGS over p0 of the Eq. 3 loss.  Returns
+    (p0, info) with info a dict (loss, grad_norm0, grad_norm, avg_dist,
+    max_dist, iters, evals, status)."""
+    m_ = _Marshal(q0)
+    pq, pt = m_.inp(q0, "q0"), m_.inp(target, "target")
+    if p0 is None:
+        p0 = np.zeros((m_.n, 3), np.float32) if not m_.device else m_.torch.zeros(
+            (m_.n, 3), dtype=m_.torch.float32, device=m_.dev)
+    if m_.device:
+        pout = p0.detach().to(device=m_.dev, dtype=m_.torch.float32).clone().contiguous()
+        pp = ctypes.c_void_p(pout.data_ptr())
+    else:
+        pout = np.array(p0.detach().cpu().numpy() if hasattr(p0, "detach") else p0, dtype=np.float32, copy=True)
+        pp = ctypes.c_void_p(pout.ctypes.data)
+    if tuple(pout.shape) != (m_.n, 3):
+        raise ValueError("p0: expected shape (%d, 3)" % m_.n)
+    prm = _params(m_.n, T, sigma, lam, 0, m, max_iter, grad_tol)
+    info = GsRegisterInfo()
+    check(load().register_landmarks(ctypes.byref(prm), pq, pt, pp, ctypes.byref(info), m_.stream))
+    return pout, info.as_dict()
 
 
 def release_workspace() -> None:

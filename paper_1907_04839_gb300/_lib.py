@@ -21,7 +21,7 @@ GS_STATUS = {
 
 # Every symbol the header declares; tests check the library exports them all.
 EXPORTS = [
-    "step_forward", "step_backward", "shoot_forward", "shoot_gradient",
+    "step_forward", "step_backward", "shoot_forward", "shoot_gradient", "register_landmarks",
     "gs_time_pair_kernels", "gs_time_pair_config", "gs_set_step_config", "step_forward_noalloc",
     "gs_last_error",
     "gs_release_workspace",
@@ -43,6 +43,24 @@ class GsParams(ctypes.Structure):
     ]
 
 
+class GsRegisterInfo(ctypes.Structure):
+    """Mirror of ``gs_register_info`` in include/gshoot.h."""
+    _fields_ = [
+        ("loss", ctypes.c_double),
+        ("grad_norm0", ctypes.c_double),
+        ("grad_norm", ctypes.c_double),
+        ("avg_dist", ctypes.c_double),
+        ("max_dist", ctypes.c_double),
+        ("iters", ctypes.c_int32),
+        ("evals", ctypes.c_int32),
+        ("status", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 class GShootError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__("%s (%d): %s" % (GS_STATUS.get(status, "?"), status, msg))
@@ -57,12 +75,14 @@ def _declare(lib):
     lib.step_backward.argtypes = [i64, cd, fp, fp, fp, fp, fp, fp, vp]
     lib.shoot_forward.argtypes = [P, fp, fp, fp, fp, dp, vp]
     lib.shoot_gradient.argtypes = [P, fp, fp, fp, dp, fp, fp, vp]
+    lib.register_landmarks.argtypes = [P, fp, fp, fp, ctypes.POINTER(GsRegisterInfo), vp]
     lib.gs_time_pair_kernels.argtypes = [P, fp, fp, fp, i32, dp, dp, ctypes.c_void_p, vp]
     lib.step_forward_noalloc.argtypes = [i64, cd, fp, fp, fp, fp, vp]
     lib.gs_set_step_config.argtypes = [i32, i32, i32, i32]
     lib.gs_time_pair_config.argtypes = [i32, i64, cd, fp, fp, fp, fp, i32, i32, i32, i32, dp,
                                         ctypes.c_void_p, vp]
-    for name in ("step_forward", "step_backward", "shoot_forward", "shoot_gradient", "gs_time_pair_kernels",
+    for name in ("step_forward", "step_backward", "shoot_forward", "shoot_gradient", "register_landmarks",
+                 "gs_time_pair_kernels",
                  "step_forward_noalloc", "gs_time_pair_config", "gs_set_step_config"):
         getattr(lib, name).restype = ctypes.c_int
     lib.gs_last_error.restype = ctypes.c_char_p

@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(kThreads) k_pack(PackArgs a) {
   if (t >= 3 * a.n) return;
   const int i = t / 3, k = t - 3 * i;
   const float q = a.q[t];
-  const float p = a.p ? a.p[t] : 0.f;
+  const double p = a.p64_in ? a.p64_in[t] : (a.p ? (double)a.p[t] : 0.0);
   const float tg = a.tgt ? a.tgt[t] : 0.f;
   if (!isfinite(q) || !isfinite(p) || !isfinite(tg)) atomicOr(a.status, kErrNonFinite);
   a.q64[t] = q;
@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(kThreads) k_pack(PackArgs a) {
   if (a.t64) a.t64[t] = tg;
   float* r = reinterpret_cast<float*>(a.qp + (i >> 1) * kRecF4) + 2 * k + (i & 1);
   r[0] = -(float)(a.kq * (double)q);
-  r[6] = p;
+  r[6] = (float)p;
 }
 
 // Sum the split partials of landmark i over a group of kGroup lanes: lane l

@@ -22,74 +22,21 @@
 #include <tuple>
 #include <vector>
 
-#include "gs_internal.h"
-#include "../../include/gshoot.h"
+#include "engine.h"
 
 namespace gs {
 
 namespace {
-
 thread_local std::string g_err;
 std::mutex g_mu;
+}  // namespace
 
 gs_status fail(gs_status st, const std::string& msg) {
   g_err = msg;
   return st;
 }
 
-#define GS_CUDA(call)                                                                      \
-  do {                                                                                     \
-    cudaError_t e_ = (call);                                                               \
-    if (e_ != cudaSuccess)                                                                 \
-      return fail(e_ == cudaErrorMemoryAllocation ? GS_ENOMEM : GS_ECUDA,                  \
-                  std::string(#call) + ": " + cudaGetErrorString(e_));                     \
-  } while (0)
-
-int round_up(long long x, int m) { return static_cast<int>((x + m - 1) / m * m); }
-
-struct GraphKey {
-  int kind;  // 0 forward only, 1 gradient
-  int n, T;
-  double sigma, lambda;
-  bool operator<(const GraphKey& o) const {
-    return std::tie(kind, n, T, sigma, lambda) < std::tie(o.kind, o.n, o.T, o.sigma, o.lambda);
-  }
-};
-
-struct Workspace {
-  int device = -1;
-  int num_sms = 0;
-  // capacities
-  int cap_npad = 0, cap_T = 0, cap_splits = 0;
-  int cap_red = 0;
-  std::vector<void*> allocs;
-  float4* traj = nullptr;  // (cap_T + 1) slots of QP pair records
-  float4* adj = nullptr;   // 2 slots of AB pair records: reverse steps alternate
-  size_t slot() const { return static_cast<size_t>(kRecF4) * (cap_npad / 2); }  // float4 per slot
-  double *q64 = nullptr, *p64 = nullptr, *a64 = nullptr, *b64 = nullptr, *t64 = nullptr;
-  double *hp0 = nullptr, *hq0 = nullptr;
-  Partial* part = nullptr;   // cap_splits * cap_npad
-  float *in_q = nullptr, *in_p = nullptr, *in_t = nullptr, *in_a = nullptr;
-  float *out_a = nullptr, *out_b = nullptr;
-  double *red_h = nullptr, *red_m = nullptr, *scalars = nullptr;
-  unsigned *ticket = nullptr, *status = nullptr;
-  // The trajectory and adjoint float4 arrays hold zero padding for this N.
-  int clean_n = -1;
-  cudaStream_t capture_stream = nullptr;
-  std::map<GraphKey, cudaGraphExec_t> graphs;
-
-  void drop_graphs() {
-    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
-    graphs.clear();
-  }
-  void free_all() {
-    drop_graphs();
-    for (void* p : allocs) cudaFree(p);
-    allocs.clear();
-    cap_npad = cap_T = cap_splits = cap_red = 0;
-    clean_n = -1;
-  }
-};
+std::mutex& engine_mutex() { return g_mu; }
 
 std::map<int, Workspace*> g_ws;
 
@@ -139,6 +86,7 @@ gs_status reserve(Workspace& w, int npad, int T, int splits) {
   GS_CUDA(dalloc(w, &w.t64, n3));
   GS_CUDA(dalloc(w, &w.hp0, n3));
   GS_CUDA(dalloc(w, &w.hq0, n3));
+  GS_CUDA(dalloc(w, &w.gp64, n3));
   GS_CUDA(dalloc(w, &w.part, static_cast<size_t>(cs) * cn));
   GS_CUDA(dalloc(w, &w.in_q, n3));
   GS_CUDA(dalloc(w, &w.in_p, n3));
@@ -291,6 +239,7 @@ StepBwdArgs backward_step_args(Workspace& w, const StepConfig& c, int n, int T, 
   b.hq0 = w.hq0;
   b.grad_p0 = w.out_a;
   b.grad_q0 = w.out_b;
+  b.grad_p0_64 = w.gp64;
   b.status = w.status;
   return b;
 }
@@ -340,6 +289,54 @@ gs_status get_graph(Workspace& w, const GraphKey& key, cudaGraphExec_t* out) {
   return GS_OK;
 }
 
+gs_status enqueue_gradient64(Workspace& w, const gs_params& prm, const float* dq, const double* p64_in,
+                             const float* dt, cudaStream_t st) {
+  const int n = static_cast<int>(prm.N);
+  gs_status s = ensure_clean(w, n, st);
+  if (s != GS_OK) return s;
+  PackArgs pk;
+  pk.q = dq;
+  pk.p = nullptr;
+  pk.p64_in = p64_in;
+  pk.tgt = dt;
+  pk.q64 = w.q64;
+  pk.p64 = w.p64;
+  pk.t64 = w.t64;
+  pk.qp = w.traj;
+  pk.n = n;
+  pk.kq = make_scales(prm.sigma).kq;
+  pk.status = w.status;
+  GS_CUDA(launch_pack(pk, st));
+  cudaGraphExec_t ge = nullptr;
+  if ((s = get_graph(w, GraphKey{1, n, prm.T, prm.sigma, prm.lambda}, &ge)) != GS_OK) return s;
+  GS_CUDA(cudaGraphLaunch(ge, st));
+  return GS_OK;
+}
+
+gs_status enqueue_forward64(Workspace& w, const gs_params& prm, const float* dq, const double* p64_in,
+                            cudaStream_t st) {
+  const int n = static_cast<int>(prm.N);
+  gs_status s = ensure_clean(w, n, st);
+  if (s != GS_OK) return s;
+  PackArgs pk;
+  pk.q = dq;
+  pk.p = nullptr;
+  pk.p64_in = p64_in;
+  pk.tgt = nullptr;
+  pk.q64 = w.q64;
+  pk.p64 = w.p64;
+  pk.t64 = nullptr;
+  pk.qp = w.traj;
+  pk.n = n;
+  pk.kq = make_scales(prm.sigma).kq;
+  pk.status = w.status;
+  GS_CUDA(launch_pack(pk, st));
+  cudaGraphExec_t ge = nullptr;
+  if ((s = get_graph(w, GraphKey{0, n, prm.T, prm.sigma, 0.0}, &ge)) != GS_OK) return s;
+  GS_CUDA(cudaGraphLaunch(ge, st));
+  return GS_OK;
+}
+
 // Common driver of shoot_forward / shoot_gradient.
 gs_status run_shoot(int kind, const gs_params* prm, const float* q0, const float* p0, const float* target,
                     float* q1, float* p1, double* H0, double* loss, float* gp, float* gq, void* stream) {
@@ -365,6 +362,7 @@ gs_status run_shoot(int kind, const gs_params* prm, const float* q0, const float
   PackArgs pk;
   pk.q = dq;
   pk.p = dp;
+  pk.p64_in = nullptr;
   pk.tgt = dt;
   pk.q64 = w->q64;
   pk.p64 = w->p64;
@@ -617,8 +615,6 @@ gs_status time_pair_config(int kind_in, int64_t N, double sigma, const float* q,
   if (used) *used = kind < 2 ? c.splits : sc.cluster;
   return finish_sync(*w, st);
 }
-
-}  // namespace
 
 void set_last_error(const char* msg) { g_err = msg ? msg : ""; }
 

@@ -1,0 +1,113 @@
+// Host engine internals shared by engine.cu and lbfgs.cu: the per-device
+// workspace, the CUDA-call error macro and the helpers that stage arrays,
+// cache graphs and read the device status word.
+#pragma once
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "gs_internal.h"
+#include "../../include/gshoot.h"
+
+namespace gs {
+
+// Record the calling thread's error message and return `st`.
+gs_status fail(gs_status st, const std::string& msg);
+
+#define GS_CUDA(call)                                                                      \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return ::gs::fail(e_ == cudaErrorMemoryAllocation ? GS_ENOMEM : GS_ECUDA,            \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));               \
+  } while (0)
+
+inline int round_up(long long x, int m) { return static_cast<int>((x + m - 1) / m * m); }
+
+struct GraphKey {
+  int kind;  // 0 forward only, 1 gradient
+  int n, T;
+  double sigma, lambda;
+  bool operator<(const GraphKey& o) const {
+    return std::tie(kind, n, T, sigma, lambda) < std::tie(o.kind, o.n, o.T, o.sigma, o.lambda);
+  }
+};
+
+// FP64 vectors of the device-resident L-BFGS (register_landmarks).
+struct LbfgsBufs {
+  int n3 = 0, m = 0;
+  std::vector<void*> allocs;
+  double *x = nullptr, *g = nullptr, *d = nullptr, *xt = nullptr, *gt = nullptr;
+  double *S = nullptr, *Y = nullptr;  // m x n3 each
+  double* scal = nullptr;             // alpha[m], beta, dots...
+  double* part = nullptr;             // per-CTA partial sums of a dot product
+  unsigned* ticket = nullptr;
+  void free_all() {
+    for (void* p : allocs) cudaFree(p);
+    allocs.clear();
+    n3 = m = 0;
+  }
+};
+
+struct Workspace {
+  int device = -1;
+  int num_sms = 0;
+  // capacities
+  int cap_npad = 0, cap_T = 0, cap_splits = 0;
+  int cap_red = 0;
+  std::vector<void*> allocs;
+  float4* traj = nullptr;  // (cap_T + 1) slots of QP pair records
+  float4* adj = nullptr;   // 2 slots of AB pair records: reverse steps alternate
+  size_t slot() const { return static_cast<size_t>(kRecF4) * (cap_npad / 2); }  // float4 per slot
+  double *q64 = nullptr, *p64 = nullptr, *a64 = nullptr, *b64 = nullptr, *t64 = nullptr;
+  double *hp0 = nullptr, *hq0 = nullptr;
+  double* gp64 = nullptr;  // FP64 dL/dp0 of the last gradient
+  Partial* part = nullptr;   // cap_splits * cap_npad
+  float *in_q = nullptr, *in_p = nullptr, *in_t = nullptr, *in_a = nullptr;
+  float *out_a = nullptr, *out_b = nullptr;
+  double *red_h = nullptr, *red_m = nullptr, *scalars = nullptr;
+  unsigned *ticket = nullptr, *status = nullptr;
+  // The trajectory and adjoint records hold zero padding for this N.
+  int clean_n = -1;
+  cudaStream_t capture_stream = nullptr;
+  std::map<GraphKey, cudaGraphExec_t> graphs;
+  LbfgsBufs lb;
+
+  void drop_graphs() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    graphs.clear();
+  }
+  void free_all() {
+    drop_graphs();
+    for (void* p : allocs) cudaFree(p);
+    allocs.clear();
+    lb.free_all();
+    cap_npad = cap_T = cap_splits = cap_red = 0;
+    clean_n = -1;
+  }
+};
+
+// The process-wide lock that serialises calls into the library.
+std::mutex& engine_mutex();
+gs_status get_workspace(Workspace** out);
+gs_status reserve(Workspace& w, int npad, int T, int splits);
+gs_status ensure_clean(Workspace& w, int n, cudaStream_t st);
+bool is_device_ptr(const void* p);
+gs_status stage_in(const float* src, float* staging, size_t n3, cudaStream_t st, const float** dev, bool* host);
+gs_status copy_out(float* dst, const float* src, size_t n3, cudaStream_t st, bool* host);
+gs_status finish_sync(Workspace& w, cudaStream_t st);
+gs_status check_params(const gs_params* prm);
+gs_status get_graph(Workspace& w, const GraphKey& key, cudaGraphExec_t* out);
+// Enqueue one gradient evaluation at FP64 momenta p64_in (device, N*3) with
+// q0 and target already on the device: pack, then replay the gradient graph.
+// Afterwards w.gp64 holds dL/dp0 and w.scalars[1] the loss (stream order).
+gs_status enqueue_gradient64(Workspace& w, const gs_params& prm, const float* dq, const double* p64_in,
+                             const float* dt, cudaStream_t st);
+// Enqueue the forward flow only at FP64 momenta; w.q64 then holds q(1).
+gs_status enqueue_forward64(Workspace& w, const gs_params& prm, const float* dq, const double* p64_in,
+                            cudaStream_t st);
+
+}  // namespace gs

@@ -147,6 +147,7 @@ struct StepBwdArgs {
   const double* hq0;
   float* grad_p0;
   float* grad_q0;
+  double* grad_p0_64;  // FP64 copy of dL/dp0 (may be null)
   int dry;
   unsigned* status;
 };
@@ -163,6 +164,7 @@ cudaError_t launch_step_backward(const StepConfig& cfg, const StepBwdArgs& a, cu
 struct PackArgs {
   const float* q;      // (N,3) float32 inputs (device)
   const float* p;      // may be null (zeros)
+  const double* p64_in;  // FP64 momenta (used instead of p when set)
   const float* tgt;    // may be null
   double* q64;
   double* p64;

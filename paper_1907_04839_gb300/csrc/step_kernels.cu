@@ -225,7 +225,9 @@ __global__ void __launch_bounds__(NT) k_step_backward(StepBwdArgs a) {
     an[0] = (float)al;
     an[6] = -(float)(a.kappa64 * be);
     if (a.first) {
-      if (a.grad_p0) a.grad_p0[tt] = (float)(be + a.hp0[tt]);
+      const double gp = be + a.hp0[tt];
+      if (a.grad_p0) a.grad_p0[tt] = (float)gp;
+      if (a.grad_p0_64) a.grad_p0_64[tt] = gp;
       if (a.grad_q0) a.grad_q0[tt] = (float)(al + a.hq0[tt]);
     }
   }

@@ -1,0 +1,82 @@
+"""register_landmarks (L-BFGS over p0, Algorithm 1 lines 18-19) on the GPU
+against the oracle's L-BFGS, which is written independently to the same
+specification.  Pair sums in FP32 put rounding noise of about 1e-7 into each
+gradient, so the two optimisation paths agree closely for the first
+iterations and then drift apart on a non-convex problem.  The first
+iterates are compared directly.  The end state is compared by its loss and by
+the landmark distances of Section 3.1."""
+import numpy as np
+import pytest
+
+import landmark_synth as ls
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def gs():
+    import paper_1907_04839_gb300 as m
+    return m
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64).ravel(); b = np.asarray(b, np.float64).ravel()
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def case(n=256, bumps=4, seed=0):
+    pr = ls.ellipsoid_pair(n, seed=seed, n_bumps=bumps)
+    return pr.q0.astype(np.float32), pr.target.astype(np.float32)
+
+
+@pytest.mark.parametrize("iters", [1, 2, 3, 5])
+def test_register_first_iterates_match_oracle(iters):
+    # 256 landmarks (4 bumps), sigma = 0.2, lambda = 10, T = 10, p0 = 0.
+    q0, t = case()
+    p_gpu, info = gs().register(torch.tensor(q0, device="cuda"), torch.tensor(t, device="cuda"), 10, 0.2, 10.0,
+                                max_iter=iters, grad_tol=0.0)
+    r = oracle.register(q0.astype(np.float64), t.astype(np.float64), 10, 0.2, 10.0, max_iter=iters,
+                        grad_tol=0.0)
+    e = rel(p_gpu.cpu().numpy(), r["x"])
+    print("iters=%d p0 rel err %.2e loss gpu %.9g oracle %.9g evals %d/%d" % (
+        iters, e, info["loss"], r["f"], info["evals"], r["evals"]))
+    assert info["iters"] == iters
+    assert e < 1e-4
+    assert abs(info["loss"] - r["f"]) < 1e-5 * r["f"]
+
+
+def test_register_end_state_256_landmarks():
+    q0, t = case()
+    p_gpu, info = gs().register(torch.tensor(q0, device="cuda"), torch.tensor(t, device="cuda"), 10, 0.2, 10.0,
+                                max_iter=50, grad_tol=1e-5)
+    r = oracle.register(q0.astype(np.float64), t.astype(np.float64), 10, 0.2, 10.0, max_iter=50, grad_tol=1e-5)
+    before = np.linalg.norm(q0 - t, axis=1)
+    print("gpu", info, "oracle loss", r["f"], "iters", r["iters"])
+    # the GPU loss, recomputed by the oracle at the GPU's p0, is as good as the oracle's own
+    L = oracle.loss(q0.astype(np.float64), p_gpu.cpu().numpy().astype(np.float64), t.astype(np.float64),
+                    10, 0.2, 10.0)
+    assert abs(L - info["loss"]) < 1e-5 * L
+    assert L <= r["f"] * (1 + 1e-3)
+    assert info["avg_dist"] < 0.5 * before.mean()
+    assert info["max_dist"] < before.max()
+    # distances reported by the library match q(1) of the oracle's flow at that p0
+    q1, _ = oracle.shoot_forward(q0.astype(np.float64), p_gpu.cpu().numpy().astype(np.float64), 10, 0.2)
+    d = np.linalg.norm(q1 - t, axis=1)
+    assert abs(info["avg_dist"] - d.mean()) < 1e-5 * d.mean()
+    assert abs(info["max_dist"] - d.max()) < 1e-5 * d.max()
+
+
+def test_register_host_arrays_and_status():
+    q0, t = case(n=200, seed=3)
+    p, info = gs().register(q0, t, 6, 0.2, 10.0, max_iter=3, grad_tol=0.0)
+    assert isinstance(p, np.ndarray) and p.shape == (200, 3)
+    assert info["status"] == 1 and info["iters"] == 3
+    assert info["loss"] < 10.0 * np.sum((q0 - t) ** 2)
+
+
+def test_register_rejects_bad_memory():
+    q0, t = case(n=64)
+    with pytest.raises(gs().GShootError):
+        gs().register(q0, t, 5, 0.2, 10.0, m=0)

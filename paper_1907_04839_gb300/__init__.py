@@ -19,7 +19,7 @@ import numpy as np
 from ._lib import EXPORTS, GShootError, GsParams, GsRegisterInfo, check, load
 
 __all__ = [
-    "step_forward", "step_backward", "shoot_forward", "shoot_gradient", "register",
+    "step_forward", "step_backward", "shoot_forward", "shoot_gradient", "register", "shoot",
     "release_workspace", "version", "GShootError", "GsParams", "EXPORTS",
 ]
 
@@ -132,6 +132,48 @@ def shoot_gradient(q0, p0, target, T, sigma, lam, ckpt_every=0):
     loss = ctypes.c_double(0.0)
     check(load().shoot_gradient(ctypes.byref(prm), pq, pp, pt, ctypes.byref(loss), og, oq, m.stream))
     return loss.value, gp, gq
+
+
+_SHOOT_FN = None
+
+
+def _shoot_function():
+    """torch.autograd.Function over shoot_gradient (built on first use, so
+    that the package imports without torch)."""
+    global _SHOOT_FN
+    if _SHOOT_FN is None:
+        import torch
+
+        class ShootLoss(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, q0, p0, target, T, sigma, lam, ckpt_every):
+                loss, gp, gq = shoot_gradient(q0, p0, target, T, sigma, lam, ckpt_every)
+                if not isinstance(gp, torch.Tensor):
+                    gp, gq = torch.from_numpy(gp), torch.from_numpy(gq)
+                ctx.save_for_backward(gq, gp)
+                ctx.dtypes = (q0.dtype, p0.dtype)
+                return torch.tensor(loss, dtype=torch.float64, device=q0.device)
+
+            @staticmethod
+            def backward(ctx, gout):
+                gq, gp = ctx.saved_tensors
+                dq = (gout.to(gq.dtype) * gq).to(ctx.dtypes[0]) if ctx.needs_input_grad[0] else None
+                dp = (gout.to(gp.dtype) * gp).to(ctx.dtypes[1]) if ctx.needs_input_grad[1] else None
+                return dq, dp, None, None, None, None, None
+
+        _SHOOT_FN = ShootLoss
+    return _SHOOT_FN
+
+
+def shoot(q0, p0, target, T, sigma, lam, ckpt_every=0):
+    """The loss of Eq. 3 as a differentiable torch scalar (FP64).
+
+    Backward gives dL/dq0 and dL/dp0 (no gradient flows to ``target``).  Both
+    come from the same library call as the loss: the forward flow, the loss,
+    and the exact reverse sweep of the Euler steps.  With ``ckpt_every = k``
+    (0 < k < T), the reverse sweep keeps the state only every k steps and
+    recomputes the rest.  The results are bitwise identical."""
+    return _shoot_function().apply(q0, p0, target, T, sigma, lam, ckpt_every)
 
 
 def register(q0, target, T, sigma, lam, p0=None, m=10, max_iter=100, grad_tol=1e-5):

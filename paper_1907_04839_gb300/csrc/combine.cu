@@ -36,6 +36,19 @@ __global__ void __launch_bounds__(kThreads) k_pack(PackArgs a) {
   r[6] = (float)p;
 }
 
+__global__ void __launch_bounds__(kThreads) k_restore(const double* ckq, const double* ckp, double* q64,
+                                                      double* p64, float4* rec, int n, double kq) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * n) return;
+  const int i = t / 3, k = t - 3 * i;
+  const double q = ckq[t], p = ckp[t];
+  q64[t] = q;
+  p64[t] = p;
+  float* r = reinterpret_cast<float*>(rec + (i >> 1) * kRecF4) + 2 * k + (i & 1);
+  r[0] = -(float)(kq * q);
+  r[6] = (float)p;
+}
+
 // Sum the split partials of landmark i over a group of kGroup lanes: lane l
 // takes splits l, l + kGroup, ..., then a fixed xor-butterfly combines the
 // lanes.  Every lane of the group ends with the same six sums (TwoSum is
@@ -138,6 +151,12 @@ int combine_group() { return kGroup; }
 cudaError_t launch_pack(const PackArgs& a, cudaStream_t st) {
   if (a.n <= 0) return cudaSuccess;
   k_pack<<<blocks_for(3LL * a.n), kThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restore(const double* ckq, const double* ckp, double* q64, double* p64, float4* rec, int n,
+                           double kq, cudaStream_t st) {
+  k_restore<<<blocks_for(3LL * n), kThreads, 0, st>>>(ckq, ckp, q64, p64, rec, n, kq);
   return cudaGetLastError();
 }
 

@@ -67,13 +67,15 @@ gs_status get_workspace(Workspace** out) {
 }
 
 // Make room for npad landmarks, T steps and the given split counts.
-gs_status reserve(Workspace& w, int npad, int T, int splits) {
+gs_status reserve(Workspace& w, int npad, int T, int splits, int nck) {
   // per-CTA reduction slots: at most Npad/4 fused-step CTAs (tiles of >= 64
   // targets, clusters of <= 16)
   const int red = npad + 64;
-  if (npad <= w.cap_npad && T <= w.cap_T && splits <= w.cap_splits && red <= w.cap_red) return GS_OK;
+  if (npad <= w.cap_npad && T <= w.cap_T && splits <= w.cap_splits && red <= w.cap_red && nck <= w.cap_ck)
+    return GS_OK;
   const int cn = std::max(npad, w.cap_npad), cT = std::max(T, w.cap_T);
   const int cs = std::max(splits, w.cap_splits), cr = std::max(red, w.cap_red);
+  const int ck = std::max(nck, w.cap_ck);
   w.free_all();
   const size_t n3 = 3 * static_cast<size_t>(cn);
   const size_t slot = static_cast<size_t>(kRecF4) * (cn / 2);
@@ -87,6 +89,7 @@ gs_status reserve(Workspace& w, int npad, int T, int splits) {
   GS_CUDA(dalloc(w, &w.hp0, n3));
   GS_CUDA(dalloc(w, &w.hq0, n3));
   GS_CUDA(dalloc(w, &w.gp64, n3));
+  if (ck > 0) GS_CUDA(dalloc(w, &w.ck64, 2 * static_cast<size_t>(ck) * n3));
   GS_CUDA(dalloc(w, &w.part, static_cast<size_t>(cs) * cn));
   GS_CUDA(dalloc(w, &w.in_q, n3));
   GS_CUDA(dalloc(w, &w.in_p, n3));
@@ -106,6 +109,7 @@ gs_status reserve(Workspace& w, int npad, int T, int splits) {
   w.cap_T = cT;
   w.cap_splits = cs;
   w.cap_red = cr;
+  w.cap_ck = ck;
   return GS_OK;
 }
 
@@ -179,14 +183,14 @@ gs_status check_params(const gs_params* prm) {
 // Arguments of fused forward step k (kind 1: the last step also forms the
 // loss and the adjoint initialisation).
 StepFwdArgs forward_step_args(Workspace& w, const StepConfig& c, int kind, int n, int T, int k, double sigma,
-                              double lambda) {
+                              double lambda, int rd = -1, int wr = -1, bool recompute = false) {
   const int npad = round_up(n, kPad);
   const KernelScales sc = make_scales(sigma);
   const size_t slot = w.slot();
   StepFwdArgs a;
   std::memset(&a, 0, sizeof(a));
-  a.qp = w.traj + k * slot;
-  a.qp_next = w.traj + (k + 1) * slot;
+  a.qp = w.traj + (rd < 0 ? k : rd) * slot;
+  a.qp_next = w.traj + (wr < 0 ? k + 1 : wr) * slot;
   a.n = n;
   a.npad = npad;
   a.split_len = c.split_len;
@@ -195,11 +199,12 @@ StepFwdArgs forward_step_args(Workspace& w, const StepConfig& c, int kind, int n
   a.kq = sc.kq;
   a.q64 = w.q64;
   a.p64 = w.p64;
-  a.first = (k == 0);
+  // A recomputed step (checkpointed reverse sweep) only rebuilds the state.
+  a.first = (k == 0) && !recompute;
   a.hp0 = w.hp0;
   a.hq0 = w.hq0;
-  a.last = (k == T - 1);
-  a.with_loss = (kind == 1);
+  a.last = (k == T - 1) && !recompute;
+  a.with_loss = (kind == 1) && !recompute;
   a.t64 = w.t64;
   a.lambda = lambda;
   a.a64 = w.a64;
@@ -215,14 +220,14 @@ StepFwdArgs forward_step_args(Workspace& w, const StepConfig& c, int kind, int n
 }
 
 // Arguments of fused reverse step number s = 0..T-1 (time step k = T-1-s).
-StepBwdArgs backward_step_args(Workspace& w, const StepConfig& c, int n, int T, int s, double sigma) {
+StepBwdArgs backward_step_args(Workspace& w, const StepConfig& c, int n, int T, int s, double sigma, int rd = -1) {
   const int npad = round_up(n, kPad);
   const KernelScales sc = make_scales(sigma);
   const size_t slot = w.slot();
   const int k = T - 1 - s;
   StepBwdArgs b;
   std::memset(&b, 0, sizeof(b));
-  b.qp = w.traj + k * slot;
+  b.qp = w.traj + (rd < 0 ? k : rd) * slot;
   b.ab = w.adj + (s & 1) * slot;
   b.ab_next = w.adj + ((s + 1) & 1) * slot;
   b.n = n;
@@ -246,19 +251,55 @@ StepBwdArgs backward_step_args(Workspace& w, const StepConfig& c, int n, int T, 
 
 // Enqueue the T forward steps (and, for kind 1, the loss and T reverse
 // steps): one fused cluster kernel per time step.
-gs_status enqueue_steps(Workspace& w, int kind, int n, int T, double sigma, double lambda, cudaStream_t st) {
+//
+// With a checkpoint interval c (0 < c < T), the forward sweep keeps only the
+// FP64 state at steps 0, c, 2c, ...  The reverse sweep handles the segments
+// from the last to the first.  For each segment it restores the checkpoint,
+// recomputes the segment's forward steps into record slots 0..c-1, then runs
+// its reverse steps.  Each recomputed record is bitwise the one the forward
+// sweep made, because it comes from the same FP64 state through the same
+// kernels.
+gs_status enqueue_steps(Workspace& w, int kind, int n, int T, double sigma, double lambda, int ckpt,
+                        cudaStream_t st) {
   const int npad = round_up(n, kPad);
   const StepConfig fc = choose_step_config(0, npad, w.num_sms);
   const StepConfig bc = choose_step_config(1, npad, w.num_sms);
   if (fc.threads == 0 || bc.threads == 0) return fail(GS_EINVAL, "no step kernel configuration");
+  if (kind == 0) ckpt = 0;
+  const size_t n3 = 3 * static_cast<size_t>(n);
   for (int k = 0; k < T; ++k) {
-    const StepFwdArgs a = forward_step_args(w, fc, kind, n, T, k, sigma, lambda);
+    if (ckpt && k % ckpt == 0) {
+      double* ck = w.ck64 + 2 * static_cast<size_t>(k / ckpt) * n3;
+      GS_CUDA(cudaMemcpyAsync(ck, w.q64, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      GS_CUDA(cudaMemcpyAsync(ck + n3, w.p64, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+    const int rd = ckpt ? (k & 1) : k, wr = ckpt ? ((k + 1) & 1) : k + 1;
+    const StepFwdArgs a = forward_step_args(w, fc, kind, n, T, k, sigma, lambda, rd, wr, false);
     GS_CUDA(launch_step_forward(fc, a, st, k > 0));
   }
   if (kind == 0) return GS_OK;
-  for (int s = 0; s < T; ++s) {
-    const StepBwdArgs b = backward_step_args(w, bc, n, T, s, sigma);
-    GS_CUDA(launch_step_backward(bc, b, st, true));
+  if (!ckpt) {
+    for (int s = 0; s < T; ++s) {
+      const StepBwdArgs b = backward_step_args(w, bc, n, T, s, sigma);
+      GS_CUDA(launch_step_backward(bc, b, st, true));
+    }
+    return GS_OK;
+  }
+  const KernelScales sc = make_scales(sigma);
+  const int nseg = (T + ckpt - 1) / ckpt;
+  int s = 0;  // reverse-step counter (picks the adjoint buffers)
+  for (int m = nseg - 1; m >= 0; --m) {
+    const int s0 = m * ckpt, len = std::min(ckpt, T - s0);
+    const double* ck = w.ck64 + 2 * static_cast<size_t>(m) * n3;
+    GS_CUDA(launch_restore(ck, ck + n3, w.q64, w.p64, w.traj, n, sc.kq, st));
+    for (int r = 0; r + 1 < len; ++r) {
+      const StepFwdArgs a = forward_step_args(w, fc, kind, n, T, s0 + r, sigma, lambda, r, r + 1, true);
+      GS_CUDA(launch_step_forward(fc, a, st, r > 0));
+    }
+    for (int r = len - 1; r >= 0; --r, ++s) {
+      const StepBwdArgs b = backward_step_args(w, bc, n, T, s, sigma, r);
+      GS_CUDA(launch_step_backward(bc, b, st, true));
+    }
   }
   return GS_OK;
 }
@@ -272,7 +313,7 @@ gs_status get_graph(Workspace& w, const GraphKey& key, cudaGraphExec_t* out) {
   if (w.graphs.size() >= 16) w.drop_graphs();
   cudaStream_t cs = w.capture_stream;
   GS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  gs_status s = enqueue_steps(w, key.kind, key.n, key.T, key.sigma, key.lambda, cs);
+  gs_status s = enqueue_steps(w, key.kind, key.n, key.T, key.sigma, key.lambda, key.ckpt, cs);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(cs, &g);
   if (s != GS_OK) {
@@ -308,7 +349,9 @@ gs_status enqueue_gradient64(Workspace& w, const gs_params& prm, const float* dq
   pk.status = w.status;
   GS_CUDA(launch_pack(pk, st));
   cudaGraphExec_t ge = nullptr;
-  if ((s = get_graph(w, GraphKey{1, n, prm.T, prm.sigma, prm.lambda}, &ge)) != GS_OK) return s;
+  if ((s = get_graph(w, GraphKey{1, n, prm.T, prm.sigma, prm.lambda, effective_ckpt(prm.ckpt_every, prm.T)}, &ge)) !=
+      GS_OK)
+    return s;
   GS_CUDA(cudaGraphLaunch(ge, st));
   return GS_OK;
 }
@@ -332,7 +375,7 @@ gs_status enqueue_forward64(Workspace& w, const gs_params& prm, const float* dq,
   pk.status = w.status;
   GS_CUDA(launch_pack(pk, st));
   cudaGraphExec_t ge = nullptr;
-  if ((s = get_graph(w, GraphKey{0, n, prm.T, prm.sigma, 0.0}, &ge)) != GS_OK) return s;
+  if ((s = get_graph(w, GraphKey{0, n, prm.T, prm.sigma, 0.0, 0}, &ge)) != GS_OK) return s;
   GS_CUDA(cudaGraphLaunch(ge, st));
   return GS_OK;
 }
@@ -343,14 +386,13 @@ gs_status run_shoot(int kind, const gs_params* prm, const float* q0, const float
   gs_status s = check_params(prm);
   if (s != GS_OK) return s;
   if (!q0 || !p0 || (kind == 1 && !target)) return fail(GS_EINVAL, "q0, p0 (and target) must not be NULL");
-  if (prm->ckpt_every != 0 && prm->ckpt_every < prm->T)
-    return fail(GS_EINVAL, "trajectory checkpointing is not available in this build");
   std::lock_guard<std::mutex> lk(g_mu);
   Workspace* w = nullptr;
   if ((s = get_workspace(&w)) != GS_OK) return s;
   const int n = static_cast<int>(prm->N), T = prm->T;
   const int npad = round_up(n, kPad);
-  if ((s = reserve(*w, npad, T, 1)) != GS_OK) return s;
+  const int ckpt = kind == 1 ? effective_ckpt(prm->ckpt_every, T) : 0;
+  if ((s = reserve(*w, npad, record_slots(T, ckpt), 1, ckpt ? (T + ckpt - 1) / ckpt : 0)) != GS_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if ((s = ensure_clean(*w, n, st)) != GS_OK) return s;
   const size_t n3 = 3 * static_cast<size_t>(n);
@@ -373,7 +415,7 @@ gs_status run_shoot(int kind, const gs_params* prm, const float* q0, const float
   pk.status = w->status;
   GS_CUDA(launch_pack(pk, st));
   cudaGraphExec_t ge = nullptr;
-  const GraphKey key{kind, n, T, prm->sigma, kind == 1 ? prm->lambda : 0.0};
+  const GraphKey key{kind, n, T, prm->sigma, kind == 1 ? prm->lambda : 0.0, ckpt};
   if ((s = get_graph(*w, key, &ge)) != GS_OK) return s;
   GS_CUDA(cudaGraphLaunch(ge, st));
   bool want_sync = host;
@@ -479,10 +521,10 @@ gs_status time_pair_kernels(const gs_params* prm, const float* q0, const float* 
   const StepConfig fc = choose_step_config(0, npad, w->num_sms);
   const StepConfig bc = choose_step_config(1, npad, w->num_sms);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // Middle time step of the trajectory just computed; dry runs change no state.
-  StepFwdArgs fa = forward_step_args(*w, fc, 1, n, T, T / 2, prm->sigma, prm->lambda);
+  // A middle time step on the state in record slot 0; dry runs change no state.
+  StepFwdArgs fa = forward_step_args(*w, fc, 1, n, T, T / 2, prm->sigma, prm->lambda, 0, 1, true);
   fa.dry = 1;
-  StepBwdArgs ba = backward_step_args(*w, bc, n, T, T - 1 - T / 2, prm->sigma);
+  StepBwdArgs ba = backward_step_args(*w, bc, n, T, T - 1 - T / 2, prm->sigma, 0);
   ba.dry = 1;
   cudaEvent_t e0, e1, e2;
   GS_CUDA(cudaEventCreate(&e0));

@@ -31,10 +31,16 @@ struct GraphKey {
   int kind;  // 0 forward only, 1 gradient
   int n, T;
   double sigma, lambda;
+  int ckpt;  // checkpoint interval of the reverse sweep (0: whole trajectory)
   bool operator<(const GraphKey& o) const {
-    return std::tie(kind, n, T, sigma, lambda) < std::tie(o.kind, o.n, o.T, o.sigma, o.lambda);
+    return std::tie(kind, n, T, sigma, lambda, ckpt) < std::tie(o.kind, o.n, o.T, o.sigma, o.lambda, o.ckpt);
   }
 };
+
+// Effective checkpoint interval for T steps: 0 keeps the whole trajectory.
+inline int effective_ckpt(int ckpt_every, int T) { return (ckpt_every > 0 && ckpt_every < T) ? ckpt_every : 0; }
+// Trajectory record slots needed (slots 0..return value).
+inline int record_slots(int T, int ckpt) { return ckpt ? (ckpt > 2 ? ckpt : 2) : T; }
 
 // FP64 vectors of the device-resident L-BFGS (register_landmarks).
 struct LbfgsBufs {
@@ -57,7 +63,7 @@ struct Workspace {
   int num_sms = 0;
   // capacities
   int cap_npad = 0, cap_T = 0, cap_splits = 0;
-  int cap_red = 0;
+  int cap_red = 0, cap_ck = 0;
   std::vector<void*> allocs;
   float4* traj = nullptr;  // (cap_T + 1) slots of QP pair records
   float4* adj = nullptr;   // 2 slots of AB pair records: reverse steps alternate
@@ -65,6 +71,7 @@ struct Workspace {
   double *q64 = nullptr, *p64 = nullptr, *a64 = nullptr, *b64 = nullptr, *t64 = nullptr;
   double *hp0 = nullptr, *hq0 = nullptr;
   double* gp64 = nullptr;  // FP64 dL/dp0 of the last gradient
+  double* ck64 = nullptr;  // cap_ck checkpoints of the FP64 state: (q64, p64) pairs
   Partial* part = nullptr;   // cap_splits * cap_npad
   float *in_q = nullptr, *in_p = nullptr, *in_t = nullptr, *in_a = nullptr;
   float *out_a = nullptr, *out_b = nullptr;
@@ -85,7 +92,7 @@ struct Workspace {
     for (void* p : allocs) cudaFree(p);
     allocs.clear();
     lb.free_all();
-    cap_npad = cap_T = cap_splits = cap_red = 0;
+    cap_npad = cap_T = cap_splits = cap_red = cap_ck = 0;
     clean_n = -1;
   }
 };
@@ -93,7 +100,9 @@ struct Workspace {
 // The process-wide lock that serialises calls into the library.
 std::mutex& engine_mutex();
 gs_status get_workspace(Workspace** out);
-gs_status reserve(Workspace& w, int npad, int T, int splits);
+// Room for npad landmarks, record slots 0..T, the split partials and nck
+// FP64 state checkpoints.
+gs_status reserve(Workspace& w, int npad, int T, int splits, int nck = 0);
 gs_status ensure_clean(Workspace& w, int n, cudaStream_t st);
 bool is_device_ptr(const void* p);
 gs_status stage_in(const float* src, float* staging, size_t n3, cudaStream_t st, const float** dev, bool* host);

@@ -183,6 +183,10 @@ struct UnpackArgs {
 
 cudaError_t launch_pack(const PackArgs& a, cudaStream_t st);
 cudaError_t launch_unpack(const UnpackArgs& a, cudaStream_t st);
+// Restore an FP64 state checkpoint into q64, p64 and record slot 0 of rec,
+// with the same rounding as the step kernels' epilogue.
+cudaError_t launch_restore(const double* ckq, const double* ckp, double* q64, double* p64, float4* rec, int n,
+                           double kq, cudaStream_t st);
 // Hq, Hp straight from one split-partial set (step_forward entry point).
 cudaError_t launch_partials_to_out(const Partial* part, int splits, int n, int npad,
                                    float* out_a, float* out_b, cudaStream_t st);

@@ -430,13 +430,14 @@ gs_status run_register(const gs_params* prm, const float* q0, const float* targe
   if (prm->lbfgs_m < 1 || prm->lbfgs_m > kMaxM) return fail(GS_EINVAL, "lbfgs_m must be in [1, 64]");
   if (prm->max_iter < 0) return fail(GS_EINVAL, "max_iter must be >= 0");
   if (!(prm->grad_tol >= 0.0)) return fail(GS_EINVAL, "grad_tol must be >= 0");
-  if (prm->ckpt_every != 0 && prm->ckpt_every < prm->T)
-    return fail(GS_EINVAL, "trajectory checkpointing is not available in register_landmarks");
   std::lock_guard<std::mutex> lk(engine_mutex());
   Workspace* w = nullptr;
   if ((s = get_workspace(&w)) != GS_OK) return s;
   const int n = static_cast<int>(prm->N), npad = round_up(n, kPad), n3 = 3 * n;
-  if ((s = reserve(*w, npad, prm->T, 1)) != GS_OK) return s;
+  const int ckpt = effective_ckpt(prm->ckpt_every, prm->T);
+  if ((s = reserve(*w, npad, std::max(prm->T, record_slots(prm->T, ckpt)), 1, ckpt ? (prm->T + ckpt - 1) / ckpt : 0)) !=
+      GS_OK)
+    return s;
   if ((s = alloc_lbfgs(*w, n3, prm->lbfgs_m)) != GS_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   bool host = false;

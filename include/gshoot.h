@@ -94,7 +94,7 @@ gs_status step_backward(int64_t N, double sigma, const float* q, const float* p,
                         float* dalpha, float* dbeta, void* stream);
 
 /*
- * shoot_forward — the forward flow of Algorithm 1 (lines 2-9): T explicit
+ * shoot_forward — the forward flow of Algorithm 1 (its forward loop): T explicit
  * Euler steps q <- q + dt Hp, p <- p - dt Hq from (q0, p0).
  * In: prm (N, T, sigma used), q0, p0.  Out: q1, p1 = state at t = 1 (either
  * may be NULL), *H0 = H(p0, q0) (Eq. 1) in FP64 (NULL to skip).
@@ -129,7 +129,7 @@ typedef struct gs_register_info {
 } gs_register_info;
 
 /*
- * register_landmarks — Algorithm 1, lines 18-19: L-BFGS over the initial
+ * register_landmarks — the outer optimisation of Algorithm 1: L-BFGS over the initial
  * momentum p0 of the loss L(p0) = H(p0, q0) + lambda ||q(1) - target||^2
  * (Eq. 3), each function evaluation being one ComputeGradient.  Settings
  * (the paper used VNL's L-BFGS without stating them): memory prm->lbfgs_m
@@ -146,6 +146,79 @@ typedef struct gs_register_info {
  */
 gs_status register_landmarks(const gs_params* prm, const float* q0, const float* target,
                              float* p0_inout, gs_register_info* info, void* stream);
+
+/* ---------------------------------------------------------------- batches and serving
+ * Many independent registrations share packed device arrays.  Each time
+ * step of their gradients is a single launch over all of them (one cluster
+ * per target tile of any problem).  L-BFGS advances in rounds: each round
+ * evaluates every active problem once.  The serving entry points add
+ * continuous batching: requests that arrive while others run are admitted at
+ * round boundaries as soon as device memory frees up.
+ */
+
+/* One problem of register_batch. */
+typedef struct gs_batch_problem {
+    int64_t N;                /* landmarks, >= 1 */
+    double sigma, lambda;     /* kernel width and mismatch weight of this problem */
+    const float* q0;          /* (N,3) template, host or device */
+    const float* target;      /* (N,3) target, host or device */
+    float* p0;                /* (N,3) starting momenta (NULL: zeros); receives the result */
+    gs_register_info info;    /* output */
+} gs_batch_problem;
+
+/*
+ * register_batch — B independent runs of register_landmarks, packed: every
+ * time step of every gradient evaluation is one launch over all problems
+ * still running.  Shared settings: T, lbfgs_m (1..64), max_iter, grad_tol.
+ * Writes probs[b].p0 (when non-NULL) and probs[b].info.  Each problem
+ * follows the same L-BFGS as register_landmarks.  Returns GS_OK,
+ * GS_NOT_CONVERGED if any problem stopped short of grad_tol, or the first
+ * error.  Synchronises `stream`.
+ */
+gs_status register_batch(int32_t B, gs_batch_problem* probs, int32_t T, int32_t lbfgs_m,
+                         int32_t max_iter, double grad_tol, void* stream);
+
+/* Settings of a registration server. */
+typedef struct gs_server_config {
+    int32_t T;              /* time steps of every request */
+    int32_t lbfgs_m;        /* L-BFGS memory (1..64) */
+    int32_t max_iter;       /* L-BFGS iteration limit */
+    int32_t max_problems;   /* requests resident at once */
+    double grad_tol;        /* stop at ||g|| <= grad_tol ||g0|| */
+    uint64_t memory_budget; /* device bytes the server may allocate (admission limit) */
+    void* stream;           /* cudaStream_t for all of the server's work */
+} gs_server_config;
+
+typedef struct gs_server gs_server;
+
+/* Create a server; allocates its whole memory budget up front. */
+gs_status gs_server_create(const gs_server_config* cfg, gs_server** out);
+
+/* Queue a request (arrays are copied; host or device).  *request_id names it.
+ * GS_ENOMEM if the request alone exceeds the memory budget. */
+gs_status gs_server_submit(gs_server* sv, int64_t N, double sigma, double lambda,
+                           const float* q0, const float* target, const float* p0,
+                           int64_t* request_id);
+
+/* One round: admit queued requests while memory allows, evaluate every
+ * active request once, advance their L-BFGS, retire finished ones, admit
+ * again.  Out (each may be NULL): requests resident, requests queued,
+ * requests finished in this round. */
+gs_status gs_server_step(gs_server* sv, int32_t* active, int32_t* queued, int32_t* completed);
+
+/* Result of a request.  *done = 0 while it is queued or running.  When done:
+ * p0_out (N,3 float32, host or device, may be NULL), *info, and latency[0]
+ * = seconds from submission to result, latency[1] = from admission to
+ * result (latency may be NULL). */
+gs_status gs_server_poll(gs_server* sv, int64_t request_id, float* p0_out,
+                         gs_register_info* info, double* latency, int32_t* done);
+
+/* Capacity and free space of the packed arrays (landmarks), bytes allocated. */
+gs_status gs_server_stats(gs_server* sv, int64_t* capacity_landmarks, int64_t* free_landmarks,
+                          int64_t* bytes);
+
+/* Free the server and its device memory. */
+void gs_server_destroy(gs_server* sv);
 
 /*
  * gs_time_pair_kernels — diagnostics (no counterpart in the paper): the

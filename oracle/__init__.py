@@ -206,7 +206,7 @@ def lbfgs_rosenbrock(x0, m=10, max_iter=500, grad_tol=1e-10):
 
 
 def register(q0, target, T, sigma, lam, p0=None, m=10, max_iter=50, grad_tol=1e-5):
-    """Algorithm 1 (lines 18-19): L-BFGS over p0 of the Eq. 3 loss.  Returns
+    """Algorithm 1, outer optimisation: L-BFGS over p0 of the Eq. 3 loss.  Returns
     dict(status, f, iters, evals, x=p0 (N,3), trace=loss per iterate)."""
     q0 = _in(q0); n = q0.shape[0]; target = _in(target, n)
     x = np.zeros((n, 3)) if p0 is None else _in(p0, n).copy()

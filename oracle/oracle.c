@@ -17,7 +17,7 @@
  * N landmarks, Gaussian kernel g_ij = exp(-||q_i - q_j||^2 / (2 sigma^2)),
  * s = 1/sigma^2, d_ij = q_i - q_j, c_ij = p_i . p_j.
  *
- * Readings of the garbled extraction (each is listed in the design doc):
+ * Readings of the paper where its text is garbled or silent:
  *   Eq. 1     H(p, q) = 1/2 <p, K(q) p> = 1/2 sum_ij g_ij p_i . p_j.
  *   Eq. 2     dq/dt = Hp = dH/dp,  dp/dt = -Hq = -dH/dq, so
  *             Hp_i = sum_j g_ij p_j,  Hq_i = -s sum_j c_ij g_ij d_ij.
@@ -211,7 +211,7 @@ double orc_hamiltonian(int64_t n, double sigma, const double* q, const double* p
     return 0.5 * h;
 }
 
-/* Forward flow of Algorithm 1 (lines 2-9 with q_t <- q0): T explicit Euler
+/* Forward flow of Algorithm 1 (its forward loop, started at q0): T explicit Euler
  * steps of Eq. 2.  traj_q / traj_p, when non-null, receive all T+1 states as
  * (T+1, N, 3) arrays. */
 void orc_shoot_forward(int64_t n, int T, double sigma, const double* q0, const double* p0,
@@ -537,8 +537,8 @@ int orc_lbfgs_rosenbrock(int64_t n, double* x, int m, int max_iter, double grad_
     return orc_lbfgs(n, x, rosen_fg, &n, m, max_iter, grad_tol, f_out, iters, evals, NULL);
 }
 
-/* register: minimise the Eq. 3 loss over p0 from p0_inout (Algorithm 1,
- * lines 18-19).  Returns the orc_lbfgs status. */
+/* register: minimise the Eq. 3 loss over p0 from p0_inout (the outer
+ * optimisation of Algorithm 1).  Returns the orc_lbfgs status. */
 typedef struct {
     int64_t n;
     int T;

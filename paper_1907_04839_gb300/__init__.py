@@ -16,10 +16,12 @@ import ctypes
 
 import numpy as np
 
-from ._lib import EXPORTS, GShootError, GsParams, GsRegisterInfo, check, load
+from ._lib import (EXPORTS, GShootError, GsBatchProblem, GsParams, GsRegisterInfo, GsServerConfig, check,
+                   load)
 
 __all__ = [
     "step_forward", "step_backward", "shoot_forward", "shoot_gradient", "register", "shoot",
+    "register_batch", "Server",
     "release_workspace", "version", "GShootError", "GsParams", "EXPORTS",
 ]
 
@@ -177,7 +179,7 @@ def shoot(q0, p0, target, T, sigma, lam, ckpt_every=0):
 
 
 def register(q0, target, T, sigma, lam, p0=None, m=10, max_iter=100, grad_tol=1e-5):
-    """Algorithm 1 (lines 18-19): L-BFGS over p0 of the Eq. 3 loss.  Returns
+    """Algorithm 1, outer optimisation: L-BFGS over p0 of the Eq. 3 loss.  Returns
     (p0, info) with info a dict (loss, grad_norm0, grad_norm, avg_dist,
     max_dist, iters, evals, status)."""
     m_ = _Marshal(q0)
@@ -197,6 +199,103 @@ def register(q0, target, T, sigma, lam, p0=None, m=10, max_iter=100, grad_tol=1e
     info = GsRegisterInfo()
     check(load().register_landmarks(ctypes.byref(prm), pq, pt, pp, ctypes.byref(info), m_.stream))
     return pout, info.as_dict()
+
+
+def _host_f32(x, n=None):
+    if hasattr(x, "detach"):
+        x = x.detach().cpu().numpy()
+    a = np.ascontiguousarray(x, dtype=np.float32)
+    if a.ndim != 2 or a.shape[1] != 3 or (n is not None and a.shape[0] != n):
+        raise ValueError("expected an (N, 3) array")
+    return a
+
+
+def register_batch(problems, T, m=10, max_iter=100, grad_tol=1e-5, stream=None):
+    """Run register over many independent problems at once (packed launches).
+
+    ``problems`` is a list of dicts with keys q0, target, sigma, lam and
+    optionally p0 (host arrays or tensors).  Returns a list of (p0, info)."""
+    keep = []
+    arr = (GsBatchProblem * len(problems))()
+    outs = []
+    for k, pr in enumerate(problems):
+        q0 = _host_f32(pr["q0"])
+        n = q0.shape[0]
+        t = _host_f32(pr["target"], n)
+        p0 = _host_f32(pr["p0"], n).copy() if pr.get("p0") is not None else np.zeros((n, 3), np.float32)
+        keep += [q0, t, p0]
+        outs.append(p0)
+        arr[k].N = n
+        arr[k].sigma = float(pr["sigma"])
+        arr[k].lambda_ = float(pr["lam"])
+        arr[k].q0 = q0.ctypes.data
+        arr[k].target = t.ctypes.data
+        arr[k].p0 = p0.ctypes.data
+    check(load().register_batch(len(problems), arr, int(T), int(m), int(max_iter), float(grad_tol),
+                                ctypes.c_void_p(stream or 0)))
+    return [(outs[k], arr[k].info.as_dict()) for k in range(len(problems))]
+
+
+class Server:
+    """Continuous-batching registration server (gs_server_* in the C ABI).
+
+    submit() queues a request; step() runs one round (admission by memory
+    budget, one evaluation of every resident request, retirement); poll()
+    returns (p0, info, latency) of a finished request or None."""
+
+    def __init__(self, T, m=10, max_iter=100, grad_tol=1e-5, memory_budget=8 << 30, max_problems=1024,
+                 stream=None):
+        self._lib = load()
+        cfg = GsServerConfig(T=int(T), lbfgs_m=int(m), max_iter=int(max_iter), max_problems=int(max_problems),
+                             grad_tol=float(grad_tol), memory_budget=int(memory_budget),
+                             stream=ctypes.c_void_p(stream or 0))
+        self._h = ctypes.c_void_p(0)
+        check(self._lib.gs_server_create(ctypes.byref(cfg), ctypes.byref(self._h)))
+        self._n = {}
+
+    def submit(self, q0, target, sigma, lam, p0=None):
+        q0 = _host_f32(q0)
+        n = q0.shape[0]
+        t = _host_f32(target, n)
+        p = _host_f32(p0, n) if p0 is not None else None
+        rid = ctypes.c_int64(0)
+        check(self._lib.gs_server_submit(self._h, n, float(sigma), float(lam), q0.ctypes.data, t.ctypes.data,
+                                         p.ctypes.data if p is not None else None, ctypes.byref(rid)))
+        self._n[rid.value] = n
+        return rid.value
+
+    def step(self):
+        a, q, c = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+        check(self._lib.gs_server_step(self._h, ctypes.byref(a), ctypes.byref(q), ctypes.byref(c)))
+        return a.value, q.value, c.value
+
+    def poll(self, rid):
+        n = self._n[rid]
+        p0 = np.empty((n, 3), np.float32)
+        info = GsRegisterInfo()
+        lat = (ctypes.c_double * 2)()
+        done = ctypes.c_int32(0)
+        check(self._lib.gs_server_poll(self._h, int(rid), p0.ctypes.data, ctypes.byref(info), lat,
+                                       ctypes.byref(done)))
+        if not done.value:
+            return None
+        return p0, info.as_dict(), (lat[0], lat[1])
+
+    def stats(self):
+        c, f, b = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+        check(self._lib.gs_server_stats(self._h, ctypes.byref(c), ctypes.byref(f), ctypes.byref(b)))
+        return {"capacity_landmarks": c.value, "free_landmarks": f.value, "bytes": b.value}
+
+    def close(self):
+        if self._h:
+            self._lib.gs_server_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def release_workspace() -> None:

@@ -22,6 +22,8 @@ GS_STATUS = {
 # Every symbol the header declares; tests check the library exports them all.
 EXPORTS = [
     "step_forward", "step_backward", "shoot_forward", "shoot_gradient", "register_landmarks",
+    "register_batch", "gs_server_create", "gs_server_submit", "gs_server_step", "gs_server_poll",
+    "gs_server_stats", "gs_server_destroy",
     "gs_time_pair_kernels", "gs_time_pair_config", "gs_set_step_config", "step_forward_noalloc",
     "gs_last_error",
     "gs_release_workspace",
@@ -61,6 +63,32 @@ class GsRegisterInfo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class GsBatchProblem(ctypes.Structure):
+    """Mirror of ``gs_batch_problem``."""
+    _fields_ = [
+        ("N", ctypes.c_int64),
+        ("sigma", ctypes.c_double),
+        ("lambda_", ctypes.c_double),
+        ("q0", ctypes.c_void_p),
+        ("target", ctypes.c_void_p),
+        ("p0", ctypes.c_void_p),
+        ("info", GsRegisterInfo),
+    ]
+
+
+class GsServerConfig(ctypes.Structure):
+    """Mirror of ``gs_server_config``."""
+    _fields_ = [
+        ("T", ctypes.c_int32),
+        ("lbfgs_m", ctypes.c_int32),
+        ("max_iter", ctypes.c_int32),
+        ("max_problems", ctypes.c_int32),
+        ("grad_tol", ctypes.c_double),
+        ("memory_budget", ctypes.c_uint64),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
 class GShootError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__("%s (%d): %s" % (GS_STATUS.get(status, "?"), status, msg))
@@ -76,6 +104,20 @@ def _declare(lib):
     lib.shoot_forward.argtypes = [P, fp, fp, fp, fp, dp, vp]
     lib.shoot_gradient.argtypes = [P, fp, fp, fp, dp, fp, fp, vp]
     lib.register_landmarks.argtypes = [P, fp, fp, fp, ctypes.POINTER(GsRegisterInfo), vp]
+    lib.register_batch.argtypes = [i32, ctypes.POINTER(GsBatchProblem), i32, i32, i32, cd, vp]
+    lib.register_batch.restype = ctypes.c_int
+    SV = ctypes.c_void_p
+    lib.gs_server_create.argtypes = [ctypes.POINTER(GsServerConfig), ctypes.POINTER(SV)]
+    lib.gs_server_submit.argtypes = [SV, i64, cd, cd, fp, fp, fp, ctypes.POINTER(ctypes.c_int64)]
+    lib.gs_server_step.argtypes = [SV, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.gs_server_poll.argtypes = [SV, ctypes.c_int64, fp, ctypes.POINTER(GsRegisterInfo),
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
+    lib.gs_server_stats.argtypes = [SV, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                    ctypes.POINTER(ctypes.c_int64)]
+    lib.gs_server_destroy.argtypes = [SV]
+    lib.gs_server_destroy.restype = None
+    for name in ("gs_server_create", "gs_server_submit", "gs_server_step", "gs_server_poll", "gs_server_stats"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.gs_time_pair_kernels.argtypes = [P, fp, fp, fp, i32, dp, dp, ctypes.c_void_p, vp]
     lib.step_forward_noalloc.argtypes = [i64, cd, fp, fp, fp, fp, vp]
     lib.gs_set_step_config.argtypes = [i32, i32, i32, i32]

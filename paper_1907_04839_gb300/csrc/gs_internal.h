@@ -152,6 +152,20 @@ struct StepBwdArgs {
   unsigned* status;
 };
 
+// Packed batches of independent problems.  Problem b occupies landmarks
+// [off, off+npad) of every packed array; items are (problem, target tile).
+struct BatchProb {
+  int off, n, npad, split_len;
+  double kq, kappa, dt, lambda;
+};
+struct BatchItem {
+  int prob, tile;
+};
+struct BatchTables {
+  const BatchItem* items;
+  const BatchProb* probs;
+};
+
 StepConfig step_config_for(int kind, int npad, int threads, int R, int cluster);
 StepConfig choose_step_config(int kind, int npad, int num_sms);
 // Override the fused step configuration of `kind` (threads == 0 restores the
@@ -159,6 +173,12 @@ StepConfig choose_step_config(int kind, int npad, int num_sms);
 bool set_step_override(int kind, int threads, int R, int cluster);
 cudaError_t launch_step_forward(const StepConfig& cfg, const StepFwdArgs& a, cudaStream_t st, bool pdl);
 cudaError_t launch_step_backward(const StepConfig& cfg, const StepBwdArgs& a, cudaStream_t st, bool pdl);
+// One launch over `items` (problem, tile) items; cfg gives the kernel variant
+// and cluster size (its tiles / split_len fields are unused).
+cudaError_t launch_bstep_forward(const StepConfig& cfg, int items, const StepFwdArgs& a, const BatchTables& bt,
+                                 cudaStream_t st, bool pdl);
+cudaError_t launch_bstep_backward(const StepConfig& cfg, int items, const StepBwdArgs& a, const BatchTables& bt,
+                                  cudaStream_t st, bool pdl);
 
 // ---------------------------------------------------------------- combine kernels
 struct PackArgs {

@@ -1,7 +1,6 @@
 // register_landmarks: minimise the loss of Eq. 3 over p0 by L-BFGS
-// (Section 2.1, Algorithm 1 lines 18-19).  The paper used VNL's L-BFGS
-// without stating its settings.  This one follows the reading of the
-// design notes:
+// (Section 2.1; the outer optimisation of Algorithm 1).  The paper used
+// VNL's L-BFGS without stating its settings; this one uses textbook choices:
 //  * memory m, two-loop recursion with initial scaling gamma = s.y / y.y;
 //  * first step -g scaled to 1/||g0||;
 //  * strong-Wolfe line search (c1 = 1e-4, c2 = 0.9) by bracketing and zoom

@@ -1,5 +1,6 @@
-// Fused time-step kernels: StepForward plus the Euler update (Algorithm 1,
-// lines 6-8), and StepBackward plus the adjoint update (lines 13-15).  Each
+// Fused time-step kernels: StepForward plus the Euler update of the forward
+// loop of Algorithm 1, and StepBackward plus the adjoint update of its
+// reverse loop.  Each
 // runs as one launch per time step.
 //
 // Work split.  A thread-block cluster of C CTAs owns a tile of M = NT*R
@@ -57,9 +58,21 @@ __device__ __forceinline__ bool grid_sum2(double vh, double vm, double* red_h, d
 
 }  // namespace
 
-// ---------------------------------------------------------------- forward step
+// ---------------------------------------------------------------- step bodies
+// One problem as seen by a CTA: the problem's landmarks are [off, off+npad)
+// of the packed arrays (off = 0 for a single problem), n of them real.  The
+// CTA owns target tile `tile` of the problem and source split `rank` of its
+// cluster.
+struct StepView {
+  int off, n, npad, split_len, tile;
+  float kappa_f, kq_f;
+  double kq, kappa, dt, lambda;
+};
+
+// Forward step of one tile: pair sums, cluster reduction, Euler update.
+// Accumulates this thread's H0 and mismatch contributions in hc, mc.
 template <int NT, int R>
-__global__ void __launch_bounds__(NT) k_step_forward(StepFwdArgs a) {
+__device__ __forceinline__ void forward_body(const StepFwdArgs& a, const StepView& v, double& hc, double& mc) {
   constexpr int M = NT * R;
   union Smem {
     StageBuf<1> st;
@@ -67,41 +80,38 @@ __global__ void __launch_bounds__(NT) k_step_forward(StepFwdArgs a) {
   };
   __shared__ __align__(128) Smem sm;
   __shared__ __align__(8) Pipe pp;
-  __shared__ double shred[NT / 32];
-  __shared__ int am_last;
 
   const unsigned rank = cluster_rank(), C = cluster_size();
-  const int tile = blockIdx.y;
-  const int j0 = min(static_cast<int>(rank) * a.split_len, a.npad);
-  const int j1 = min(j0 + a.split_len, a.npad);
+  const int lim = v.off + v.npad;
+  const int j0 = min(v.off + static_cast<int>(rank) * v.split_len, lim);
+  const int j1 = min(j0 + v.split_len, lim);
   if (threadIdx.x == 0) pipe_init(pp, NT / 32);
   __syncthreads();
   pdl_wait();  // the previous step's state must be complete
   pdl_launch_dependents();
 
-  const int base = tile * M + threadIdx.x;
+  const int tile0 = v.off + v.tile * M;
   FwdTile<R> t;
-  t.load(a.qp, base, NT, a.npad);
+  t.load(a.qp, tile0 + threadIdx.x, NT, lim);
   const float4* src[1] = {a.qp};
   stream_sources<1>(sm.st, pp, src, j0, j1, t, a.status);  // ends with a CTA barrier
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    ds v[6];
-    t.result(r, a.kappa, v);
+    ds w[6];
+    t.result(r, v.kappa_f, w);
     const int lt = threadIdx.x + r * NT;
-    sm.red[lt][0] = make_float4(v[0].hi, v[0].lo, v[1].hi, v[1].lo);
-    sm.red[lt][1] = make_float4(v[2].hi, v[2].lo, v[3].hi, v[3].lo);
-    sm.red[lt][2] = make_float4(v[4].hi, v[4].lo, v[5].hi, v[5].lo);
+    sm.red[lt][0] = make_float4(w[0].hi, w[0].lo, w[1].hi, w[1].lo);
+    sm.red[lt][1] = make_float4(w[2].hi, w[2].lo, w[3].hi, w[3].lo);
+    sm.red[lt][2] = make_float4(w[4].hi, w[4].lo, w[5].hi, w[5].lo);
   }
   cluster_sync();  // every CTA's tile partials are visible to the cluster
 
   const int slice = M / static_cast<int>(C);
-  double hc = 0.0, mc = 0.0;
   for (int item = threadIdx.x; item < slice * 3; item += NT) {
     const int lt = static_cast<int>(rank) * slice + item / 3;
     const int k = item % 3;
-    const int i = tile * M + lt;
-    if (i >= a.n) continue;
+    if (v.tile * M + lt >= v.n) continue;
+    const int i = tile0 + lt;  // packed landmark index
     const uint32_t lp = smem_u32(&sm.red[lt][0]);
     ds hp{0.f, 0.f}, hq{0.f, 0.f};
 #pragma unroll 4
@@ -119,8 +129,8 @@ __global__ void __launch_bounds__(NT) k_step_forward(StepFwdArgs a) {
     const int tt = 3 * i + k;
     const double Hp = ds_to_double(hp), Hq = ds_to_double(hq);
     const double p_old = a.p64[tt];
-    const double q = a.q64[tt] + a.dt * Hp;
-    const double p = p_old - a.dt * Hq;
+    const double q = a.q64[tt] + v.dt * Hp;
+    const double p = p_old - v.dt * Hq;
     if (!isfinite(q) || !isfinite(p)) atomicOr(a.status, kErrNonFinite);
     if (a.first) hc += 0.5 * p_old * Hp;  // H0 = 1/2 sum_i p0_i . Hp_i(q0, p0)
     double r = 0.0;
@@ -135,10 +145,10 @@ __global__ void __launch_bounds__(NT) k_step_forward(StepFwdArgs a) {
     a.q64[tt] = q;
     a.p64[tt] = p;
     float* qn = reinterpret_cast<float*>(a.qp_next + (i >> 1) * kRecF4) + 2 * k + (i & 1);
-    qn[0] = -(float)(a.kq * q);
+    qn[0] = -(float)(v.kq * q);
     qn[6] = (float)p;
     if (a.last && a.with_loss) {
-      const double al = 2.0 * a.lambda * r;
+      const double al = 2.0 * v.lambda * r;
       a.a64[tt] = al;
       a.b64[tt] = 0.0;
       float* an = reinterpret_cast<float*>(a.ab + (i >> 1) * kRecF4) + 2 * k + (i & 1);
@@ -147,21 +157,12 @@ __global__ void __launch_bounds__(NT) k_step_forward(StepFwdArgs a) {
     }
   }
   cluster_sync();  // peers may still be reading this CTA's partials
-
-  const bool reduce_h = a.first != 0;
-  const bool reduce_m = a.last && a.with_loss;
-  if ((!reduce_h && !reduce_m) || a.dry) return;  // uniform across the grid
-  double h, m;
-  if (grid_sum2(hc, mc, a.red_h, a.red_m, a.ticket, shred, &am_last, &h, &m) && threadIdx.x == 0) {
-    if (reduce_h) a.scalars[0] = h;
-    if (reduce_m) a.scalars[1] = (reduce_h ? h : a.scalars[0]) + a.lambda * m;
-    *a.ticket = 0u;
-  }
 }
 
-// ---------------------------------------------------------------- backward step
+// Reverse step of one tile: adjoint pair sums, cluster reduction, adjoint
+// update, and at time step 0 the gradient.
 template <int NT, int R>
-__global__ void __launch_bounds__(NT) k_step_backward(StepBwdArgs a) {
+__device__ __forceinline__ void backward_body(const StepBwdArgs& a, const StepView& v) {
   constexpr int M = NT * R;
   union Smem {
     StageBuf<2> st;
@@ -171,27 +172,27 @@ __global__ void __launch_bounds__(NT) k_step_backward(StepBwdArgs a) {
   __shared__ __align__(8) Pipe pp;
 
   const unsigned rank = cluster_rank(), C = cluster_size();
-  const int tile = blockIdx.y;
-  const int j0 = min(static_cast<int>(rank) * a.split_len, a.npad);
-  const int j1 = min(j0 + a.split_len, a.npad);
+  const int lim = v.off + v.npad;
+  const int j0 = min(v.off + static_cast<int>(rank) * v.split_len, lim);
+  const int j1 = min(j0 + v.split_len, lim);
   if (threadIdx.x == 0) pipe_init(pp, NT / 32);
   __syncthreads();
   pdl_wait();
   pdl_launch_dependents();
 
-  const int base = tile * M + threadIdx.x;
+  const int tile0 = v.off + v.tile * M;
   BwdTile<R> t;
-  t.load(a.qp, a.ab, base, NT, a.npad);
+  t.load(a.qp, a.ab, tile0 + threadIdx.x, NT, lim);
   const float4* src[2] = {a.qp, a.ab};
   stream_sources<2>(sm.st, pp, src, j0, j1, t, a.status);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    ds v[6];
-    t.result(r, a.kq, a.kappa, v);
+    ds w[6];
+    t.result(r, v.kq_f, v.kappa_f, w);
     const int lt = threadIdx.x + r * NT;
-    sm.red[lt][0] = make_float4(v[0].hi, v[0].lo, v[1].hi, v[1].lo);
-    sm.red[lt][1] = make_float4(v[2].hi, v[2].lo, v[3].hi, v[3].lo);
-    sm.red[lt][2] = make_float4(v[4].hi, v[4].lo, v[5].hi, v[5].lo);
+    sm.red[lt][0] = make_float4(w[0].hi, w[0].lo, w[1].hi, w[1].lo);
+    sm.red[lt][1] = make_float4(w[2].hi, w[2].lo, w[3].hi, w[3].lo);
+    sm.red[lt][2] = make_float4(w[4].hi, w[4].lo, w[5].hi, w[5].lo);
   }
   cluster_sync();
 
@@ -199,8 +200,8 @@ __global__ void __launch_bounds__(NT) k_step_backward(StepBwdArgs a) {
   for (int item = threadIdx.x; item < slice * 3; item += NT) {
     const int lt = static_cast<int>(rank) * slice + item / 3;
     const int k = item % 3;
-    const int i = tile * M + lt;
-    if (i >= a.n) continue;
+    if (v.tile * M + lt >= v.n) continue;
+    const int i = tile0 + lt;
     const uint32_t lp = smem_u32(&sm.red[lt][0]);
     ds da{0.f, 0.f}, db{0.f, 0.f};
 #pragma unroll 4
@@ -216,14 +217,14 @@ __global__ void __launch_bounds__(NT) k_step_backward(StepBwdArgs a) {
       continue;
     }
     const int tt = 3 * i + k;
-    const double al = a.a64[tt] + a.dt * ds_to_double(da);
-    const double be = a.b64[tt] + a.dt * ds_to_double(db);
+    const double al = a.a64[tt] + v.dt * ds_to_double(da);
+    const double be = a.b64[tt] + v.dt * ds_to_double(db);
     if (!isfinite(al) || !isfinite(be)) atomicOr(a.status, kErrNonFinite);
     a.a64[tt] = al;
     a.b64[tt] = be;
     float* an = reinterpret_cast<float*>(a.ab_next + (i >> 1) * kRecF4) + 2 * k + (i & 1);
     an[0] = (float)al;
-    an[6] = -(float)(a.kappa64 * be);
+    an[6] = -(float)(v.kappa * be);
     if (a.first) {
       const double gp = be + a.hp0[tt];
       if (a.grad_p0) a.grad_p0[tt] = (float)gp;
@@ -232,6 +233,98 @@ __global__ void __launch_bounds__(NT) k_step_backward(StepBwdArgs a) {
     }
   }
   cluster_sync();
+}
+
+// ---------------------------------------------------------------- single-problem kernels
+template <int NT, int R>
+__global__ void __launch_bounds__(NT) k_step_forward(StepFwdArgs a) {
+  __shared__ double shred[NT / 32];
+  __shared__ int am_last;
+  StepView v;
+  v.off = 0;
+  v.n = a.n;
+  v.npad = a.npad;
+  v.split_len = a.split_len;
+  v.tile = blockIdx.y;
+  v.kappa_f = a.kappa;
+  v.kq_f = static_cast<float>(a.kq);
+  v.kq = a.kq;
+  v.kappa = a.kappa64;
+  v.dt = a.dt;
+  v.lambda = a.lambda;
+  double hc = 0.0, mc = 0.0;
+  forward_body<NT, R>(a, v, hc, mc);
+  const bool reduce_h = a.first != 0;
+  const bool reduce_m = a.last && a.with_loss;
+  if ((!reduce_h && !reduce_m) || a.dry) return;  // uniform across the grid
+  double h, m;
+  if (grid_sum2(hc, mc, a.red_h, a.red_m, a.ticket, shred, &am_last, &h, &m) && threadIdx.x == 0) {
+    if (reduce_h) a.scalars[0] = h;
+    if (reduce_m) a.scalars[1] = (reduce_h ? h : a.scalars[0]) + a.lambda * m;
+    *a.ticket = 0u;
+  }
+}
+
+template <int NT, int R>
+__global__ void __launch_bounds__(NT) k_step_backward(StepBwdArgs a) {
+  StepView v;
+  v.off = 0;
+  v.n = a.n;
+  v.npad = a.npad;
+  v.split_len = a.split_len;
+  v.tile = blockIdx.y;
+  v.kappa_f = a.kappa;
+  v.kq_f = a.kq;
+  v.kq = 0.0;
+  v.kappa = a.kappa64;
+  v.dt = a.dt;
+  v.lambda = 0.0;
+  backward_body<NT, R>(a, v);
+}
+
+// ---------------------------------------------------------------- packed batch kernels
+// blockIdx.y indexes the item table; each item is one target tile of one
+// problem.  The H0 and mismatch sums of each CTA go to red_h / red_m at
+// index blockIdx.y * C + rank; a separate kernel adds them per problem.
+__device__ __forceinline__ StepView batch_view(const BatchTables& bt) {
+  const BatchItem it = bt.items[blockIdx.y];
+  const BatchProb P = bt.probs[it.prob];
+  StepView v;
+  v.off = P.off;
+  v.n = P.n;
+  v.npad = P.npad;
+  v.split_len = P.split_len;
+  v.tile = it.tile;
+  v.kappa_f = static_cast<float>(P.kappa);
+  v.kq_f = static_cast<float>(P.kq);
+  v.kq = P.kq;
+  v.kappa = P.kappa;
+  v.dt = P.dt;
+  v.lambda = P.lambda;
+  return v;
+}
+
+template <int NT, int R>
+__global__ void __launch_bounds__(NT) k_bstep_forward(StepFwdArgs a, BatchTables bt) {
+  __shared__ double shred[NT / 32];
+  const StepView v = batch_view(bt);
+  double hc = 0.0, mc = 0.0;
+  forward_body<NT, R>(a, v, hc, mc);
+  const bool reduce_h = a.first != 0;
+  const bool reduce_m = a.last && a.with_loss;
+  if ((!reduce_h && !reduce_m) || a.dry) return;
+  const double bh = block_sum_f64(hc, shred);
+  const double bm = block_sum_f64(mc, shred);
+  if (threadIdx.x == 0) {
+    const unsigned cta = blockIdx.y * gridDim.x + cluster_rank();
+    if (reduce_h) a.red_h[cta] = bh;
+    if (reduce_m) a.red_m[cta] = bm;
+  }
+}
+
+template <int NT, int R>
+__global__ void __launch_bounds__(NT) k_bstep_backward(StepBwdArgs a, BatchTables bt) {
+  backward_body<NT, R>(a, batch_view(bt));
 }
 
 // ---------------------------------------------------------------- host side
@@ -335,6 +428,52 @@ StepConfig choose_step_config(int kind, int npad, int num_sms) {
   while (c * 2 <= cl) c *= 2;
   if (kind == 0) return step_config_for(0, npad, 128, 1, c);
   return step_config_for(1, npad, 64, 1, c);
+}
+
+template <typename K, typename A>
+cudaError_t launch_cluster2(K kern, int cluster, int threads, int items, const A& args, const BatchTables& bt,
+                            cudaStream_t st, bool pdl) {
+  {
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    const void* key = reinterpret_cast<const void*>(kern);
+    if (!g_attr_done.count(key)) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+      g_attr_done.insert(key);
+    }
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cluster, items);
+  cfg.blockDim = dim3(threads);
+  cfg.stream = st;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 2 : 1;
+  return cudaLaunchKernelEx(&cfg, kern, args, bt);
+}
+
+cudaError_t launch_bstep_forward(const StepConfig& c, int items, const StepFwdArgs& a, const BatchTables& bt,
+                                 cudaStream_t st, bool pdl) {
+#define X(T_, R_) \
+  if (c.threads == T_ && c.R == R_) return launch_cluster2(k_bstep_forward<T_, R_>, c.cluster, T_, items, a, bt, st, pdl);
+  GS_STEP_FWD_CASES(X)
+#undef X
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_bstep_backward(const StepConfig& c, int items, const StepBwdArgs& a, const BatchTables& bt,
+                                  cudaStream_t st, bool pdl) {
+#define X(T_, R_) \
+  if (c.threads == T_ && c.R == R_) return launch_cluster2(k_bstep_backward<T_, R_>, c.cluster, T_, items, a, bt, st, pdl);
+  GS_STEP_BWD_CASES(X)
+#undef X
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_step_forward(const StepConfig& c, const StepFwdArgs& a, cudaStream_t st, bool pdl) {

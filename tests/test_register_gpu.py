@@ -1,4 +1,4 @@
-"""register_landmarks (L-BFGS over p0, Algorithm 1 lines 18-19) on the GPU
+"""register_landmarks (L-BFGS over p0, the outer optimisation of Algorithm 1) on the GPU
 against the oracle's L-BFGS, which is written independently to the same
 specification.  Pair sums in FP32 put rounding noise of about 1e-7 into each
 gradient, so the two optimisation paths agree closely for the first

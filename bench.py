@@ -10,9 +10,15 @@ lambda = 10, T = 20, and p0 ~ N(0, 0.01^2).  All inputs are synthetic and
 seeded.
 
 Metric: gradient evaluations per second.  Each step also reports its pair
-interactions per second, 2 T N^2 / t.
+interactions per second, 2 T N^2 / t.  The same line carries two bounded
+samples of the other workloads: `batched` (independent registrations packed
+into shared launches, against a loop of single registrations) and `served`
+(a Poisson request trace through the continuous-batching server, with p50 /
+p99 latency).  `--workload batched|served` runs those workloads at their
+full sizes instead and prints their own line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gshoot|reference]
+                    [--workload grad|batched|served]
 
 It prints one JSON line on rank 0.  `--impl reference` times the FP64 CPU
 oracle on this host's cores on a bounded sample of the same workload.
@@ -49,6 +55,10 @@ FLOPS_PER_PAIR_BWD = 65
 # FP32 instructions per pair issued by the kernels (for the pipe fraction).
 INSTR_PER_PAIR_FWD = 16
 INSTR_PER_PAIR_BWD = 36
+# DRAM bytes (read + write) of one k_step_backward launch, from ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum, caches flushed before the
+# launch) of the current kernel, by N.  Empty it whenever the kernel changes.
+DRAM_BYTES_PER_BWD_LAUNCH = {4096: 416256, 16384: 1595904}
 
 
 def parse():
@@ -61,6 +71,12 @@ def parse():
     ap.add_argument("--n", type=int, default=N_LANDMARKS,
                     help="landmark count (profiling runs only; the reported workload is N=4096)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["grad", "batched", "served"], default="grad")
+    ap.add_argument("--batched-count", type=int, default=None,
+                    help="registrations of the batched workload (default: 128 in the grad run's sample, 512 alone)")
+    ap.add_argument("--served-count", type=int, default=None,
+                    help="requests of the served trace (default: 8 in the grad run's sample, 64 alone)")
+    ap.add_argument("--no-samples", action="store_true", help="grad run without the batched / served samples")
     return ap.parse_args()
 
 
@@ -70,6 +86,30 @@ def workload(n=N_LANDMARKS):
     p0 = ls.random_momentum(n, P0_SCALE, seed=1)
     f = lambda a: np.ascontiguousarray(a, dtype=np.float32)
     return f(pr.q0), f(p0), f(pr.target)
+
+
+def batched_problems(count):
+    """Independent registrations: N log-uniform in [500, 8000], sigma uniform
+    over {0.05, 0.1, 0.2}, lambda = 10, each its own ellipsoid-plus-bumps pair."""
+    import landmark_synth as ls
+    out = []
+    for r in ls.batched_requests(count, n_lo=500, n_hi=8000, sigmas=(0.05, 0.1, 0.2), first_seed=1):
+        pr = ls.ellipsoid_pair(r["n"], seed=r["seed"], n_bumps=8)
+        out.append(dict(q0=np.ascontiguousarray(pr.q0, np.float32), target=np.ascontiguousarray(pr.target, np.float32),
+                        sigma=r["sigma"], lam=LAMBDA))
+    return out
+
+
+def served_trace(count, rate=200.0):
+    """Poisson arrivals (mean `rate` per second), N log-uniform in [1000, 50000],
+    sigma = 0.1, lambda = 10."""
+    import landmark_synth as ls
+    out = []
+    for r in ls.poisson_trace(count, rate, n_lo=1000, n_hi=50000, trace_seed=0, first_seed=1001):
+        pr = ls.ellipsoid_pair(r["n"], seed=r["seed"], n_bumps=8)
+        out.append(dict(q0=np.ascontiguousarray(pr.q0, np.float32), target=np.ascontiguousarray(pr.target, np.float32),
+                        sigma=0.1, lam=LAMBDA, t_arrival=r["t_arrival"]))
+    return out
 
 
 # ---------------------------------------------------------------- distributed
@@ -246,6 +286,119 @@ def run_reference(args, dist):
     return 0
 
 
+# ---------------------------------------------------------------- batched and served workloads
+
+def measure_batched(gsh, count, max_iter=100, T=T_STEPS):
+    """`count` registrations two ways, each timed by wall clock from host
+    inputs to host results: packed (register_batch: every time step of every
+    resident problem in one launch) and a loop of register() calls."""
+    import torch
+    probs = batched_problems(count)
+    gsh.register_batch(probs[:2], T=T, max_iter=2, grad_tol=1e-5)       # warm-up (module load)
+    gsh.register(probs[0]["q0"], probs[0]["target"], T, probs[0]["sigma"], probs[0]["lam"], max_iter=2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    packed = gsh.register_batch(probs, T=T, max_iter=max_iter, grad_tol=1e-5)
+    torch.cuda.synchronize()
+    t_packed = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    loop = [gsh.register(p["q0"], p["target"], T, p["sigma"], p["lam"], max_iter=max_iter, grad_tol=1e-5)
+            for p in probs]
+    torch.cuda.synchronize()
+    t_loop = time.perf_counter() - t0
+    pairs = lambda res: sum(2 * T * p["q0"].shape[0] ** 2 * r[1]["evals"] for p, r in zip(probs, res))
+    rel = [abs(a[1]["loss"] - b[1]["loss"]) / max(abs(b[1]["loss"]), 1e-300) for a, b in zip(packed, loop)]
+    ns = [p["q0"].shape[0] for p in probs]
+    return {
+        "registrations": count, "T": T, "max_iter": max_iter, "grad_tol": 1e-5,
+        "N": "log-uniform [500, 8000], sum N^2 = %.3g" % float(sum(n * n for n in ns)),
+        "packed_regs_per_s": count / t_packed, "loop_regs_per_s": count / t_loop,
+        "speedup": t_loop / t_packed,
+        "packed_pair_interactions_per_s": pairs(packed) / t_packed,
+        "loop_pair_interactions_per_s": pairs(loop) / t_loop,
+        "packed_s": t_packed, "loop_s": t_loop,
+        "evals_packed": int(sum(r[1]["evals"] for r in packed)), "evals_loop": int(sum(r[1]["evals"] for r in loop)),
+        "loss_rel_diff_median": float(np.median(rel)), "loss_rel_diff_max": float(np.max(rel)),
+        "avg_dist_packed": float(np.mean([r[1]["avg_dist"] for r in packed])),
+        "avg_dist_loop": float(np.mean([r[1]["avg_dist"] for r in loop])),
+        "timing": "wall clock, host inputs and results included",
+    }
+
+
+def measure_served(gsh, count, max_iter=200, budget=120 << 30, rate=200.0, T=T_STEPS):
+    """A Poisson trace through the continuous-batching server.  Requests are
+    submitted at their arrival times while the server runs rounds; latency is
+    from arrival to the round that finished the request."""
+    trace = served_trace(count, rate)
+    sv = gsh.Server(T=T, max_iter=max_iter, grad_tol=1e-5, memory_budget=budget, max_problems=1024)
+    rid = [None] * count
+    done_at = [None] * count
+    service = [None] * count
+    evals = [0] * count
+    t0 = time.perf_counter()
+    nsub = 0
+    outstanding = set()
+    while True:
+        now = time.perf_counter() - t0
+        while nsub < count and trace[nsub]["t_arrival"] <= now:
+            r = trace[nsub]
+            rid[nsub] = sv.submit(r["q0"], r["target"], r["sigma"], r["lam"])
+            outstanding.add(nsub)
+            nsub += 1
+        if not outstanding:
+            if nsub == count:
+                break
+            time.sleep(max(0.0, trace[nsub]["t_arrival"] - (time.perf_counter() - t0)))
+            continue
+        a, q, c = sv.step()
+        if c > 0:
+            tw = time.perf_counter() - t0
+            for k in list(outstanding):
+                out = sv.poll(rid[k])
+                if out is not None:
+                    done_at[k] = tw
+                    service[k] = out[2][1]
+                    evals[k] = out[1]["evals"]
+                    outstanding.discard(k)
+    sv.close()
+    lat = np.array([done_at[k] - trace[k]["t_arrival"] for k in range(count)])
+    svc = np.array(service)
+    makespan = max(done_at) - trace[0]["t_arrival"]
+    ns = [r["q0"].shape[0] for r in trace]
+    return {
+        "requests": count, "arrival_rate_per_s": rate, "T": T, "max_iter": max_iter, "grad_tol": 1e-5,
+        "memory_budget_bytes": budget, "N": "log-uniform [1000, 50000], mean %.0f" % float(np.mean(ns)),
+        "regs_per_s": count / makespan, "makespan_s": makespan,
+        "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+        "service_p50_s": float(np.percentile(svc, 50)), "service_p99_s": float(np.percentile(svc, 99)),
+        "pair_interactions_per_s": sum(2 * T * n * n * e for n, e in zip(ns, evals)) / makespan,
+        "timing": "wall clock from arrival to result, host inputs, queueing included",
+    }
+
+
+def run_workload(args, dist):
+    """--workload batched|served: the full-size workload, its own JSON line."""
+    import torch
+    import paper_1907_04839_gb300 as gsh
+    dist.init("nccl")
+    torch.cuda.set_device(dist.local)
+    if args.workload == "batched":
+        res = measure_batched(gsh, args.batched_count or 512)
+        metric = "registrations/s (%d packed registrations, N~LogU[500,8000], T=20)" % res["registrations"]
+        value, ms = res["packed_regs_per_s"], res["packed_s"] * 1e3
+    else:
+        res = measure_served(gsh, args.served_count or 64)
+        metric = "served registrations/s (Poisson 200/s, N~LogU[1000,50000], T=20)"
+        value, ms = res["regs_per_s"], res["makespan_s"] * 1e3
+    line = {"metric": metric, "value": value * dist.world, "unit": "regs/s", "n_gpus": dist.world, "steps": 1,
+            "warmup": 1, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic", "config": {"workload": args.workload, **res}}
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+    dist.close()
+    return 0
+
+
 # ---------------------------------------------------------------- GPU arm
 
 def run_gshoot(args, dist):
@@ -291,6 +444,13 @@ def run_gshoot(args, dist):
     clocks = ClockSampler(uuid)
     K = args.steps
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    # The graph records events around its forward and reverse sweeps: the
+    # per-launch times of the roofline come from the timed steps themselves.
+    gsh.check(lib.gs_set_phase_timing(1))
+    step_device()
+    torch.cuda.synchronize(dev)
+    fwd_phase = bwd_phase = 0.0
+    pf, pb = ctypes.c_double(0.0), ctypes.c_double(0.0)
     dist.barrier()
     torch.cuda.synchronize(dev)
     clocks.start()
@@ -299,9 +459,14 @@ def run_gshoot(args, dist):
         ev[k][0].record(stream)
         step_device()
         ev[k][1].record(stream)
+        ev[k][1].synchronize()         # host-side wait, outside the events
+        gsh.check(lib.gs_phase_times(ctypes.byref(pf), ctypes.byref(pb)))
+        fwd_phase += pf.value
+        bwd_phase += pb.value
     torch.cuda.synchronize(dev)
     dist.barrier()
     clk = clocks.stop()
+    gsh.check(lib.gs_set_phase_timing(0))
     total_ms = sum(a.elapsed_time(b) for a, b in ev)
     total_ms = dist.max(total_ms)
     ms_per_step = total_ms / K
@@ -328,32 +493,45 @@ def run_gshoot(args, dist):
     for _ in range(3):
         step_host()
     KE = max(1, min(args.e2e_steps, K))
-    dist.barrier()
-    t0 = time.perf_counter()
-    for _ in range(KE):
-        step_host()
-    e2e_s = dist.max(time.perf_counter() - t0)
-    e2e = {"value": dist.world * KE / e2e_s, "unit": "grad-evals/s",
+    # three blocks of KE / 3 calls; the median block is reported
+    nb = 3 if KE >= 3 else 1
+    per = KE // nb
+    rates = []
+    for _ in range(nb):
+        dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(per):
+            step_host()
+        rates.append(dist.world * per / dist.max(time.perf_counter() - t0))
+    e2e = {"value": float(np.median(rates)), "unit": "grad-evals/s",
            "h2d_bytes_per_step": 3 * n * 3 * 4, "d2h_bytes_per_step": 2 * n * 3 * 4 + 8,
-           "steps": KE}
+           "steps": per * nb, "blocks": [round(r, 1) for r in rates],
+           "path": "shoot_gradient with pinned host q0, p0, target in and grad_p0, grad_q0, loss out"}
 
     num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peaks = read_measured_peaks()
     max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak = alu_peak_tflops(num_sms, max_mhz)
     pairs = n * n
-    bwd_tf = FLOPS_PER_PAIR_BWD * pairs / (bwd_ms.value * 1e-3) / 1e12
-    fwd_tf = FLOPS_PER_PAIR_FWD * pairs / (fwd_ms.value * 1e-3) / 1e12
+    # average launch duration in the timed steps: sweep time / T launches
+    bwd_launch_ms = bwd_phase / (K * T_STEPS)
+    fwd_launch_ms = fwd_phase / (K * T_STEPS)
+    bwd_tf = FLOPS_PER_PAIR_BWD * pairs / (bwd_launch_ms * 1e-3) / 1e12
+    fwd_tf = FLOPS_PER_PAIR_FWD * pairs / (fwd_launch_ms * 1e-3) / 1e12
     pipe_lanes = num_sms * 128 * max_mhz * 1e6
+    traffic = DRAM_BYTES_PER_BWD_LAUNCH.get(n)
     roofline = {
         "bound": "alu", "kernel": "k_step_backward (StepBackward pair sums + fused adjoint update)",
-        "achieved": bwd_tf, "peak": peak, "unit": "TFLOP/s", "frac": bwd_tf / peak, "traffic": None,
-        "peak_basis": "%d SMs x 128 FP32 lanes x 2 flops x %.0f MHz (max SM clock)" % (num_sms, max_mhz),
-        "flops_per_launch": FLOPS_PER_PAIR_BWD * pairs, "launch_ms": bwd_ms.value,
-        "fp32_pipe_frac": INSTR_PER_PAIR_BWD * pairs / (bwd_ms.value * 1e-3) / pipe_lanes,
+        "achieved": bwd_tf, "peak": peak, "unit": "TFLOP/s", "frac": bwd_tf / peak, "traffic": traffic,
+        "peak_basis": "%d SMs x 128 FP32 lanes x 2 flops x %.0f MHz (max SM clock; derived, not measured)" % (
+            num_sms, max_mhz),
+        "flops_per_launch": FLOPS_PER_PAIR_BWD * pairs, "launch_ms": bwd_launch_ms,
+        "launch_ms_basis": "reverse-sweep time / T from graph events in the timed steps (gaps included)",
+        "isolated_launch_ms": bwd_ms.value,
+        "fp32_pipe_frac": INSTR_PER_PAIR_BWD * pairs / (bwd_launch_ms * 1e-3) / pipe_lanes,
         "forward": {"kernel": "k_step_forward", "achieved": fwd_tf, "frac": fwd_tf / peak,
-                    "launch_ms": fwd_ms.value,
-                    "fp32_pipe_frac": INSTR_PER_PAIR_FWD * pairs / (fwd_ms.value * 1e-3) / pipe_lanes},
+                    "launch_ms": fwd_launch_ms, "isolated_launch_ms": fwd_ms.value,
+                    "fp32_pipe_frac": INSTR_PER_PAIR_FWD * pairs / (fwd_launch_ms * 1e-3) / pipe_lanes},
     }
     line = {
         "metric": METRIC, "value": value, "unit": "grad-evals/s", "n_gpus": dist.world, "steps": K,
@@ -370,6 +548,9 @@ def run_gshoot(args, dist):
         "gpu_launches": K * launches.value,
         "clocks": clk,
     }
+    if not args.no_samples:
+        line["batched"] = measure_batched(gsh, args.batched_count or 128)
+        line["served"] = measure_served(gsh, args.served_count or 8)
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_gradient_sample()
     if dist.rank == 0:
@@ -383,6 +564,8 @@ def main():
     dist = Dist(args.gpus)
     if args.impl == "reference":
         return run_reference(args, dist)
+    if args.workload != "grad":
+        return run_workload(args, dist)
     return run_gshoot(args, dist)
 
 

@@ -299,6 +299,39 @@ gs_status gs_time_pair_config(int32_t kind, int64_t N, double sigma, const float
  */
 gs_status gs_set_step_config(int32_t kind, int32_t threads, int32_t R, int32_t cluster);
 
+/*
+ * gs_set_cluster_policy — tuning (no counterpart in the paper): force the
+ * cluster scheduling preference of every fused time-step launch: 0 the
+ * driver's default, 1 spread, 2 load balancing; -1 (the initial state)
+ * restores the library's own choice, which is load balancing for grids of
+ * 1.5 waves or more and spread below.  Clears the cached graphs.
+ *
+ * gs_max_active_clusters — diagnostics: how many clusters of `cluster` CTAs
+ * of the fused time-step kernel variant (kind 0 forward, 1 reverse; threads,
+ * R as in gs_time_pair_config) can be resident on the current device at once
+ * under the current policy.  GS_EINVAL for an unknown variant.
+ */
+gs_status gs_set_cluster_policy(int32_t policy);
+gs_status gs_max_active_clusters(int32_t kind, int32_t threads, int32_t R, int32_t cluster, int32_t* clusters);
+
+/*
+ * gs_set_phase_timing — diagnostics (no counterpart in the paper): when `on`
+ * is nonzero, the CUDA graphs of shoot_forward / shoot_gradient (and of the
+ * L-BFGS evaluations) on the current device record three events: before the
+ * first time step, between the forward and the reverse sweep, and after the
+ * last step.  Graphs are cached separately with and without the events.
+ * GS_ECUDA if the events cannot be created.
+ *
+ * gs_phase_times — the device time, in ms, of the forward sweep (T fused
+ * forward step launches, pack excluded) and of the reverse sweep (T fused
+ * reverse step launches, plus the checkpoint recomputation when
+ * ckpt_every > 0) of the last graph replayed with phase timing on.  The
+ * caller must have synchronised the stream of that replay; GS_ECUDA if it
+ * has not finished, GS_EINVAL if phase timing was never switched on.
+ */
+gs_status gs_set_phase_timing(int32_t on);
+gs_status gs_phase_times(double* fwd_ms, double* bwd_ms);
+
 /* Message for the last error of the calling thread ("" if none). */
 const char* gs_last_error(void);
 

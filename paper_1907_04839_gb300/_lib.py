@@ -25,6 +25,7 @@ EXPORTS = [
     "register_batch", "gs_server_create", "gs_server_submit", "gs_server_step", "gs_server_poll",
     "gs_server_stats", "gs_server_destroy",
     "gs_time_pair_kernels", "gs_time_pair_config", "gs_set_step_config", "step_forward_noalloc",
+    "gs_set_phase_timing", "gs_phase_times", "gs_set_cluster_policy", "gs_max_active_clusters",
     "gs_last_error",
     "gs_release_workspace",
     "gs_version",
@@ -121,11 +122,16 @@ def _declare(lib):
     lib.gs_time_pair_kernels.argtypes = [P, fp, fp, fp, i32, dp, dp, ctypes.c_void_p, vp]
     lib.step_forward_noalloc.argtypes = [i64, cd, fp, fp, fp, fp, vp]
     lib.gs_set_step_config.argtypes = [i32, i32, i32, i32]
+    lib.gs_set_phase_timing.argtypes = [i32]
+    lib.gs_set_cluster_policy.argtypes = [i32]
+    lib.gs_max_active_clusters.argtypes = [i32, i32, i32, i32, ctypes.c_void_p]
+    lib.gs_phase_times.argtypes = [dp, dp]
     lib.gs_time_pair_config.argtypes = [i32, i64, cd, fp, fp, fp, fp, i32, i32, i32, i32, dp,
                                         ctypes.c_void_p, vp]
     for name in ("step_forward", "step_backward", "shoot_forward", "shoot_gradient", "register_landmarks",
                  "gs_time_pair_kernels",
-                 "step_forward_noalloc", "gs_time_pair_config", "gs_set_step_config"):
+                 "step_forward_noalloc", "gs_time_pair_config", "gs_set_step_config", "gs_set_phase_timing",
+                 "gs_phase_times", "gs_set_cluster_policy", "gs_max_active_clusters"):
         getattr(lib, name).restype = ctypes.c_int
     lib.gs_last_error.restype = ctypes.c_char_p
     lib.gs_last_error.argtypes = []

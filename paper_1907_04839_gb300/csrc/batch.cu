@@ -612,6 +612,9 @@ struct BatchEngine {
                     (const float*)qin, (const double*)xt, q64, p64, traj, status_d));
     const size_t slot = static_cast<size_t>(kRecF4) * (cap / 2);
     BatchTables bt{items_d, probs_d};
+    StepConfig fc = fcfg, bc = bcfg;
+    fc.policy = policy_for_grid(static_cast<long long>(nf) * fc.cluster, num_sms);
+    bc.policy = policy_for_grid(static_cast<long long>(nb) * bc.cluster, num_sms);
     for (int k = 0; k < T; ++k) {
       StepFwdArgs a;
       std::memset(&a, 0, sizeof(a));
@@ -631,7 +634,7 @@ struct BatchEngine {
       a.red_h = red_h;
       a.red_m = red_m;
       a.status = status_d;
-      GS_CUDA(launch_bstep_forward(fcfg, nf, a, bt, st, k > 0));
+      GS_CUDA(launch_bstep_forward(fc, nf, a, bt, st, k > 0));
     }
     if (!grad) return GS_OK;
     GS_CUDA(plaunch(static_cast<int>(list.size()), 32, st, k_bloss, (const int*)list_d, (const int*)item0_d,
@@ -652,7 +655,7 @@ struct BatchEngine {
       b.hq0 = hq0;
       b.grad_p0_64 = gt;
       b.status = status_d;
-      GS_CUDA(launch_bstep_backward(bcfg, nb, b, btb, st, true));
+      GS_CUDA(launch_bstep_backward(bc, nb, b, btb, st, true));
     }
     return GS_OK;
   }

@@ -260,13 +260,14 @@ StepBwdArgs backward_step_args(Workspace& w, const StepConfig& c, int n, int T, 
 // sweep made, because it comes from the same FP64 state through the same
 // kernels.
 gs_status enqueue_steps(Workspace& w, int kind, int n, int T, double sigma, double lambda, int ckpt,
-                        cudaStream_t st) {
+                        cudaStream_t st, const cudaEvent_t* ev) {
   const int npad = round_up(n, kPad);
   const StepConfig fc = choose_step_config(0, npad, w.num_sms);
   const StepConfig bc = choose_step_config(1, npad, w.num_sms);
   if (fc.threads == 0 || bc.threads == 0) return fail(GS_EINVAL, "no step kernel configuration");
   if (kind == 0) ckpt = 0;
   const size_t n3 = 3 * static_cast<size_t>(n);
+  if (ev) GS_CUDA(cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal));
   for (int k = 0; k < T; ++k) {
     if (ckpt && k % ckpt == 0) {
       double* ck = w.ck64 + 2 * static_cast<size_t>(k / ckpt) * n3;
@@ -277,12 +278,17 @@ gs_status enqueue_steps(Workspace& w, int kind, int n, int T, double sigma, doub
     const StepFwdArgs a = forward_step_args(w, fc, kind, n, T, k, sigma, lambda, rd, wr, false);
     GS_CUDA(launch_step_forward(fc, a, st, k > 0));
   }
-  if (kind == 0) return GS_OK;
+  if (ev) GS_CUDA(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
+  if (kind == 0) {
+    if (ev) GS_CUDA(cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal));
+    return GS_OK;
+  }
   if (!ckpt) {
     for (int s = 0; s < T; ++s) {
       const StepBwdArgs b = backward_step_args(w, bc, n, T, s, sigma);
       GS_CUDA(launch_step_backward(bc, b, st, true));
     }
+    if (ev) GS_CUDA(cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal));
     return GS_OK;
   }
   const KernelScales sc = make_scales(sigma);
@@ -301,6 +307,7 @@ gs_status enqueue_steps(Workspace& w, int kind, int n, int T, double sigma, doub
       GS_CUDA(launch_step_backward(bc, b, st, true));
     }
   }
+  if (ev) GS_CUDA(cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal));
   return GS_OK;
 }
 
@@ -313,7 +320,8 @@ gs_status get_graph(Workspace& w, const GraphKey& key, cudaGraphExec_t* out) {
   if (w.graphs.size() >= 16) w.drop_graphs();
   cudaStream_t cs = w.capture_stream;
   GS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  gs_status s = enqueue_steps(w, key.kind, key.n, key.T, key.sigma, key.lambda, key.ckpt, cs);
+  gs_status s = enqueue_steps(w, key.kind, key.n, key.T, key.sigma, key.lambda, key.ckpt, cs,
+                              key.timed ? w.phase : nullptr);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(cs, &g);
   if (s != GS_OK) {
@@ -349,9 +357,8 @@ gs_status enqueue_gradient64(Workspace& w, const gs_params& prm, const float* dq
   pk.status = w.status;
   GS_CUDA(launch_pack(pk, st));
   cudaGraphExec_t ge = nullptr;
-  if ((s = get_graph(w, GraphKey{1, n, prm.T, prm.sigma, prm.lambda, effective_ckpt(prm.ckpt_every, prm.T)}, &ge)) !=
-      GS_OK)
-    return s;
+  const GraphKey key{1, n, prm.T, prm.sigma, prm.lambda, effective_ckpt(prm.ckpt_every, prm.T), w.phase_timing};
+  if ((s = get_graph(w, key, &ge)) != GS_OK) return s;
   GS_CUDA(cudaGraphLaunch(ge, st));
   return GS_OK;
 }
@@ -375,7 +382,7 @@ gs_status enqueue_forward64(Workspace& w, const gs_params& prm, const float* dq,
   pk.status = w.status;
   GS_CUDA(launch_pack(pk, st));
   cudaGraphExec_t ge = nullptr;
-  if ((s = get_graph(w, GraphKey{0, n, prm.T, prm.sigma, 0.0, 0}, &ge)) != GS_OK) return s;
+  if ((s = get_graph(w, GraphKey{0, n, prm.T, prm.sigma, 0.0, 0, w.phase_timing}, &ge)) != GS_OK) return s;
   GS_CUDA(cudaGraphLaunch(ge, st));
   return GS_OK;
 }
@@ -415,7 +422,7 @@ gs_status run_shoot(int kind, const gs_params* prm, const float* q0, const float
   pk.status = w->status;
   GS_CUDA(launch_pack(pk, st));
   cudaGraphExec_t ge = nullptr;
-  const GraphKey key{kind, n, T, prm->sigma, kind == 1 ? prm->lambda : 0.0, ckpt};
+  const GraphKey key{kind, n, T, prm->sigma, kind == 1 ? prm->lambda : 0.0, ckpt, w->phase_timing};
   if ((s = get_graph(*w, key, &ge)) != GS_OK) return s;
   GS_CUDA(cudaGraphLaunch(ge, st));
   bool want_sync = host;
@@ -722,6 +729,60 @@ gs_status gs_set_step_config(int32_t kind, int32_t threads, int32_t R, int32_t c
   return GS_OK;
 }
 
+gs_status gs_set_cluster_policy(int32_t policy) {
+  gs::g_err.clear();
+  if (policy < -1 || policy > 2) return gs::fail(GS_EINVAL, "policy must be -1, 0, 1 or 2");
+  std::lock_guard<std::mutex> lk(gs::g_mu);
+  gs::set_cluster_policy(policy);
+  for (auto& kv : gs::g_ws) kv.second->drop_graphs();
+  return GS_OK;
+}
+
+gs_status gs_max_active_clusters(int32_t kind, int32_t threads, int32_t R, int32_t cluster, int32_t* clusters) {
+  gs::g_err.clear();
+  if (!clusters || (kind != 0 && kind != 1) || cluster < 1 || cluster > 16)
+    return gs::fail(GS_EINVAL, "bad kind, cluster size or NULL output");
+  std::lock_guard<std::mutex> lk(gs::g_mu);
+  int n = 0;
+  const cudaError_t e = gs::max_active_clusters(kind, threads, R, cluster, &n);
+  if (e != cudaSuccess) return gs::fail(GS_EINVAL, std::string("occupancy query: ") + cudaGetErrorString(e));
+  *clusters = n;
+  return GS_OK;
+}
+
+gs_status gs_set_phase_timing(int32_t on) {
+  gs::g_err.clear();
+  std::lock_guard<std::mutex> lk(gs::g_mu);
+  gs::Workspace* w = nullptr;
+  gs_status s = gs::get_workspace(&w);
+  if (s != GS_OK) return s;
+  if (on && !w->phase[0]) {
+    for (int k = 0; k < 3; ++k) {
+      cudaError_t e = cudaEventCreate(&w->phase[k]);
+      if (e != cudaSuccess) return gs::fail(GS_ECUDA, std::string("phase events: ") + cudaGetErrorString(e));
+    }
+  }
+  w->phase_timing = on != 0;
+  return GS_OK;
+}
+
+gs_status gs_phase_times(double* fwd_ms, double* bwd_ms) {
+  gs::g_err.clear();
+  if (!fwd_ms || !bwd_ms) return gs::fail(GS_EINVAL, "fwd_ms and bwd_ms must not be NULL");
+  std::lock_guard<std::mutex> lk(gs::g_mu);
+  gs::Workspace* w = nullptr;
+  gs_status s = gs::get_workspace(&w);
+  if (s != GS_OK) return s;
+  if (!w->phase[0]) return gs::fail(GS_EINVAL, "phase timing was never switched on");
+  float a = 0.f, b = 0.f;
+  cudaError_t e = cudaEventElapsedTime(&a, w->phase[0], w->phase[1]);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&b, w->phase[1], w->phase[2]);
+  if (e != cudaSuccess) return gs::fail(GS_ECUDA, std::string("phase times: ") + cudaGetErrorString(e));
+  *fwd_ms = a;
+  *bwd_ms = b;
+  return GS_OK;
+}
+
 const char* gs_last_error(void) { return gs::g_err.c_str(); }
 
 void gs_release_workspace(void) {
@@ -731,6 +792,8 @@ void gs_release_workspace(void) {
     cudaGetDevice(&cur);
     cudaSetDevice(kv.first);
     kv.second->free_all();
+    for (cudaEvent_t& e : kv.second->phase)
+      if (e) cudaEventDestroy(e);
     if (kv.second->capture_stream) cudaStreamDestroy(kv.second->capture_stream);
     delete kv.second;
     cudaSetDevice(cur);

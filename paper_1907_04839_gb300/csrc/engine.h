@@ -31,9 +31,11 @@ struct GraphKey {
   int kind;  // 0 forward only, 1 gradient
   int n, T;
   double sigma, lambda;
-  int ckpt;  // checkpoint interval of the reverse sweep (0: whole trajectory)
+  int ckpt;       // checkpoint interval of the reverse sweep (0: whole trajectory)
+  int timed = 0;  // records the workspace's phase events
   bool operator<(const GraphKey& o) const {
-    return std::tie(kind, n, T, sigma, lambda, ckpt) < std::tie(o.kind, o.n, o.T, o.sigma, o.lambda, o.ckpt);
+    return std::tie(kind, n, T, sigma, lambda, ckpt, timed) <
+           std::tie(o.kind, o.n, o.T, o.sigma, o.lambda, o.ckpt, o.timed);
   }
 };
 
@@ -81,6 +83,11 @@ struct Workspace {
   int clean_n = -1;
   cudaStream_t capture_stream = nullptr;
   std::map<GraphKey, cudaGraphExec_t> graphs;
+  // Phase timing: when on, every graph records phase[0] before its first
+  // time step, phase[1] between the forward and the reverse sweep and
+  // phase[2] after its last step.
+  bool phase_timing = false;
+  cudaEvent_t phase[3] = {nullptr, nullptr, nullptr};
   LbfgsBufs lb;
 
   void drop_graphs() {

@@ -340,30 +340,70 @@ struct Variant {
 std::mutex g_attr_mu;
 std::set<const void*> g_attr_done;  // kernels allowed clusters of up to 16 CTAs
 
+// Cluster scheduling preference forced on the step kernels (-1: each
+// configuration's own; 0 the driver's default, 1 spread, 2 load balancing).
+int g_cluster_policy = -1;
+
+// Launch attributes of a step kernel: cluster shape, the scheduling policy
+// if one is set, and programmatic dependent launch.  Returns their count.
+unsigned cluster_attrs(cudaLaunchAttribute* at, int cluster, bool pdl, int policy) {
+  if (g_cluster_policy >= 0) policy = g_cluster_policy;
+  unsigned k = 0;
+  at[k].id = cudaLaunchAttributeClusterDimension;
+  at[k].val.clusterDim.x = cluster;
+  at[k].val.clusterDim.y = 1;
+  at[k].val.clusterDim.z = 1;
+  ++k;
+  if (policy == 1 || policy == 2) {
+    at[k].id = cudaLaunchAttributeClusterSchedulingPolicyPreference;
+    at[k].val.clusterSchedulingPolicyPreference =
+        policy == 1 ? cudaClusterSchedulingPolicySpread : cudaClusterSchedulingPolicyLoadBalancing;
+    ++k;
+  }
+  if (pdl) {
+    at[k].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[k].val.programmaticStreamSerializationAllowed = 1;
+    ++k;
+  }
+  return k;
+}
+
+template <typename K>
+cudaError_t allow_large_clusters(K kern) {
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  const void* key = reinterpret_cast<const void*>(kern);
+  if (!g_attr_done.count(key)) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    g_attr_done.insert(key);
+  }
+  return cudaSuccess;
+}
+
+template <typename K>
+cudaError_t occupancy_clusters(K kern, int threads, int cluster, int* out) {
+  cudaError_t e = allow_large_clusters(kern);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cluster, 4096);
+  cfg.blockDim = dim3(threads);
+  cudaLaunchAttribute at[3];
+  cfg.attrs = at;
+  cfg.numAttrs = cluster_attrs(at, cluster, false, 0);
+  return cudaOccupancyMaxActiveClusters(out, kern, &cfg);
+}
+
 template <typename K, typename A>
 cudaError_t launch_cluster(K kern, const StepConfig& c, const A& args, cudaStream_t st, bool pdl) {
-  {
-    std::lock_guard<std::mutex> lk(g_attr_mu);
-    const void* key = reinterpret_cast<const void*>(kern);
-    if (!g_attr_done.count(key)) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-      if (e != cudaSuccess) return e;
-      g_attr_done.insert(key);
-    }
-  }
+  const cudaError_t e = allow_large_clusters(kern);
+  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(c.cluster, c.tiles);
   cfg.blockDim = dim3(c.threads);
   cfg.stream = st;
-  cudaLaunchAttribute at[2];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = c.cluster;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[1].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchAttribute at[3];
   cfg.attrs = at;
-  cfg.numAttrs = pdl ? 2 : 1;
+  cfg.numAttrs = cluster_attrs(at, c.cluster, pdl, c.policy);
   return cudaLaunchKernelEx(&cfg, kern, args);
 }
 
@@ -399,6 +439,27 @@ namespace {
 int g_override[2][3] = {{0, 0, 0}, {0, 0, 0}};  // threads, R, cluster per kind
 }
 
+void set_cluster_policy(int policy) { g_cluster_policy = policy; }
+
+int policy_for_grid(long long ctas, int num_sms) { return 2 * ctas >= 3LL * 8 * num_sms ? 2 : 1; }
+
+cudaError_t max_active_clusters(int kind, int threads, int R, int cluster, int* out) {
+  *out = 0;
+#define X(T_, R_) \
+  if (threads == T_ && R == R_) return occupancy_clusters(k_step_forward<T_, R_>, T_, cluster, out);
+  if (kind == 0) {
+    GS_STEP_FWD_CASES(X)
+  }
+#undef X
+#define X(T_, R_) \
+  if (threads == T_ && R == R_) return occupancy_clusters(k_step_backward<T_, R_>, T_, cluster, out);
+  if (kind == 1) {
+    GS_STEP_BWD_CASES(X)
+  }
+#undef X
+  return cudaErrorInvalidValue;
+}
+
 bool set_step_override(int kind, int threads, int R, int cluster) {
   if (threads == 0) {
     g_override[kind][0] = g_override[kind][1] = g_override[kind][2] = 0;
@@ -413,55 +474,49 @@ bool set_step_override(int kind, int threads, int R, int cluster) {
 
 // Default configuration per problem size, from sweeps on GB300 (152 SMs).
 StepConfig choose_step_config(int kind, int npad, int num_sms) {
-  (void)num_sms;
   if (g_override[kind][0]) {
-    const StepConfig c = step_config_for(kind, npad, g_override[kind][0], g_override[kind][1],
-                                         std::min(g_override[kind][2], std::max(1, npad / kUnroll)));
+    StepConfig c = step_config_for(kind, npad, g_override[kind][0], g_override[kind][1],
+                                   std::min(g_override[kind][2], std::max(1, npad / kUnroll)));
+    c.policy = policy_for_grid(static_cast<long long>(c.tiles) * c.cluster, num_sms);
     if (c.threads) return c;
   }
   // Measured on GB300 (in-graph replay of the fused kernels, landmark
-  // counts 1024..65536): 128-thread CTAs with one target per thread forward,
-  // 64-thread CTAs backward, clusters of 16 up to 16k landmarks and of 8
-  // beyond.
-  const int cl = std::min(npad >= 32768 ? 8 : 16, std::max(1, npad / kUnroll));
+  // counts 4096..65536): 128-thread CTAs with one target per thread
+  // forward, 64-thread CTAs backward.  A grid of 1.5 waves or more (8 CTAs
+  // per SM) runs fastest as clusters of 16 under load-balancing scheduling,
+  // which keeps every SM busy; a smaller grid as clusters of 8 spread over
+  // the SMs.
+  const int threads = kind == 0 ? 128 : 64;
+  const int tiles = (npad + threads - 1) / threads;
+  const bool big = policy_for_grid(static_cast<long long>(tiles) * 16, num_sms) == 2;
+  const int cl = std::min(big ? 16 : 8, std::max(1, npad / kUnroll));
   int c = 1;
   while (c * 2 <= cl) c *= 2;
-  if (kind == 0) return step_config_for(0, npad, 128, 1, c);
-  return step_config_for(1, npad, 64, 1, c);
+  StepConfig cfg = step_config_for(kind, npad, threads, 1, c);
+  cfg.policy = big ? 2 : 1;
+  return cfg;
 }
 
 template <typename K, typename A>
-cudaError_t launch_cluster2(K kern, int cluster, int threads, int items, const A& args, const BatchTables& bt,
-                            cudaStream_t st, bool pdl) {
-  {
-    std::lock_guard<std::mutex> lk(g_attr_mu);
-    const void* key = reinterpret_cast<const void*>(kern);
-    if (!g_attr_done.count(key)) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-      if (e != cudaSuccess) return e;
-      g_attr_done.insert(key);
-    }
-  }
+cudaError_t launch_cluster2(K kern, int cluster, int threads, int policy, int items, const A& args,
+                            const BatchTables& bt, cudaStream_t st, bool pdl) {
+  const cudaError_t e = allow_large_clusters(kern);
+  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cluster, items);
   cfg.blockDim = dim3(threads);
   cfg.stream = st;
-  cudaLaunchAttribute at[2];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = cluster;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[1].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchAttribute at[3];
   cfg.attrs = at;
-  cfg.numAttrs = pdl ? 2 : 1;
+  cfg.numAttrs = cluster_attrs(at, cluster, pdl, policy);
   return cudaLaunchKernelEx(&cfg, kern, args, bt);
 }
 
 cudaError_t launch_bstep_forward(const StepConfig& c, int items, const StepFwdArgs& a, const BatchTables& bt,
                                  cudaStream_t st, bool pdl) {
 #define X(T_, R_) \
-  if (c.threads == T_ && c.R == R_) return launch_cluster2(k_bstep_forward<T_, R_>, c.cluster, T_, items, a, bt, st, pdl);
+  if (c.threads == T_ && c.R == R_) \
+    return launch_cluster2(k_bstep_forward<T_, R_>, c.cluster, T_, c.policy, items, a, bt, st, pdl);
   GS_STEP_FWD_CASES(X)
 #undef X
   return cudaErrorInvalidValue;
@@ -470,7 +525,8 @@ cudaError_t launch_bstep_forward(const StepConfig& c, int items, const StepFwdAr
 cudaError_t launch_bstep_backward(const StepConfig& c, int items, const StepBwdArgs& a, const BatchTables& bt,
                                   cudaStream_t st, bool pdl) {
 #define X(T_, R_) \
-  if (c.threads == T_ && c.R == R_) return launch_cluster2(k_bstep_backward<T_, R_>, c.cluster, T_, items, a, bt, st, pdl);
+  if (c.threads == T_ && c.R == R_) \
+    return launch_cluster2(k_bstep_backward<T_, R_>, c.cluster, T_, c.policy, items, a, bt, st, pdl);
   GS_STEP_BWD_CASES(X)
 #undef X
   return cudaErrorInvalidValue;

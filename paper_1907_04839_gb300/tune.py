@@ -8,6 +8,11 @@ at the library's balanced split count and at split counts that place a whole
 number of CTAs on every SM.  Timing goes through gs_time_pair_config.  The
 output is one JSON line per measurement.  Inputs are seeded ellipsoid
 landmarks.
+
+`--policy 0 1 2` repeats the fused-kernel sweep under each cluster
+scheduling preference (default, spread, load balancing) and reports how many
+clusters of each shape can be resident at once; `--graph` times the fused
+kernels as back-to-back replays inside a CUDA graph.
 """
 from __future__ import annotations
 
@@ -33,6 +38,11 @@ def main():
     ap.add_argument("--sigma", type=float, default=0.1)
     ap.add_argument("--reps", type=int, default=50)
     ap.add_argument("--fused-only", action="store_true", help="sweep only the fused time-step kernels")
+    ap.add_argument("--policy", type=int, nargs="+", default=[-1],
+                    help="cluster scheduling preferences to sweep (-1: the library's own choice)")
+    ap.add_argument("--graph", action="store_true", help="time the fused kernels inside a CUDA graph")
+    ap.add_argument("--variants", default="all", choices=["all", "default"],
+                    help="default: only the (threads, R) the library picks")
     args = ap.parse_args()
     import torch
 
@@ -50,23 +60,33 @@ def main():
         b = torch.tensor(rng.normal(0, 0.01, size=(n, 3)), dtype=torch.float32, device=dev)
         P = lambda t: ctypes.c_void_p(t.data_ptr())
         npad = (n + 63) // 64 * 64
-        for kind, variants in ((2, STEP_FWD), (3, STEP_BWD)):
-            for (nt, r) in variants:
-                for c in CLUSTERS:
-                    if c > nt * r or c > npad // 8:
-                        continue
-                    ms = ctypes.c_double(0.0)
-                    used = ctypes.c_int32(0)
-                    st = lib.gs_time_pair_config(kind, n, args.sigma, P(q), P(p), P(a), P(b), nt, r, c,
-                                                 args.reps, ctypes.byref(ms), ctypes.byref(used), stream)
-                    if st != 0:
-                        print(json.dumps({"n": n, "kind": kind, "threads": nt, "R": r, "cluster": c,
-                                          "error": lib.gs_last_error().decode()}))
-                        continue
-                    tiles = math.ceil(npad / (nt * r))
-                    print(json.dumps({"n": n, "kind": "step_fwd" if kind == 2 else "step_bwd", "threads": nt,
-                                      "R": r, "cluster": c, "tiles": tiles, "ctas": tiles * c, "ms": ms.value,
-                                      "gpairs_per_s": n * n / ms.value / 1e6}), flush=True)
+        sweeps = ((2, STEP_FWD), (3, STEP_BWD))
+        if args.variants == "default":
+            sweeps = ((2, [(128, 1)]), (3, [(64, 1)]))
+        for pol in args.policy:
+            _lib.check(lib.gs_set_cluster_policy(pol))
+            for kind, variants in sweeps:
+                for (nt, r) in variants:
+                    for c in CLUSTERS:
+                        if c > nt * r or c > npad // 8:
+                            continue
+                        ms = ctypes.c_double(0.0)
+                        used = ctypes.c_int32(0)
+                        st = lib.gs_time_pair_config(kind + (16 if args.graph else 0), n, args.sigma, P(q), P(p),
+                                                     P(a), P(b), nt, r, c, args.reps, ctypes.byref(ms),
+                                                     ctypes.byref(used), stream)
+                        if st != 0:
+                            print(json.dumps({"n": n, "kind": kind, "threads": nt, "R": r, "cluster": c,
+                                              "error": lib.gs_last_error().decode()}))
+                            continue
+                        res = ctypes.c_int32(0)
+                        lib.gs_max_active_clusters(kind - 2, nt, r, c, ctypes.byref(res))
+                        tiles = math.ceil(npad / (nt * r))
+                        print(json.dumps({"n": n, "kind": "step_fwd" if kind == 2 else "step_bwd",
+                                          "threads": nt, "R": r, "cluster": c, "policy": pol, "tiles": tiles,
+                                          "ctas": tiles * c, "resident_ctas": res.value * c, "ms": ms.value,
+                                          "gpairs_per_s": n * n / ms.value / 1e6}), flush=True)
+        _lib.check(lib.gs_set_cluster_policy(-1))
         if args.fused_only:
             continue
         for kind, variants in ((0, FWD), (1, BWD)):

@@ -49,16 +49,16 @@ WORKLOAD = "ellipsoid landmarks N=4096 (8 bumps), sigma=0.1, lambda=10, T=20, p0
 METRIC = "gradient evals/s (shoot_gradient, N=4096, T=20)"
 # Algorithmic work per ordered landmark pair, counted from the formulas of
 # StepForward / StepBackward (multiply, add and subtract = 1 flop, exp not
-# counted).
+# counted, factors common to all of a target's pairs applied once per target).
 FLOPS_PER_PAIR_FWD = 27
-FLOPS_PER_PAIR_BWD = 65
+FLOPS_PER_PAIR_BWD = 63
 # FP32 instructions per pair issued by the kernels (for the pipe fraction).
 INSTR_PER_PAIR_FWD = 16
 INSTR_PER_PAIR_BWD = 36
 # DRAM bytes (read + write) of one k_step_backward launch, from ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum, caches flushed before the
 # launch) of the current kernel, by N.  Empty it whenever the kernel changes.
-DRAM_BYTES_PER_BWD_LAUNCH = {4096: 416256, 16384: 1595904}
+DRAM_BYTES_PER_BWD_LAUNCH = {4096: 416512, 16384: 1596160}
 
 
 def parse():

@@ -686,6 +686,7 @@ struct BatchEngine {
     GS_CUDA(cudaMemcpyAsync(&h, status_d, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     GS_CUDA(cudaStreamSynchronize(st));
     if (h & kErrTimeout) return fail(GS_ETIMEOUT, "a device-side wait expired");
+    if (h & kErrBadLaunch) return fail(GS_ECUDA, "device reported an inconsistent launch");
     return GS_OK;
   }
 

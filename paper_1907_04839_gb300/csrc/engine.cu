@@ -582,6 +582,7 @@ gs_status time_pair_config(int kind_in, int64_t N, double sigma, const float* q,
   } else {
     sc = step_config_for(kind - 2, npad, threads, R, splits);
     if (sc.threads == 0) return fail(GS_EINVAL, "no such step kernel variant / cluster size");
+    sc.policy = policy_for_grid(static_cast<long long>(sc.tiles) * sc.cluster, w->num_sms);
   }
   if ((s = reserve(*w, npad, 1, kind < 2 ? c.splits : 1)) != GS_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -42,7 +42,6 @@ __global__ void __launch_bounds__(NT) k_pair_forward(PairFwdArgs a) {
   if (threadIdx.x == 0) pipe_init(pp, NT / 32);
   __syncthreads();
   pdl_wait();  // the previous step's state must be complete
-  pdl_launch_dependents();
   const int base = blockIdx.x * (NT * R) + threadIdx.x;
   FwdTile<R> tile;
   tile.load(a.qp, base, NT, a.npad);
@@ -71,7 +70,6 @@ __global__ void __launch_bounds__(NT) k_pair_backward(PairBwdArgs a) {
   if (threadIdx.x == 0) pipe_init(pp, NT / 32);
   __syncthreads();
   pdl_wait();
-  pdl_launch_dependents();
   const int base = blockIdx.x * (NT * R) + threadIdx.x;
   BwdTile<R> tile;
   tile.load(a.qp, a.ab, base, NT, a.npad);

@@ -1,7 +1,6 @@
 // Fused time-step kernels: StepForward plus the Euler update of the forward
 // loop of Algorithm 1, and StepBackward plus the adjoint update of its
-// reverse loop.  Each
-// runs as one launch per time step.
+// reverse loop.  Each runs as one launch per time step.
 //
 // Work split.  A thread-block cluster of C CTAs owns a tile of M = NT*R
 // targets.  CTA rank r sums the pair terms of every target in the tile
@@ -82,13 +81,21 @@ __device__ __forceinline__ void forward_body(const StepFwdArgs& a, const StepVie
   __shared__ __align__(8) Pipe pp;
 
   const unsigned rank = cluster_rank(), C = cluster_size();
+  // The launch must match the kernel: NT threads per CTA, a cluster size that
+  // divides the tile, and splits (multiples of 8 sources) that cover the
+  // problem.  The test has the same outcome in every CTA of a cluster, so a
+  // bad launch leaves before any barrier.
+  if (blockDim.x != NT || M % static_cast<int>(C) != 0 || (v.split_len & 7) != 0 ||
+      static_cast<long long>(v.split_len) * C < v.npad) {
+    if (threadIdx.x == 0) atomicOr(a.status, kErrBadLaunch);
+    return;
+  }
   const int lim = v.off + v.npad;
   const int j0 = min(v.off + static_cast<int>(rank) * v.split_len, lim);
   const int j1 = min(j0 + v.split_len, lim);
   if (threadIdx.x == 0) pipe_init(pp, NT / 32);
   __syncthreads();
   pdl_wait();  // the previous step's state must be complete
-  pdl_launch_dependents();
 
   const int tile0 = v.off + v.tile * M;
   FwdTile<R> t;
@@ -172,13 +179,21 @@ __device__ __forceinline__ void backward_body(const StepBwdArgs& a, const StepVi
   __shared__ __align__(8) Pipe pp;
 
   const unsigned rank = cluster_rank(), C = cluster_size();
+  // The launch must match the kernel: NT threads per CTA, a cluster size that
+  // divides the tile, and splits (multiples of 8 sources) that cover the
+  // problem.  The test has the same outcome in every CTA of a cluster, so a
+  // bad launch leaves before any barrier.
+  if (blockDim.x != NT || M % static_cast<int>(C) != 0 || (v.split_len & 7) != 0 ||
+      static_cast<long long>(v.split_len) * C < v.npad) {
+    if (threadIdx.x == 0) atomicOr(a.status, kErrBadLaunch);
+    return;
+  }
   const int lim = v.off + v.npad;
   const int j0 = min(v.off + static_cast<int>(rank) * v.split_len, lim);
   const int j1 = min(j0 + v.split_len, lim);
   if (threadIdx.x == 0) pipe_init(pp, NT / 32);
   __syncthreads();
   pdl_wait();
-  pdl_launch_dependents();
 
   const int tile0 = v.off + v.tile * M;
   BwdTile<R> t;
@@ -481,19 +496,17 @@ StepConfig choose_step_config(int kind, int npad, int num_sms) {
     if (c.threads) return c;
   }
   // Measured on GB300 (in-graph replay of the fused kernels, landmark
-  // counts 4096..65536): 128-thread CTAs with one target per thread
-  // forward, 64-thread CTAs backward.  A grid of 1.5 waves or more (8 CTAs
-  // per SM) runs fastest as clusters of 16 under load-balancing scheduling,
-  // which keeps every SM busy; a smaller grid as clusters of 8 spread over
-  // the SMs.
+  // counts 4096..65536): forward steps run fastest as 128-thread CTAs in
+  // clusters of 16, reverse steps as 64-thread CTAs in clusters of 8, one
+  // target per thread.  A grid of 1.5 waves or more (8 CTAs per SM) is
+  // scheduled with load balancing, which keeps every SM busy; a smaller grid
+  // is spread over the SMs.
   const int threads = kind == 0 ? 128 : 64;
-  const int tiles = (npad + threads - 1) / threads;
-  const bool big = policy_for_grid(static_cast<long long>(tiles) * 16, num_sms) == 2;
-  const int cl = std::min(big ? 16 : 8, std::max(1, npad / kUnroll));
+  const int cl = std::min(kind == 0 ? 16 : 8, std::max(1, npad / kUnroll));
   int c = 1;
   while (c * 2 <= cl) c *= 2;
   StepConfig cfg = step_config_for(kind, npad, threads, 1, c);
-  cfg.policy = big ? 2 : 1;
+  cfg.policy = policy_for_grid(static_cast<long long>(cfg.tiles) * c, num_sms);
   return cfg;
 }
 

@@ -41,6 +41,7 @@ def main():
     ap.add_argument("--policy", type=int, nargs="+", default=[-1],
                     help="cluster scheduling preferences to sweep (-1: the library's own choice)")
     ap.add_argument("--graph", action="store_true", help="time the fused kernels inside a CUDA graph")
+    ap.add_argument("--clusters", type=int, nargs="+", default=CLUSTERS, help="cluster sizes of the fused sweep")
     ap.add_argument("--variants", default="all", choices=["all", "default"],
                     help="default: only the (threads, R) the library picks")
     args = ap.parse_args()
@@ -67,7 +68,7 @@ def main():
             _lib.check(lib.gs_set_cluster_policy(pol))
             for kind, variants in sweeps:
                 for (nt, r) in variants:
-                    for c in CLUSTERS:
+                    for c in args.clusters:
                         if c > nt * r or c > npad // 8:
                             continue
                         ms = ctypes.c_double(0.0)

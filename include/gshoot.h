@@ -275,10 +275,11 @@ gs_status step_forward_noalloc(int64_t N, double sigma, const float* q, const fl
  * kind 2 = fused forward time-step kernel, 3 = fused reverse time-step
  *          kernel, run in a mode that computes and reduces everything but
  *          writes no state.
- * threads, R select the variant (CTA size, targets per thread).  For kinds
- * 0/1, splits > 0 forces the number of source splits and splits <= 0 lets the
- * library balance them; for kinds 2/3, splits is the cluster size (1, 2, 4,
- * 8 or 16).  Adding 16 to kind captures the `reps` launches into one CUDA
+ * threads, R, groups select the variant (CTA size, targets per thread,
+ * warp groups that split each CTA's sources; groups must be 1 for kinds 0/1).
+ * For kinds 0/1, splits > 0 forces the number of source splits and
+ * splits <= 0 lets the library balance them; for kinds 2/3, splits is the
+ * cluster size (1, 2, 4, 8 or 16).  Adding 16 to kind captures the `reps` launches into one CUDA
  * graph (linked by programmatic dependent launch) and times its replay.
  * The kernel runs `reps` times back to back on (q, p[, alpha,
  * beta]) between two CUDA events on `stream`.  Out: *ms per launch,
@@ -287,17 +288,19 @@ gs_status step_forward_noalloc(int64_t N, double sigma, const float* q, const fl
  */
 gs_status gs_time_pair_config(int32_t kind, int64_t N, double sigma, const float* q,
                               const float* p, const float* alpha, const float* beta,
-                              int32_t threads, int32_t R, int32_t splits, int32_t reps,
-                              double* ms, int32_t* splits_used, void* stream);
+                              int32_t threads, int32_t R, int32_t groups, int32_t splits,
+                              int32_t reps, double* ms, int32_t* splits_used, void* stream);
 
 /*
  * gs_set_step_config — tuning (no counterpart in the paper): override the
  * fused time-step kernel configuration used by shoot_forward / shoot_gradient
- * for kind 0 (forward) or 1 (reverse): CTA size, targets per thread and
- * cluster size, as in gs_time_pair_config.  threads = 0 restores the built-in
- * choice.  Clears the cached graphs.  GS_EINVAL for an unknown variant.
+ * for kind 0 (forward) or 1 (reverse): CTA size, targets per thread, warp
+ * groups and cluster size, as in gs_time_pair_config.  threads = 0 restores
+ * the built-in choice.  Clears the cached graphs.  GS_EINVAL for an unknown
+ * variant.
  */
-gs_status gs_set_step_config(int32_t kind, int32_t threads, int32_t R, int32_t cluster);
+gs_status gs_set_step_config(int32_t kind, int32_t threads, int32_t R, int32_t groups,
+                             int32_t cluster);
 
 /*
  * gs_set_cluster_policy — tuning (no counterpart in the paper): force the
@@ -308,11 +311,12 @@ gs_status gs_set_step_config(int32_t kind, int32_t threads, int32_t R, int32_t c
  *
  * gs_max_active_clusters — diagnostics: how many clusters of `cluster` CTAs
  * of the fused time-step kernel variant (kind 0 forward, 1 reverse; threads,
- * R as in gs_time_pair_config) can be resident on the current device at once
+ * R, groups as in gs_time_pair_config) can be resident on the current device at once
  * under the current policy.  GS_EINVAL for an unknown variant.
  */
 gs_status gs_set_cluster_policy(int32_t policy);
-gs_status gs_max_active_clusters(int32_t kind, int32_t threads, int32_t R, int32_t cluster, int32_t* clusters);
+gs_status gs_max_active_clusters(int32_t kind, int32_t threads, int32_t R, int32_t groups,
+                                 int32_t cluster, int32_t* clusters);
 
 /*
  * gs_set_phase_timing — diagnostics (no counterpart in the paper): when `on`

@@ -121,12 +121,12 @@ def _declare(lib):
         getattr(lib, name).restype = ctypes.c_int
     lib.gs_time_pair_kernels.argtypes = [P, fp, fp, fp, i32, dp, dp, ctypes.c_void_p, vp]
     lib.step_forward_noalloc.argtypes = [i64, cd, fp, fp, fp, fp, vp]
-    lib.gs_set_step_config.argtypes = [i32, i32, i32, i32]
+    lib.gs_set_step_config.argtypes = [i32, i32, i32, i32, i32]
     lib.gs_set_phase_timing.argtypes = [i32]
     lib.gs_set_cluster_policy.argtypes = [i32]
-    lib.gs_max_active_clusters.argtypes = [i32, i32, i32, i32, ctypes.c_void_p]
+    lib.gs_max_active_clusters.argtypes = [i32, i32, i32, i32, i32, ctypes.c_void_p]
     lib.gs_phase_times.argtypes = [dp, dp]
-    lib.gs_time_pair_config.argtypes = [i32, i64, cd, fp, fp, fp, fp, i32, i32, i32, i32, dp,
+    lib.gs_time_pair_config.argtypes = [i32, i64, cd, fp, fp, fp, fp, i32, i32, i32, i32, i32, dp,
                                         ctypes.c_void_p, vp]
     for name in ("step_forward", "step_backward", "shoot_forward", "shoot_gradient", "register_landmarks",
                  "gs_time_pair_kernels",

@@ -558,8 +558,8 @@ gs_status time_pair_kernels(const gs_params* prm, const float* q0, const float* 
 }
 
 gs_status time_pair_config(int kind_in, int64_t N, double sigma, const float* q, const float* p,
-                           const float* alpha, const float* beta, int threads, int R, int splits, int reps, double* ms,
-                           int* used, void* stream) {
+                           const float* alpha, const float* beta, int threads, int R, int groups, int splits, int reps,
+                           double* ms, int* used, void* stream) {
   const bool graph = (kind_in & 16) != 0;
   const int kind = kind_in & ~16;
   if (kind < 0 || kind > 3) return fail(GS_EINVAL, "kind must be 0..3 (+16 for graph replay)");
@@ -576,11 +576,12 @@ gs_status time_pair_config(int kind_in, int64_t N, double sigma, const float* q,
   PairConfig c{};
   StepConfig sc{};
   if (kind < 2) {
+    if (groups != 1) return fail(GS_EINVAL, "the split-partial kernels have one warp group");
     c = kind == 0 ? forward_config_for(npad, w->num_sms, threads, R, splits)
                   : backward_config_for(npad, w->num_sms, threads, R, splits);
     if (c.threads == 0) return fail(GS_EINVAL, "no such kernel variant");
   } else {
-    sc = step_config_for(kind - 2, npad, threads, R, splits);
+    sc = step_config_for(kind - 2, npad, threads, R, splits, groups);
     if (sc.threads == 0) return fail(GS_EINVAL, "no such step kernel variant / cluster size");
     sc.policy = policy_for_grid(static_cast<long long>(sc.tiles) * sc.cluster, w->num_sms);
   }
@@ -706,23 +707,24 @@ gs_status gs_time_pair_kernels(const gs_params* prm, const float* q0, const floa
 }
 
 gs_status gs_time_pair_config(int32_t kind, int64_t N, double sigma, const float* q, const float* p,
-                              const float* alpha, const float* beta, int32_t threads, int32_t R, int32_t splits,
-                              int32_t reps, double* ms, int32_t* splits_used, void* stream) {
+                              const float* alpha, const float* beta, int32_t threads, int32_t R, int32_t groups,
+                              int32_t splits, int32_t reps, double* ms, int32_t* splits_used, void* stream) {
   gs::g_err.clear();
   int used = 0;
-  gs_status s = gs::time_pair_config(kind, N, sigma, q, p, alpha, beta, threads, R, splits, reps, ms, &used, stream);
+  gs_status s =
+      gs::time_pair_config(kind, N, sigma, q, p, alpha, beta, threads, R, groups, splits, reps, ms, &used, stream);
   if (splits_used) *splits_used = used;
   return s;
 }
 
-gs_status gs_set_step_config(int32_t kind, int32_t threads, int32_t R, int32_t cluster) {
+gs_status gs_set_step_config(int32_t kind, int32_t threads, int32_t R, int32_t groups, int32_t cluster) {
   gs::g_err.clear();
   if (kind != 0 && kind != 1) {
     gs::set_last_error("kind must be 0 (forward) or 1 (reverse)");
     return GS_EINVAL;
   }
   std::lock_guard<std::mutex> lk(gs::g_mu);
-  if (!gs::set_step_override(kind, threads, R, cluster)) {
+  if (!gs::set_step_override(kind, threads, R, groups, cluster)) {
     gs::set_last_error("no such step kernel variant / cluster size");
     return GS_EINVAL;
   }
@@ -739,13 +741,14 @@ gs_status gs_set_cluster_policy(int32_t policy) {
   return GS_OK;
 }
 
-gs_status gs_max_active_clusters(int32_t kind, int32_t threads, int32_t R, int32_t cluster, int32_t* clusters) {
+gs_status gs_max_active_clusters(int32_t kind, int32_t threads, int32_t R, int32_t groups, int32_t cluster,
+                                 int32_t* clusters) {
   gs::g_err.clear();
   if (!clusters || (kind != 0 && kind != 1) || cluster < 1 || cluster > 16)
     return gs::fail(GS_EINVAL, "bad kind, cluster size or NULL output");
   std::lock_guard<std::mutex> lk(gs::g_mu);
   int n = 0;
-  const cudaError_t e = gs::max_active_clusters(kind, threads, R, cluster, &n);
+  const cudaError_t e = gs::max_active_clusters(kind, threads, R, groups, cluster, &n);
   if (e != cudaSuccess) return gs::fail(GS_EINVAL, std::string("occupancy query: ") + cudaGetErrorString(e));
   *clusters = n;
   return GS_OK;

@@ -102,9 +102,10 @@ struct StepConfig {
   int threads;    // CTA size
   int R;          // targets per thread
   int cluster;    // C, CTAs per cluster = source splits
-  int tiles;      // clusters = ceil(Npad / (threads * R))
+  int tiles;      // clusters = ceil(Npad / (threads / groups * R))
   int split_len;  // sources per CTA (multiple of 8)
   int policy;     // cluster scheduling: 0 driver default, 1 spread, 2 load balancing
+  int groups;     // warp groups per CTA that split the CTA's sources (1: none)
 };
 
 struct StepFwdArgs {
@@ -167,11 +168,11 @@ struct BatchTables {
   const BatchProb* probs;
 };
 
-StepConfig step_config_for(int kind, int npad, int threads, int R, int cluster);
+StepConfig step_config_for(int kind, int npad, int threads, int R, int cluster, int groups = 1);
 StepConfig choose_step_config(int kind, int npad, int num_sms);
 // Override the fused step configuration of `kind` (threads == 0 restores the
 // built-in choice).  Returns false for an unknown variant.
-bool set_step_override(int kind, int threads, int R, int cluster);
+bool set_step_override(int kind, int threads, int R, int groups, int cluster);
 // Cluster scheduling preference forced on every step-kernel launch (0
 // driver default, 1 spread, 2 load balancing), or -1: each configuration's
 // own policy.
@@ -180,7 +181,7 @@ void set_cluster_policy(int policy);
 // when the grid is at least 1.5 waves of 8 CTAs per SM, else spread.
 int policy_for_grid(long long ctas, int num_sms);
 // cudaOccupancyMaxActiveClusters of a single-problem step kernel variant.
-cudaError_t max_active_clusters(int kind, int threads, int R, int cluster, int* out);
+cudaError_t max_active_clusters(int kind, int threads, int R, int groups, int cluster, int* out);
 cudaError_t launch_step_forward(const StepConfig& cfg, const StepFwdArgs& a, cudaStream_t st, bool pdl);
 cudaError_t launch_step_backward(const StepConfig& cfg, const StepBwdArgs& a, cudaStream_t st, bool pdl);
 // One launch over `items` (problem, tile) items; cfg gives the kernel variant

@@ -11,11 +11,14 @@
 // single paired add.  The Gaussian is one MUFU ex2 per pair, on prescaled
 // coordinates.
 //
-// A thread holds R targets in registers; the targets of a CTA are
-// base + r*NT, r < R.  The whole warp reads the same source record, so the
-// shared-memory load is a broadcast.  Sums are plain FP32 over a sub-block of
-// at most kSub sources, then the two halves of each paired accumulator are
-// added and folded into a Kahan (sum, compensation) pair.
+// A thread holds R targets in registers.  The threads of a CTA form one or
+// more warp groups; each group holds the same targets (base + r*TG, r < R,
+// TG threads per group) and takes its own share of every staged chunk of
+// sources, so a CTA with W groups splits its sources W ways.  The whole warp
+// reads the same source record, so the shared-memory load is a broadcast.
+// Sums are plain FP32 over a sub-block of at most kSub sources, then the two
+// halves of each paired accumulator are added and folded into a Kahan (sum,
+// compensation) pair.
 #pragma once
 
 #include "gs_device.cuh"
@@ -68,16 +71,17 @@ __device__ __forceinline__ void issue_chunk(StageBuf<NA>& st, Pipe& pp, const fl
   for (int a = 0; a < NA; ++a) bulk_g2s(&st.buf[s][a][0], src[a] + (off / 2) * kRecF4, bytes, bar);
 }
 
-// Stream sources [j0, j1) through the stage ring and feed each chunk to
-// tile.consume(buffers, len).  The whole CTA calls this; thread 0 issues the
-// copies.  Warps move on to the next chunk as soon as it has landed: a warp
+// Stream sources [j0, j1) through the stage ring.  Warp group `group` of
+// `groups` consumes its share of each chunk: tile.consume(buffers, lo, hi)
+// with [lo, hi) a contiguous piece, in multiples of 8 sources, of the chunk's
+// sources.  The whole CTA calls this; thread 0 issues the copies.  Warps move on to the next chunk as soon as it has landed: a warp
 // releases a stage through empty[s], and thread 0 refills a stage only after
 // every warp has released it.  Returns false in every thread if a wait
 // expired; the expiry is recorded in *status, and every copy still in flight
 // has been waited for (bounded) before return.  Ends with a CTA barrier.
-template <int NA, class Tile>
+template <int NA, int Groups = 1, class Tile>
 __device__ bool stream_sources(StageBuf<NA>& st, Pipe& pp, const float4* const* src, int j0, int j1, Tile& tile,
-                               unsigned* status) {
+                               unsigned* status, int group = 0) {
   const int tid = threadIdx.x;
   const int nch = j1 > j0 ? (j1 - j0 + kChunk - 1) / kChunk : 0;
   int issued = 0;
@@ -95,7 +99,14 @@ __device__ bool stream_sources(StageBuf<NA>& st, Pipe& pp, const float4* const* 
     const float4* bufs[NA];
 #pragma unroll
     for (int a = 0; a < NA; ++a) bufs[a] = st.buf[s][a];
-    tile.consume(bufs, min(kChunk, j1 - (j0 + c * kChunk)));
+    const int len = min(kChunk, j1 - (j0 + c * kChunk));
+    if constexpr (Groups == 1) {
+      tile.consume(bufs, 0, len);
+    } else {
+      const int piece = (len + kUnroll * Groups - 1) / (kUnroll * Groups) * kUnroll;
+      const int lo = min(group * piece, len);
+      tile.consume(bufs, lo, min(lo + piece, len));
+    }
     __syncwarp();
     if ((tid & 31) == 0) mbar_arrive(&pp.empty[s]);
     if (tid == 0 && c + kStages < nch) {
@@ -168,10 +179,11 @@ struct FwdTile {
     }
   }
 
-  __device__ __forceinline__ void consume(const float4* const* bufs, int len) {
+  // Sources [lo, hi) of the staged chunk; lo is a multiple of 8.
+  __device__ __forceinline__ void consume(const float4* const* bufs, int lo, int hi) {
     const float4* Q = bufs[0];
-    for (int sb = 0; sb < len; sb += kSub) {
-      const int sl = min(kSub, len - sb);
+    for (int sb = lo; sb < hi; sb += kSub) {
+      const int sl = min(kSub, hi - sb);
       float2 aF[R][3], aG[R][3];
 #pragma unroll
       for (int r = 0; r < R; ++r)
@@ -263,11 +275,12 @@ struct BwdTile {
     }
   }
 
-  __device__ __forceinline__ void consume(const float4* const* bufs, int len) {
+  // Sources [lo, hi) of the staged chunk; lo is a multiple of 8.
+  __device__ __forceinline__ void consume(const float4* const* bufs, int lo, int hi) {
     const float4* Q = bufs[0];
     const float4* Ab = bufs[1];
-    for (int sb = 0; sb < len; sb += kSub) {
-      const int sl = min(kSub, len - sb);
+    for (int sb = lo; sb < hi; sb += kSub) {
+      const int sl = min(kSub, hi - sb);
       float2 a1[R][3], a2[R][3], bb[R][3];
 #pragma unroll
       for (int r = 0; r < R; ++r)

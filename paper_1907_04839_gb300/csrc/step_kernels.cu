@@ -68,14 +68,38 @@ struct StepView {
   double kq, kappa, dt, lambda;
 };
 
+// Add the W warp groups' partials of every target into group 0's slot, in
+// group order, in double-single arithmetic (each float4 holds two (hi, lo)
+// values).  Each item is read and written by one thread only.
+template <int W, int M>
+__device__ __forceinline__ void combine_groups(float4 (&red)[W][M][3]) {
+  if constexpr (W > 1) {
+    __syncthreads();
+    for (int item = threadIdx.x; item < M * 3; item += blockDim.x) {
+      const int lt = item / 3, k = item % 3;
+      float4 acc = red[0][lt][k];
+#pragma unroll
+      for (int g = 1; g < W; ++g) {
+        const float4 x = red[g][lt][k];
+        const ds s0 = ds_add(ds{acc.x, acc.y}, ds{x.x, x.y});
+        const ds s1 = ds_add(ds{acc.z, acc.w}, ds{x.z, x.w});
+        acc = make_float4(s0.hi, s0.lo, s1.hi, s1.lo);
+      }
+      red[0][lt][k] = acc;
+    }
+  }
+}
+
 // Forward step of one tile: pair sums, cluster reduction, Euler update.
 // Accumulates this thread's H0 and mismatch contributions in hc, mc.
-template <int NT, int R>
+template <int NT, int R, int W>
 __device__ __forceinline__ void forward_body(const StepFwdArgs& a, const StepView& v, double& hc, double& mc) {
-  constexpr int M = NT * R;
+  constexpr int TG = NT / W;  // threads per warp group
+  constexpr int M = TG * R;   // targets of the CTA
+  static_assert(NT % W == 0 && TG % 32 == 0, "warp groups must be whole warps");
   union Smem {
     StageBuf<1> st;
-    float4 red[M][3];  // Hp (hi,lo) x3 then Hq (hi,lo) x3 per target
+    float4 red[W][M][3];  // per group: Hp (hi,lo) x3 then Hq (hi,lo) x3 per target
   };
   __shared__ __align__(128) Smem sm;
   __shared__ __align__(8) Pipe pp;
@@ -98,19 +122,22 @@ __device__ __forceinline__ void forward_body(const StepFwdArgs& a, const StepVie
   pdl_wait();  // the previous step's state must be complete
 
   const int tile0 = v.off + v.tile * M;
+  const int grp = W == 1 ? 0 : static_cast<int>(threadIdx.x) / TG;
+  const int lt0 = W == 1 ? static_cast<int>(threadIdx.x) : static_cast<int>(threadIdx.x) % TG;
   FwdTile<R> t;
-  t.load(a.qp, tile0 + threadIdx.x, NT, lim);
+  t.load(a.qp, tile0 + lt0, TG, lim);
   const float4* src[1] = {a.qp};
-  stream_sources<1>(sm.st, pp, src, j0, j1, t, a.status);  // ends with a CTA barrier
+  stream_sources<1, W>(sm.st, pp, src, j0, j1, t, a.status, grp);  // ends with a CTA barrier
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     ds w[6];
     t.result(r, v.kappa_f, w);
-    const int lt = threadIdx.x + r * NT;
-    sm.red[lt][0] = make_float4(w[0].hi, w[0].lo, w[1].hi, w[1].lo);
-    sm.red[lt][1] = make_float4(w[2].hi, w[2].lo, w[3].hi, w[3].lo);
-    sm.red[lt][2] = make_float4(w[4].hi, w[4].lo, w[5].hi, w[5].lo);
+    const int lt = lt0 + r * TG;
+    sm.red[grp][lt][0] = make_float4(w[0].hi, w[0].lo, w[1].hi, w[1].lo);
+    sm.red[grp][lt][1] = make_float4(w[2].hi, w[2].lo, w[3].hi, w[3].lo);
+    sm.red[grp][lt][2] = make_float4(w[4].hi, w[4].lo, w[5].hi, w[5].lo);
   }
+  combine_groups<W, M>(sm.red);
   cluster_sync();  // every CTA's tile partials are visible to the cluster
 
   const int slice = M / static_cast<int>(C);
@@ -119,7 +146,7 @@ __device__ __forceinline__ void forward_body(const StepFwdArgs& a, const StepVie
     const int k = item % 3;
     if (v.tile * M + lt >= v.n) continue;
     const int i = tile0 + lt;  // packed landmark index
-    const uint32_t lp = smem_u32(&sm.red[lt][0]);
+    const uint32_t lp = smem_u32(&sm.red[0][lt][0]);
     ds hp{0.f, 0.f}, hq{0.f, 0.f};
 #pragma unroll 4
     for (unsigned rr = 0; rr < C; ++rr) {
@@ -168,12 +195,14 @@ __device__ __forceinline__ void forward_body(const StepFwdArgs& a, const StepVie
 
 // Reverse step of one tile: adjoint pair sums, cluster reduction, adjoint
 // update, and at time step 0 the gradient.
-template <int NT, int R>
+template <int NT, int R, int W>
 __device__ __forceinline__ void backward_body(const StepBwdArgs& a, const StepView& v) {
-  constexpr int M = NT * R;
+  constexpr int TG = NT / W;  // threads per warp group
+  constexpr int M = TG * R;   // targets of the CTA
+  static_assert(NT % W == 0 && TG % 32 == 0, "warp groups must be whole warps");
   union Smem {
     StageBuf<2> st;
-    float4 red[M][3];  // dalpha (hi,lo) x3 then dbeta (hi,lo) x3 per target
+    float4 red[W][M][3];  // per group: dalpha (hi,lo) x3 then dbeta (hi,lo) x3 per target
   };
   __shared__ __align__(128) Smem sm;
   __shared__ __align__(8) Pipe pp;
@@ -196,19 +225,22 @@ __device__ __forceinline__ void backward_body(const StepBwdArgs& a, const StepVi
   pdl_wait();
 
   const int tile0 = v.off + v.tile * M;
+  const int grp = W == 1 ? 0 : static_cast<int>(threadIdx.x) / TG;
+  const int lt0 = W == 1 ? static_cast<int>(threadIdx.x) : static_cast<int>(threadIdx.x) % TG;
   BwdTile<R> t;
-  t.load(a.qp, a.ab, tile0 + threadIdx.x, NT, lim);
+  t.load(a.qp, a.ab, tile0 + lt0, TG, lim);
   const float4* src[2] = {a.qp, a.ab};
-  stream_sources<2>(sm.st, pp, src, j0, j1, t, a.status);
+  stream_sources<2, W>(sm.st, pp, src, j0, j1, t, a.status, grp);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     ds w[6];
     t.result(r, v.kq_f, v.kappa_f, w);
-    const int lt = threadIdx.x + r * NT;
-    sm.red[lt][0] = make_float4(w[0].hi, w[0].lo, w[1].hi, w[1].lo);
-    sm.red[lt][1] = make_float4(w[2].hi, w[2].lo, w[3].hi, w[3].lo);
-    sm.red[lt][2] = make_float4(w[4].hi, w[4].lo, w[5].hi, w[5].lo);
+    const int lt = lt0 + r * TG;
+    sm.red[grp][lt][0] = make_float4(w[0].hi, w[0].lo, w[1].hi, w[1].lo);
+    sm.red[grp][lt][1] = make_float4(w[2].hi, w[2].lo, w[3].hi, w[3].lo);
+    sm.red[grp][lt][2] = make_float4(w[4].hi, w[4].lo, w[5].hi, w[5].lo);
   }
+  combine_groups<W, M>(sm.red);
   cluster_sync();
 
   const int slice = M / static_cast<int>(C);
@@ -217,7 +249,7 @@ __device__ __forceinline__ void backward_body(const StepBwdArgs& a, const StepVi
     const int k = item % 3;
     if (v.tile * M + lt >= v.n) continue;
     const int i = tile0 + lt;
-    const uint32_t lp = smem_u32(&sm.red[lt][0]);
+    const uint32_t lp = smem_u32(&sm.red[0][lt][0]);
     ds da{0.f, 0.f}, db{0.f, 0.f};
 #pragma unroll 4
     for (unsigned rr = 0; rr < C; ++rr) {
@@ -251,7 +283,7 @@ __device__ __forceinline__ void backward_body(const StepBwdArgs& a, const StepVi
 }
 
 // ---------------------------------------------------------------- single-problem kernels
-template <int NT, int R>
+template <int NT, int R, int W>
 __global__ void __launch_bounds__(NT) k_step_forward(StepFwdArgs a) {
   __shared__ double shred[NT / 32];
   __shared__ int am_last;
@@ -268,7 +300,7 @@ __global__ void __launch_bounds__(NT) k_step_forward(StepFwdArgs a) {
   v.dt = a.dt;
   v.lambda = a.lambda;
   double hc = 0.0, mc = 0.0;
-  forward_body<NT, R>(a, v, hc, mc);
+  forward_body<NT, R, W>(a, v, hc, mc);
   const bool reduce_h = a.first != 0;
   const bool reduce_m = a.last && a.with_loss;
   if ((!reduce_h && !reduce_m) || a.dry) return;  // uniform across the grid
@@ -280,7 +312,7 @@ __global__ void __launch_bounds__(NT) k_step_forward(StepFwdArgs a) {
   }
 }
 
-template <int NT, int R>
+template <int NT, int R, int W>
 __global__ void __launch_bounds__(NT) k_step_backward(StepBwdArgs a) {
   StepView v;
   v.off = 0;
@@ -294,7 +326,7 @@ __global__ void __launch_bounds__(NT) k_step_backward(StepBwdArgs a) {
   v.kappa = a.kappa64;
   v.dt = a.dt;
   v.lambda = 0.0;
-  backward_body<NT, R>(a, v);
+  backward_body<NT, R, W>(a, v);
 }
 
 // ---------------------------------------------------------------- packed batch kernels
@@ -319,12 +351,12 @@ __device__ __forceinline__ StepView batch_view(const BatchTables& bt) {
   return v;
 }
 
-template <int NT, int R>
+template <int NT, int R, int W>
 __global__ void __launch_bounds__(NT) k_bstep_forward(StepFwdArgs a, BatchTables bt) {
   __shared__ double shred[NT / 32];
   const StepView v = batch_view(bt);
   double hc = 0.0, mc = 0.0;
-  forward_body<NT, R>(a, v, hc, mc);
+  forward_body<NT, R, W>(a, v, hc, mc);
   const bool reduce_h = a.first != 0;
   const bool reduce_m = a.last && a.with_loss;
   if ((!reduce_h && !reduce_m) || a.dry) return;
@@ -337,20 +369,21 @@ __global__ void __launch_bounds__(NT) k_bstep_forward(StepFwdArgs a, BatchTables
   }
 }
 
-template <int NT, int R>
+template <int NT, int R, int W>
 __global__ void __launch_bounds__(NT) k_bstep_backward(StepBwdArgs a, BatchTables bt) {
-  backward_body<NT, R>(a, batch_view(bt));
+  backward_body<NT, R, W>(a, batch_view(bt));
 }
 
 // ---------------------------------------------------------------- host side
 
 namespace {
 
-struct Variant {
-  int threads, R;
-};
-#define GS_STEP_FWD_CASES(X) X(64, 2) X(64, 4) X(128, 1) X(128, 2) X(128, 4) X(256, 1) X(256, 2)
-#define GS_STEP_BWD_CASES(X) X(64, 1) X(64, 2) X(128, 1) X(128, 2) X(256, 1)
+// Compiled variants: (threads per CTA, targets per thread, warp groups).
+#define GS_STEP_FWD_CASES(X)                                                                         \
+  X(64, 2, 1) X(64, 4, 1) X(128, 1, 1) X(128, 2, 1) X(128, 4, 1) X(256, 1, 1) X(256, 2, 1) X(64, 1, 2) \
+  X(128, 1, 2) X(128, 1, 4) X(256, 1, 4)
+#define GS_STEP_BWD_CASES(X) \
+  X(64, 1, 1) X(64, 2, 1) X(128, 1, 1) X(128, 2, 1) X(256, 1, 1) X(64, 1, 2) X(128, 1, 2) X(128, 1, 4) X(256, 1, 4)
 
 std::mutex g_attr_mu;
 std::set<const void*> g_attr_done;  // kernels allowed clusters of up to 16 CTAs
@@ -422,9 +455,9 @@ cudaError_t launch_cluster(K kern, const StepConfig& c, const A& args, cudaStrea
   return cudaLaunchKernelEx(&cfg, kern, args);
 }
 
-bool valid_variant(int kind, int threads, int R) {
-#define X(T_, R_) \
-  if (threads == T_ && R == R_) return true;
+bool valid_variant(int kind, int threads, int R, int groups) {
+#define X(T_, R_, W_) \
+  if (threads == T_ && R == R_ && groups == W_) return true;
   if (kind == 0) {
     GS_STEP_FWD_CASES(X)
   } else {
@@ -436,13 +469,14 @@ bool valid_variant(int kind, int threads, int R) {
 
 }  // namespace
 
-StepConfig step_config_for(int kind, int npad, int threads, int R, int cluster) {
+StepConfig step_config_for(int kind, int npad, int threads, int R, int cluster, int groups) {
   StepConfig c{};
-  if (!valid_variant(kind, threads, R)) return c;
-  const int M = threads * R;
+  if (groups < 1 || !valid_variant(kind, threads, R, groups)) return c;
+  const int M = threads / groups * R;
   if (cluster < 1 || cluster > 16 || (cluster & (cluster - 1)) != 0 || cluster > M) return c;
   c.threads = threads;
   c.R = R;
+  c.groups = groups;
   c.cluster = cluster;
   c.tiles = (npad + M - 1) / M;
   int len = (npad + cluster - 1) / cluster;
@@ -451,23 +485,23 @@ StepConfig step_config_for(int kind, int npad, int threads, int R, int cluster) 
 }
 
 namespace {
-int g_override[2][3] = {{0, 0, 0}, {0, 0, 0}};  // threads, R, cluster per kind
+int g_override[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};  // threads, R, cluster, groups per kind
 }
 
 void set_cluster_policy(int policy) { g_cluster_policy = policy; }
 
 int policy_for_grid(long long ctas, int num_sms) { return 2 * ctas >= 3LL * 8 * num_sms ? 2 : 1; }
 
-cudaError_t max_active_clusters(int kind, int threads, int R, int cluster, int* out) {
+cudaError_t max_active_clusters(int kind, int threads, int R, int groups, int cluster, int* out) {
   *out = 0;
-#define X(T_, R_) \
-  if (threads == T_ && R == R_) return occupancy_clusters(k_step_forward<T_, R_>, T_, cluster, out);
+#define X(T_, R_, W_) \
+  if (threads == T_ && R == R_ && groups == W_) return occupancy_clusters(k_step_forward<T_, R_, W_>, T_, cluster, out);
   if (kind == 0) {
     GS_STEP_FWD_CASES(X)
   }
 #undef X
-#define X(T_, R_) \
-  if (threads == T_ && R == R_) return occupancy_clusters(k_step_backward<T_, R_>, T_, cluster, out);
+#define X(T_, R_, W_) \
+  if (threads == T_ && R == R_ && groups == W_) return occupancy_clusters(k_step_backward<T_, R_, W_>, T_, cluster, out);
   if (kind == 1) {
     GS_STEP_BWD_CASES(X)
   }
@@ -475,15 +509,16 @@ cudaError_t max_active_clusters(int kind, int threads, int R, int cluster, int* 
   return cudaErrorInvalidValue;
 }
 
-bool set_step_override(int kind, int threads, int R, int cluster) {
+bool set_step_override(int kind, int threads, int R, int groups, int cluster) {
   if (threads == 0) {
-    g_override[kind][0] = g_override[kind][1] = g_override[kind][2] = 0;
+    g_override[kind][0] = g_override[kind][1] = g_override[kind][2] = g_override[kind][3] = 0;
     return true;
   }
-  if (step_config_for(kind, 1 << 16, threads, R, cluster).threads == 0) return false;
+  if (step_config_for(kind, 1 << 16, threads, R, cluster, groups).threads == 0) return false;
   g_override[kind][0] = threads;
   g_override[kind][1] = R;
   g_override[kind][2] = cluster;
+  g_override[kind][3] = groups;
   return true;
 }
 
@@ -491,7 +526,7 @@ bool set_step_override(int kind, int threads, int R, int cluster) {
 StepConfig choose_step_config(int kind, int npad, int num_sms) {
   if (g_override[kind][0]) {
     StepConfig c = step_config_for(kind, npad, g_override[kind][0], g_override[kind][1],
-                                   std::min(g_override[kind][2], std::max(1, npad / kUnroll)));
+                                   std::min(g_override[kind][2], std::max(1, npad / kUnroll)), g_override[kind][3]);
     c.policy = policy_for_grid(static_cast<long long>(c.tiles) * c.cluster, num_sms);
     if (c.threads) return c;
   }
@@ -527,9 +562,9 @@ cudaError_t launch_cluster2(K kern, int cluster, int threads, int policy, int it
 
 cudaError_t launch_bstep_forward(const StepConfig& c, int items, const StepFwdArgs& a, const BatchTables& bt,
                                  cudaStream_t st, bool pdl) {
-#define X(T_, R_) \
-  if (c.threads == T_ && c.R == R_) \
-    return launch_cluster2(k_bstep_forward<T_, R_>, c.cluster, T_, c.policy, items, a, bt, st, pdl);
+#define X(T_, R_, W_) \
+  if (c.threads == T_ && c.R == R_ && c.groups == W_) \
+    return launch_cluster2(k_bstep_forward<T_, R_, W_>, c.cluster, T_, c.policy, items, a, bt, st, pdl);
   GS_STEP_FWD_CASES(X)
 #undef X
   return cudaErrorInvalidValue;
@@ -537,25 +572,25 @@ cudaError_t launch_bstep_forward(const StepConfig& c, int items, const StepFwdAr
 
 cudaError_t launch_bstep_backward(const StepConfig& c, int items, const StepBwdArgs& a, const BatchTables& bt,
                                   cudaStream_t st, bool pdl) {
-#define X(T_, R_) \
-  if (c.threads == T_ && c.R == R_) \
-    return launch_cluster2(k_bstep_backward<T_, R_>, c.cluster, T_, c.policy, items, a, bt, st, pdl);
+#define X(T_, R_, W_) \
+  if (c.threads == T_ && c.R == R_ && c.groups == W_) \
+    return launch_cluster2(k_bstep_backward<T_, R_, W_>, c.cluster, T_, c.policy, items, a, bt, st, pdl);
   GS_STEP_BWD_CASES(X)
 #undef X
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_step_forward(const StepConfig& c, const StepFwdArgs& a, cudaStream_t st, bool pdl) {
-#define X(T_, R_) \
-  if (c.threads == T_ && c.R == R_) return launch_cluster(k_step_forward<T_, R_>, c, a, st, pdl);
+#define X(T_, R_, W_) \
+  if (c.threads == T_ && c.R == R_ && c.groups == W_) return launch_cluster(k_step_forward<T_, R_, W_>, c, a, st, pdl);
   GS_STEP_FWD_CASES(X)
 #undef X
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_step_backward(const StepConfig& c, const StepBwdArgs& a, cudaStream_t st, bool pdl) {
-#define X(T_, R_) \
-  if (c.threads == T_ && c.R == R_) return launch_cluster(k_step_backward<T_, R_>, c, a, st, pdl);
+#define X(T_, R_, W_) \
+  if (c.threads == T_ && c.R == R_ && c.groups == W_) return launch_cluster(k_step_backward<T_, R_, W_>, c, a, st, pdl);
   GS_STEP_BWD_CASES(X)
 #undef X
   return cudaErrorInvalidValue;

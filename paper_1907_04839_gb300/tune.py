@@ -27,8 +27,11 @@ from . import _lib
 
 FWD = [(64, 2), (64, 4), (128, 2), (128, 4), (256, 1), (256, 2)]
 BWD = [(64, 1), (64, 2), (128, 1), (128, 2), (256, 1)]
-STEP_FWD = [(64, 2), (64, 4), (128, 1), (128, 2), (128, 4), (256, 1), (256, 2)]
-STEP_BWD = [(64, 1), (64, 2), (128, 1), (128, 2), (256, 1)]
+# fused variants: (threads per CTA, targets per thread, warp groups)
+STEP_FWD = [(64, 2, 1), (64, 4, 1), (128, 1, 1), (128, 2, 1), (128, 4, 1), (256, 1, 1), (256, 2, 1), (64, 1, 2),
+            (128, 1, 2), (128, 1, 4), (256, 1, 4)]
+STEP_BWD = [(64, 1, 1), (64, 2, 1), (128, 1, 1), (128, 2, 1), (256, 1, 1), (64, 1, 2), (128, 1, 2), (128, 1, 4),
+            (256, 1, 4)]
 CLUSTERS = [1, 2, 4, 8, 16]
 
 
@@ -63,28 +66,29 @@ def main():
         npad = (n + 63) // 64 * 64
         sweeps = ((2, STEP_FWD), (3, STEP_BWD))
         if args.variants == "default":
-            sweeps = ((2, [(128, 1)]), (3, [(64, 1)]))
+            sweeps = ((2, [(128, 1, 1)]), (3, [(64, 1, 1)]))
         for pol in args.policy:
             _lib.check(lib.gs_set_cluster_policy(pol))
             for kind, variants in sweeps:
-                for (nt, r) in variants:
+                for (nt, r, wg) in variants:
                     for c in args.clusters:
-                        if c > nt * r or c > npad // 8:
+                        if c > nt // wg * r or c > npad // 8:
                             continue
                         ms = ctypes.c_double(0.0)
                         used = ctypes.c_int32(0)
                         st = lib.gs_time_pair_config(kind + (16 if args.graph else 0), n, args.sigma, P(q), P(p),
-                                                     P(a), P(b), nt, r, c, args.reps, ctypes.byref(ms),
+                                                     P(a), P(b), nt, r, wg, c, args.reps, ctypes.byref(ms),
                                                      ctypes.byref(used), stream)
                         if st != 0:
-                            print(json.dumps({"n": n, "kind": kind, "threads": nt, "R": r, "cluster": c,
+                            print(json.dumps({"n": n, "kind": kind, "threads": nt, "R": r, "groups": wg, "cluster": c,
                                               "error": lib.gs_last_error().decode()}))
                             continue
                         res = ctypes.c_int32(0)
-                        lib.gs_max_active_clusters(kind - 2, nt, r, c, ctypes.byref(res))
-                        tiles = math.ceil(npad / (nt * r))
+                        lib.gs_max_active_clusters(kind - 2, nt, r, wg, c, ctypes.byref(res))
+                        tiles = math.ceil(npad / (nt // wg * r))
                         print(json.dumps({"n": n, "kind": "step_fwd" if kind == 2 else "step_bwd",
-                                          "threads": nt, "R": r, "cluster": c, "policy": pol, "tiles": tiles,
+                                          "threads": nt, "R": r, "groups": wg, "cluster": c, "policy": pol,
+                                          "tiles": tiles,
                                           "ctas": tiles * c, "resident_ctas": res.value * c, "ms": ms.value,
                                           "gpairs_per_s": n * n / ms.value / 1e6}), flush=True)
         _lib.check(lib.gs_set_cluster_policy(-1))
@@ -101,7 +105,7 @@ def main():
                 for s in sorted(cands):
                     ms = ctypes.c_double(0.0)
                     used = ctypes.c_int32(0)
-                    st = lib.gs_time_pair_config(kind, n, args.sigma, P(q), P(p), P(a), P(b), nt, r, s,
+                    st = lib.gs_time_pair_config(kind, n, args.sigma, P(q), P(p), P(a), P(b), nt, r, 1, s,
                                                  args.reps, ctypes.byref(ms), ctypes.byref(used), stream)
                     if st != 0:
                         print(json.dumps({"n": n, "kind": kind, "threads": nt, "R": r, "splits": s,

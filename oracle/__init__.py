@@ -56,6 +56,7 @@ def _load():
             lib.orc_shoot_gradient.argtypes = [i64, cint, cd, cd, _D, _D, _D, _D, _D, _D, _D, _D]
             lib.orc_shoot_gradient.restype = cd
             lib.orc_velocity.argtypes = [i64, _D, i64, _D, _D, cd, _D]
+            lib.orc_flow_points.argtypes = [i64, cint, cd, _D, _D, i64, _D, _D]
             _I = ctypes.POINTER(ctypes.c_int64)
             IP = ctypes.POINTER(ctypes.c_int)
             lib.orc_lbfgs_quadratic.argtypes = [i64, _D, _D, _D, cint, cint, cd, _D, IP, IP]
@@ -176,6 +177,15 @@ def velocity(x, q, p, sigma):
     v = np.empty_like(x)
     _load().orc_velocity(x.shape[0], _p(x), q.shape[0], _p(q), _p(p), float(sigma), _p(v))
     return v
+
+
+def flow_points(q0, p0, x0, T, sigma):
+    """Points x0 (M, 3) carried by the T Euler steps of the flow through the
+    Eq. 4 velocity field; returns x(1)."""
+    q0 = _in(q0); n = q0.shape[0]; p0 = _in(p0, n); x0 = _in(x0)
+    x1 = np.empty_like(x0)
+    _load().orc_flow_points(n, int(T), float(sigma), _p(q0), _p(p0), x0.shape[0], _p(x0), _p(x1))
+    return x1
 
 
 def _lbfgs_out(status, f, iters, evals, x, trace=None):

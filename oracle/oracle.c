@@ -323,6 +323,31 @@ void orc_velocity(int64_t m, const double* x, int64_t n, const double* q, const 
     }
 }
 
+/* Points carried through the deformation by the flow of Algorithm 1's
+ * forward loop (Section 2.1, Eq. 4): each of the T Euler steps moves a point x
+ * by dt times the velocity field of Eq. 4 evaluated with the landmark state
+ * of that step, x^{k+1} = x^k + dt v(x^k; q^k, p^k).  A landmark used as a
+ * point moves exactly as the landmark does, since v(q_i) = Hp_i. */
+void orc_flow_points(int64_t n, int T, double sigma, const double* q0, const double* p0,
+                     int64_t m, const double* x0, double* x1) {
+    const double dt = 1.0 / T;
+    const size_t sn = (size_t)n * 3, sm = (size_t)m * 3;
+    double* tq = malloc((size_t)(T + 1) * sn * sizeof(double));
+    double* tp = malloc((size_t)(T + 1) * sn * sizeof(double));
+    double* q1 = malloc(sn * sizeof(double));
+    double* p1 = malloc(sn * sizeof(double));
+    double* x = malloc(sm * sizeof(double));
+    double* v = malloc(sm * sizeof(double));
+    orc_shoot_forward(n, T, sigma, q0, p0, q1, p1, tq, tp);
+    memcpy(x, x0, sm * sizeof(double));
+    for (int t = 0; t < T; ++t) {
+        orc_velocity(m, x, n, tq + (size_t)t * sn, tp + (size_t)t * sn, sigma, v);
+        for (size_t k = 0; k < sm; ++k) x[k] += v[k] * dt;
+    }
+    memcpy(x1, x, sm * sizeof(double));
+    free(tq); free(tp); free(q1); free(p1); free(x); free(v);
+}
+
 /* ------------------------------------------------------------------ L-BFGS
  * Limited-memory BFGS over x (Section 2.1 uses VNL's L-BFGS; its settings are
  * not stated, so this follows the reading written down for both paths):

@@ -149,6 +149,52 @@ def test_velocity_field_eq4():
     assert rel(oracle.velocity(q, q, p, 0.2), Hp) < 1e-13
 
 
+def test_flow_points_carries_landmarks_exactly_with_q():
+    # A landmark used as a point moves with v(q_i) = Hp_i, i.e. exactly as the
+    # landmark does through the T Euler steps.
+    q, p = small_cloud(60, 21)
+    T, sigma = 7, 0.2
+    q1, _ = oracle.shoot_forward(q, p, T, sigma)
+    x1 = oracle.flow_points(q, p, q, T, sigma)
+    assert np.max(np.abs(x1 - q1)) <= 1e-14 * np.max(np.abs(q1))
+
+
+def test_flow_points_far_points_do_not_move():
+    # g underflows to exactly 0 beyond ~39 sigma, so the velocity is 0.
+    q, p = small_cloud(30, 22)
+    x0 = np.array([[60.0, 0.0, 0.0], [0.0, -45.0, 3.0]])
+    x1 = oracle.flow_points(q, p, x0, 5, 0.2)
+    assert np.array_equal(x1, x0)
+
+
+def test_flow_points_single_landmark_scalar_recursion():
+    # One landmark: q(t) = q0 + p0 t exactly.  A point offset by delta,
+    # perpendicular to p0, keeps that perpendicular offset and its separation
+    # s along p0 follows s_{k+1} = s_k + dt (g(r_k) - 1) |p0|, r_k^2 = |delta|^2 + s_k^2.
+    q0 = np.array([[0.2, -0.1, 0.4]])
+    p0 = np.array([[0.6, 0.0, 0.0]])
+    delta = np.array([0.0, 0.15, -0.05])
+    T, sigma = 25, 0.3
+    x1 = oracle.flow_points(q0, p0, q0 + delta[None, :], T, sigma)
+    dt, s = 1.0 / T, 0.0
+    d2 = float(delta @ delta)
+    for _ in range(T):
+        s += dt * (math.exp(-(d2 + s * s) / (2 * sigma * sigma)) - 1.0) * 0.6
+    expect = q0[0] + p0[0] + delta + np.array([s, 0.0, 0.0])
+    assert np.max(np.abs(x1[0] - expect)) < 1e-14
+
+
+def test_flow_points_rigid_motion_equivariance():
+    q, p = small_cloud(40, 23)
+    x0 = np.random.default_rng(24).uniform(-0.4, 0.4, size=(25, 3))
+    A = np.random.default_rng(25).normal(size=(3, 3))
+    Rm, _ = np.linalg.qr(A)
+    t0 = np.array([0.3, -0.7, 1.1])
+    x1 = oracle.flow_points(q, p, x0, 6, 0.25)
+    y1 = oracle.flow_points(q @ Rm.T + t0, p @ Rm.T, x0 @ Rm.T + t0, 6, 0.25)
+    assert rel(y1, x1 @ Rm.T + t0) < 1e-12
+
+
 # ---------------------------------------------------------------- backward
 
 def test_step_backward_is_transposed_jacobian():

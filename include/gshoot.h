@@ -129,6 +129,33 @@ typedef struct gs_register_info {
 } gs_register_info;
 
 /*
+ * velocity_field — the velocity field of Eq. 4 at M query points:
+ *   v(x_i) = sum_l g(|q_l - x_i|) p_l,   g(r) = exp(-r^2 / (2 sigma^2)),
+ * for one landmark state (q, p).  At a landmark it equals Hp.
+ * In: q, p (N, 3), x (M, 3).  Out: v (M, 3).  FP32 row-major arrays, host or
+ * device; host outputs are written before the call returns.
+ * GS_EINVAL: N or M outside [1, 2^26], sigma not finite and > 0, a NULL
+ * array.  GS_ENONFINITE (synchronous calls): a non-finite velocity.
+ */
+gs_status velocity_field(int64_t N, int64_t M, double sigma, const float* q, const float* p,
+                         const float* x, float* v, void* stream);
+
+/*
+ * flow_points — M points carried through the deformation that the initial
+ * momentum p0 generates (Section 2.1, Eq. 4): the landmarks flow forward
+ * from (q0, p0) as in shoot_forward, and every point takes the same T Euler
+ * steps through the velocity field of the same time step,
+ *   x <- x + dt v(x; q(t_k), p(t_k)),  k = 0..T-1,  dt = 1/T.
+ * A landmark used as a point follows q(t).  Points are kept in FP64
+ * between steps.
+ * In: prm (N, T, sigma used), q0, p0 (N, 3), x0 (M, 3).  Out: x1 (M, 3).
+ * Arrays as in velocity_field.  Errors as in shoot_forward; M outside
+ * [1, 2^26] or a NULL point array is GS_EINVAL.
+ */
+gs_status flow_points(const gs_params* prm, const float* q0, const float* p0, int64_t M,
+                      const float* x0, float* x1, void* stream);
+
+/*
  * register_landmarks — the outer optimisation of Algorithm 1: L-BFGS over the initial
  * momentum p0 of the loss L(p0) = H(p0, q0) + lambda ||q(1) - target||^2
  * (Eq. 3), each function evaluation being one ComputeGradient.  Settings

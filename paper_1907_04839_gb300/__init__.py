@@ -21,7 +21,7 @@ from ._lib import (EXPORTS, GShootError, GsBatchProblem, GsParams, GsRegisterInf
 
 __all__ = [
     "step_forward", "step_backward", "shoot_forward", "shoot_gradient", "register", "shoot",
-    "register_batch", "Server",
+    "register_batch", "Server", "velocity_field", "flow_points",
     "release_workspace", "version", "GShootError", "GsParams", "EXPORTS",
 ]
 
@@ -49,7 +49,8 @@ class _Marshal:
             self.stream = ctypes.c_void_p(0)
         self.n = n
 
-    def inp(self, x, name):
+    def inp(self, x, name, rows=None):
+        """Pointer to x as (rows, 3) FP32; rows defaults to the call's N."""
         if x is None:
             return None
         if self.device:
@@ -66,19 +67,23 @@ class _Marshal:
             ptr = t.ctypes.data
         if len(arr_shape) != 2 or arr_shape[1] != 3:
             raise ValueError("%s: expected shape (N, 3), got %r" % (name, arr_shape))
-        if self.n is None:
+        if rows is not None:
+            if arr_shape[0] != rows:
+                raise ValueError("%s: expected %d rows, got %d" % (name, rows, arr_shape[0]))
+        elif self.n is None:
             self.n = arr_shape[0]
         elif arr_shape[0] != self.n:
             raise ValueError("%s: expected %d rows, got %d" % (name, self.n, arr_shape[0]))
         self.keep.append(t)
         return ctypes.c_void_p(ptr)
 
-    def out(self):
+    def out(self, rows=None):
+        rows = self.n if rows is None else rows
         if self.device:
-            t = self.torch.empty((self.n, 3), dtype=self.torch.float32, device=self.dev)
+            t = self.torch.empty((rows, 3), dtype=self.torch.float32, device=self.dev)
             ptr = t.data_ptr()
         else:
-            t = np.empty((self.n, 3), dtype=np.float32)
+            t = np.empty((rows, 3), dtype=np.float32)
             ptr = t.ctypes.data
         self.keep.append(t)
         return t, ctypes.c_void_p(ptr)
@@ -98,6 +103,31 @@ def step_forward(q, p, sigma):
     Hp, op = m.out()
     check(load().step_forward(m.n, float(sigma), pq, pp, oq, op, m.stream))
     return Hq, Hp
+
+
+def velocity_field(q, p, x, sigma):
+    """Eq. 4: the velocity of the landmark state (q, p) at points x (M, 3)."""
+    m = _Marshal(q)
+    pq, pp = m.inp(q, "q"), m.inp(p, "p")
+    rows = int(x.shape[0])
+    px = m.inp(x, "x", rows=rows)
+    v, pv = m.out(rows=rows)
+    check(load().velocity_field(m.n, rows, float(sigma), pq, pp, px, pv, m.stream))
+    return v
+
+
+def flow_points(q0, p0, x0, T, sigma):
+    """Points x0 (M, 3) carried through the deformation that p0 generates:
+    the same T Euler steps as the landmarks, through the Eq. 4 velocity
+    field of each step.  Returns x(1)."""
+    m = _Marshal(q0)
+    pq, pp = m.inp(q0, "q0"), m.inp(p0, "p0")
+    rows = int(x0.shape[0])
+    px = m.inp(x0, "x0", rows=rows)
+    x1, p1 = m.out(rows=rows)
+    prm = _params(m.n, T, sigma)
+    check(load().flow_points(ctypes.byref(prm), pq, pp, rows, px, p1, m.stream))
+    return x1
 
 
 def step_backward(q, p, alpha, beta, sigma):

@@ -22,6 +22,7 @@ GS_STATUS = {
 # Every symbol the header declares; tests check the library exports them all.
 EXPORTS = [
     "step_forward", "step_backward", "shoot_forward", "shoot_gradient", "register_landmarks",
+    "velocity_field", "flow_points",
     "register_batch", "gs_server_create", "gs_server_submit", "gs_server_step", "gs_server_poll",
     "gs_server_stats", "gs_server_destroy",
     "gs_time_pair_kernels", "gs_time_pair_config", "gs_set_step_config", "step_forward_noalloc",
@@ -105,6 +106,8 @@ def _declare(lib):
     lib.shoot_forward.argtypes = [P, fp, fp, fp, fp, dp, vp]
     lib.shoot_gradient.argtypes = [P, fp, fp, fp, dp, fp, fp, vp]
     lib.register_landmarks.argtypes = [P, fp, fp, fp, ctypes.POINTER(GsRegisterInfo), vp]
+    lib.velocity_field.argtypes = [i64, i64, cd, fp, fp, fp, fp, vp]
+    lib.flow_points.argtypes = [P, fp, fp, i64, fp, fp, vp]
     lib.register_batch.argtypes = [i32, ctypes.POINTER(GsBatchProblem), i32, i32, i32, cd, vp]
     lib.register_batch.restype = ctypes.c_int
     SV = ctypes.c_void_p
@@ -129,6 +132,7 @@ def _declare(lib):
     lib.gs_time_pair_config.argtypes = [i32, i64, cd, fp, fp, fp, fp, i32, i32, i32, i32, i32, dp,
                                         ctypes.c_void_p, vp]
     for name in ("step_forward", "step_backward", "shoot_forward", "shoot_gradient", "register_landmarks",
+                 "velocity_field", "flow_points",
                  "gs_time_pair_kernels",
                  "step_forward_noalloc", "gs_time_pair_config", "gs_set_step_config", "gs_set_phase_timing",
                  "gs_phase_times", "gs_set_cluster_policy", "gs_max_active_clusters"):

@@ -89,6 +89,11 @@ struct Workspace {
   bool phase_timing = false;
   cudaEvent_t phase[3] = {nullptr, nullptr, nullptr};
   LbfgsBufs lb;
+  // Query points of velocity_field / flow_points (grown on demand).
+  int cap_pts = 0;
+  std::vector<void*> pt_allocs;
+  double* pts64 = nullptr;
+  float *pts_in = nullptr, *pts_out = nullptr;
 
   void drop_graphs() {
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
@@ -99,6 +104,9 @@ struct Workspace {
     for (void* p : allocs) cudaFree(p);
     allocs.clear();
     lb.free_all();
+    for (void* p : pt_allocs) cudaFree(p);
+    pt_allocs.clear();
+    cap_pts = 0;
     cap_npad = cap_T = cap_splits = cap_red = cap_ck = 0;
     clean_n = -1;
   }

@@ -65,6 +65,14 @@ def _load():
             lib.orc_lbfgs_rosenbrock.restype = cint
             lib.orc_register.argtypes = [i64, cint, cd, cd, cint, cint, cd, _D, _D, _D, _D, IP, IP, _D]
             lib.orc_register.restype = cint
+            lib.orc_shoot_forward_v.argtypes = [i64, cint, cd, cint, _D, _D, _D, _D]
+            lib.orc_loss_v.argtypes = [i64, cint, cd, cd, cint, cint, _D, _D, _D]
+            lib.orc_loss_v.restype = cd
+            lib.orc_shoot_gradient_v.argtypes = [i64, cint, cd, cd, cint, cint, _D, _D, _D, _D, _D, _D, _D, _D]
+            lib.orc_shoot_gradient_v.restype = cd
+            lib.orc_register_v.argtypes = [i64, cint, cd, cd, cint, cint, cint, cint, cd, _D, _D, _D, _D, IP, IP,
+                                           _D]
+            lib.orc_register_v.restype = cint
             lib.orc_step_forward_rows.argtypes = [i64, cd, _D, _D, i64, _I, _D, _D]
             lib.orc_step_backward_rows.argtypes = [i64, cd, _D, _D, _D, _D, i64, _I, _D, _D]
             _lib = lib
@@ -225,4 +233,60 @@ def register(q0, target, T, sigma, lam, p0=None, m=10, max_iter=50, grad_tol=1e-
     st = _load().orc_register(n, int(T), float(sigma), float(lam), int(m), int(max_iter), float(grad_tol),
                               _p(q0), _p(target), _p(x), ctypes.byref(f), ctypes.byref(it), ctypes.byref(ev),
                               _p(trace))
+    return _lbfgs_out(st, f, it, ev, x, trace)
+
+
+# ---------------------------------------------------------------- variants
+INTEGRATORS = {"euler": 0, "rk4": 1}
+KINETIC = {"start": 0, "end": 1}
+
+
+def _variant(integrator, h_at):
+    if integrator not in INTEGRATORS or h_at not in KINETIC:
+        raise ValueError("integrator must be one of %r and h_at one of %r" % (list(INTEGRATORS), list(KINETIC)))
+    return INTEGRATORS[integrator], KINETIC[h_at]
+
+
+def shoot_forward_v(q0, p0, T, sigma, integrator="euler"):
+    """Forward flow with the chosen integrator ("euler" or "rk4"): (q1, p1)."""
+    ig, _ = _variant(integrator, "start")
+    q0 = _in(q0); n = q0.shape[0]; p0 = _in(p0, n)
+    q1 = np.empty_like(q0); p1 = np.empty_like(q0)
+    _load().orc_shoot_forward_v(n, int(T), float(sigma), ig, _p(q0), _p(p0), _p(q1), _p(p1))
+    return q1, p1
+
+
+def loss_v(q0, p0, target, T, sigma, lam, integrator="euler", h_at="start") -> float:
+    """Loss of a variant: kinetic term at t = 0 ("start") or t = 1 ("end")."""
+    ig, he = _variant(integrator, h_at)
+    q0 = _in(q0); n = q0.shape[0]
+    p0, target = _in(p0, n), _in(target, n)
+    return float(_load().orc_loss_v(n, int(T), float(sigma), float(lam), ig, he, _p(q0), _p(p0), _p(target)))
+
+
+def shoot_gradient_v(q0, p0, target, T, sigma, lam, integrator="euler", h_at="start"):
+    """ComputeGradient of a variant: dict(loss, grad_p0, grad_q0, q1, p1, H)
+    with H the kinetic term of the loss."""
+    ig, he = _variant(integrator, h_at)
+    q0 = _in(q0); n = q0.shape[0]
+    p0, target = _in(p0, n), _in(target, n)
+    gp = np.empty_like(q0); gq = np.empty_like(q0)
+    q1 = np.empty_like(q0); p1 = np.empty_like(q0)
+    h = ctypes.c_double(0.0)
+    L = _load().orc_shoot_gradient_v(n, int(T), float(sigma), float(lam), ig, he, _p(q0), _p(p0), _p(target),
+                                     _p(gp), _p(gq), _p(q1), _p(p1), ctypes.byref(h))
+    return dict(loss=float(L), grad_p0=gp, grad_q0=gq, q1=q1, p1=p1, H=float(h.value))
+
+
+def register_v(q0, target, T, sigma, lam, integrator="euler", h_at="start", p0=None, m=10, max_iter=50,
+               grad_tol=1e-5):
+    """register with a variant of the discretisation."""
+    ig, he = _variant(integrator, h_at)
+    q0 = _in(q0); n = q0.shape[0]; target = _in(target, n)
+    x = np.zeros((n, 3)) if p0 is None else _in(p0, n).copy()
+    trace = np.zeros(max_iter + 1)
+    f = ctypes.c_double(0); it = ctypes.c_int(0); ev = ctypes.c_int(0)
+    st = _load().orc_register_v(n, int(T), float(sigma), float(lam), ig, he, int(m), int(max_iter),
+                                float(grad_tol), _p(q0), _p(target), _p(x), ctypes.byref(f), ctypes.byref(it),
+                                ctypes.byref(ev), _p(trace))
     return _lbfgs_out(st, f, it, ev, x, trace)

@@ -304,6 +304,203 @@ double orc_shoot_gradient(int64_t n, int T, double sigma, double lambda,
     return L;
 }
 
+/* ------------------------------------------------------------------ variants
+ * Two variants of the discretisation, both admitted by the paper's text:
+ *
+ * Integrator (integ = 0: explicit Euler as above; integ = 1: the classical
+ * fourth-order Runge-Kutta method).  With y = (q, p) and f(y) = (Hp, -Hq) of
+ * Eq. 2, one RK4 step of dt = 1/T is
+ *   k1 = f(y), k2 = f(y + dt/2 k1), k3 = f(y + dt/2 k2), k4 = f(y + dt k3),
+ *   y' = y + dt/6 (k1 + 2 k2 + 2 k3 + k4).
+ * Its exact discrete adjoint, with J(Y)^T w = StepBackward at stage state Y
+ * and w the adjoint of y':
+ *   v4 = J(Y4)^T (dt/6 w),
+ *   v3 = J(Y3)^T (dt/3 w + dt v4),
+ *   v2 = J(Y2)^T (dt/3 w + dt/2 v3),
+ *   v1 = J(y)^T  (dt/6 w + dt/2 v2),
+ *   adjoint of y = w + v1 + v2 + v3 + v4.
+ *
+ * Kinetic term (h_at_end = 0: H(p0, q0) as above; h_at_end = 1: H(p(1), q(1)),
+ * the form Algorithm 1's pseudocode writes, evaluating the kinetic term at
+ * the end state).  With it at the end, the adjoint starts from
+ * alpha(1) = 2 lambda (q(1) - target) + Hq(q(1), p(1)), beta(1) = Hp(q(1), p(1)),
+ * and the gradient is the adjoint at t = 0 with no extra term. */
+
+/* One step of the chosen integrator from (q, p), in place.  When stage_q /
+ * stage_p are non-null they receive the four RK4 stage states Y1..Y4 as
+ * (4, N, 3) arrays (Y1 = y). */
+static void integ_step(int64_t n, int integ, double dt, double sigma, double* q, double* p,
+                       double* stage_q, double* stage_p) {
+    const size_t m = (size_t)n * 3;
+    if (integ == 0) {
+        double* Hq = malloc(m * sizeof(double));
+        double* Hp = malloc(m * sizeof(double));
+        orc_step_forward(n, sigma, q, p, Hq, Hp);
+        for (size_t k = 0; k < m; ++k) {
+            q[k] += Hp[k] * dt;
+            p[k] -= Hq[k] * dt;
+        }
+        free(Hq); free(Hp);
+        return;
+    }
+    /* RK4: kq_s, kp_s are the q and p parts of k_s = f(Y_s). */
+    const double a[4] = {0.0, 0.5, 0.5, 1.0};      /* Y_s = y + a_s dt k_{s-1} */
+    const double b[4] = {1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6};
+    double* Yq = malloc(m * sizeof(double));
+    double* Yp = malloc(m * sizeof(double));
+    double* Hq = malloc(m * sizeof(double));
+    double* Hp = malloc(m * sizeof(double));
+    double* sq = calloc(m, sizeof(double));
+    double* sp = calloc(m, sizeof(double));
+    memcpy(Yq, q, m * sizeof(double));
+    memcpy(Yp, p, m * sizeof(double));
+    for (int st = 0; st < 4; ++st) {
+        if (st > 0) {
+            for (size_t k = 0; k < m; ++k) {
+                Yq[k] = q[k] + a[st] * dt * Hp[k];
+                Yp[k] = p[k] - a[st] * dt * Hq[k];
+            }
+        }
+        if (stage_q) memcpy(stage_q + (size_t)st * m, Yq, m * sizeof(double));
+        if (stage_p) memcpy(stage_p + (size_t)st * m, Yp, m * sizeof(double));
+        orc_step_forward(n, sigma, Yq, Yp, Hq, Hp);
+        for (size_t k = 0; k < m; ++k) {
+            sq[k] += b[st] * Hp[k];
+            sp[k] -= b[st] * Hq[k];
+        }
+    }
+    for (size_t k = 0; k < m; ++k) {
+        q[k] += dt * sq[k];
+        p[k] += dt * sp[k];
+    }
+    free(Yq); free(Yp); free(Hq); free(Hp); free(sq); free(sp);
+}
+
+/* Forward flow with the chosen integrator: T steps from (q0, p0). */
+void orc_shoot_forward_v(int64_t n, int T, double sigma, int integ, const double* q0, const double* p0,
+                         double* q1, double* p1) {
+    const double dt = 1.0 / T;
+    const size_t m = (size_t)n * 3;
+    memcpy(q1, q0, m * sizeof(double));
+    memcpy(p1, p0, m * sizeof(double));
+    for (int t = 0; t < T; ++t) integ_step(n, integ, dt, sigma, q1, p1, NULL, NULL);
+}
+
+/* Eq. 3 objective of a variant: H at (p0, q0) or at (p(1), q(1)), plus
+ * lambda ||q(1) - target||^2. */
+double orc_loss_v(int64_t n, int T, double sigma, double lambda, int integ, int h_at_end,
+                  const double* q0, const double* p0, const double* target) {
+    const size_t m = (size_t)n * 3;
+    double* q1 = malloc(m * sizeof(double));
+    double* p1 = malloc(m * sizeof(double));
+    orc_shoot_forward_v(n, T, sigma, integ, q0, p0, q1, p1);
+    double mis = 0.0;
+    for (size_t k = 0; k < m; ++k) mis += (q1[k] - target[k]) * (q1[k] - target[k]);
+    const double H = h_at_end ? orc_hamiltonian(n, sigma, q1, p1) : orc_hamiltonian(n, sigma, q0, p0);
+    free(q1); free(p1);
+    return H + lambda * mis;
+}
+
+/* ComputeGradient of a variant.  Returns the loss; grad_p0, grad_q0, q1, p1
+ * (each may be null) as in orc_shoot_gradient; *H_out (may be null) is the
+ * kinetic term of the loss. */
+double orc_shoot_gradient_v(int64_t n, int T, double sigma, double lambda, int integ, int h_at_end,
+                            const double* q0, const double* p0, const double* target,
+                            double* grad_p0, double* grad_q0, double* q1_out, double* p1_out,
+                            double* H_out) {
+    const double dt = 1.0 / T;
+    const size_t m = (size_t)n * 3;
+    const int S = integ == 0 ? 1 : 4;   /* stage states kept per step */
+    double* tq = malloc((size_t)T * S * m * sizeof(double));
+    double* tp = malloc((size_t)T * S * m * sizeof(double));
+    double* q = malloc(m * sizeof(double));
+    double* p = malloc(m * sizeof(double));
+    double* Hq = malloc(m * sizeof(double));
+    double* Hp = malloc(m * sizeof(double));
+    double* alpha = malloc(m * sizeof(double));
+    double* beta = malloc(m * sizeof(double));
+    double* ca = malloc(m * sizeof(double));
+    double* cb = malloc(m * sizeof(double));
+    double* va = malloc(m * sizeof(double));
+    double* vb = malloc(m * sizeof(double));
+    double* ya = malloc(m * sizeof(double));
+    double* yb = malloc(m * sizeof(double));
+
+    memcpy(q, q0, m * sizeof(double));
+    memcpy(p, p0, m * sizeof(double));
+    for (int t = 0; t < T; ++t) {
+        double* sq = tq + (size_t)t * S * m;
+        double* sp = tp + (size_t)t * S * m;
+        if (integ == 0) {
+            memcpy(sq, q, m * sizeof(double));
+            memcpy(sp, p, m * sizeof(double));
+            integ_step(n, 0, dt, sigma, q, p, NULL, NULL);
+        } else {
+            integ_step(n, 1, dt, sigma, q, p, sq, sp);
+        }
+    }
+    double mis = 0.0;
+    for (size_t k = 0; k < m; ++k) mis += (q[k] - target[k]) * (q[k] - target[k]);
+    double H;
+    if (h_at_end) {
+        H = orc_hamiltonian(n, sigma, q, p);
+        orc_step_forward(n, sigma, q, p, Hq, Hp);
+        for (size_t k = 0; k < m; ++k) {
+            alpha[k] = 2.0 * lambda * (q[k] - target[k]) + Hq[k];
+            beta[k] = Hp[k];
+        }
+    } else {
+        H = orc_hamiltonian(n, sigma, q0, p0);
+        for (size_t k = 0; k < m; ++k) {
+            alpha[k] = 2.0 * lambda * (q[k] - target[k]);
+            beta[k] = 0.0;
+        }
+    }
+    const double L = H + lambda * mis;
+    if (q1_out) memcpy(q1_out, q, m * sizeof(double));
+    if (p1_out) memcpy(p1_out, p, m * sizeof(double));
+
+    /* stage cotangent coefficients: cotangent of k_s = cw[s] dt w + cv[s] dt v_{s+1} */
+    const double cw[4] = {1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6};
+    const double cv[4] = {0.5, 0.5, 1.0, 0.0};
+    for (int t = T - 1; t >= 0; --t) {
+        const double* sq = tq + (size_t)t * S * m;
+        const double* sp = tp + (size_t)t * S * m;
+        if (integ == 0) {
+            orc_step_backward(n, sigma, sq, sp, alpha, beta, va, vb);
+            for (size_t k = 0; k < m; ++k) {
+                alpha[k] += dt * va[k];
+                beta[k] += dt * vb[k];
+            }
+            continue;
+        }
+        memcpy(ya, alpha, m * sizeof(double));
+        memcpy(yb, beta, m * sizeof(double));
+        for (int st = 3; st >= 0; --st) {
+            for (size_t k = 0; k < m; ++k) {
+                ca[k] = cw[st] * dt * alpha[k] + (st < 3 ? cv[st] * dt * va[k] : 0.0);
+                cb[k] = cw[st] * dt * beta[k] + (st < 3 ? cv[st] * dt * vb[k] : 0.0);
+            }
+            orc_step_backward(n, sigma, sq + (size_t)st * m, sp + (size_t)st * m, ca, cb, va, vb);
+            for (size_t k = 0; k < m; ++k) {
+                ya[k] += va[k];
+                yb[k] += vb[k];
+            }
+        }
+        memcpy(alpha, ya, m * sizeof(double));
+        memcpy(beta, yb, m * sizeof(double));
+    }
+    if (!h_at_end) orc_step_forward(n, sigma, q0, p0, Hq, Hp);
+    for (size_t k = 0; k < m; ++k) {
+        if (grad_p0) grad_p0[k] = beta[k] + (h_at_end ? 0.0 : Hp[k]);
+        if (grad_q0) grad_q0[k] = alpha[k] + (h_at_end ? 0.0 : Hq[k]);
+    }
+    if (H_out) *H_out = H;
+    free(tq); free(tp); free(q); free(p); free(Hq); free(Hp); free(alpha); free(beta);
+    free(ca); free(cb); free(va); free(vb); free(ya); free(yb);
+    return L;
+}
+
 /* Eq. 4: velocity v(x) = sum_l g(||q_l - x||) p_l at m query points x. */
 void orc_velocity(int64_t m, const double* x, int64_t n, const double* q, const double* p,
                   double sigma, double* v) {
@@ -570,16 +767,29 @@ typedef struct {
     double sigma, lambda;
     const double* q0;
     const double* target;
+    int integ, h_at_end;
 } reg_ctx;
 
 static double reg_fg(void* p, const double* x, double* g) {
     const reg_ctx* r = p;
-    return orc_shoot_gradient(r->n, r->T, r->sigma, r->lambda, r->q0, x, r->target, g, NULL, NULL, NULL, NULL);
+    if (r->integ == 0 && r->h_at_end == 0)
+        return orc_shoot_gradient(r->n, r->T, r->sigma, r->lambda, r->q0, x, r->target, g, NULL, NULL, NULL, NULL);
+    return orc_shoot_gradient_v(r->n, r->T, r->sigma, r->lambda, r->integ, r->h_at_end, r->q0, x, r->target, g,
+                                NULL, NULL, NULL, NULL);
 }
 
 int orc_register(int64_t n, int T, double sigma, double lambda, int m, int max_iter, double grad_tol,
                  const double* q0, const double* target, double* p0, double* loss, int* iters, int* evals,
                  double* trace) {
-    reg_ctx r = {n, T, sigma, lambda, q0, target};
+    reg_ctx r = {n, T, sigma, lambda, q0, target, 0, 0};
+    return orc_lbfgs(3 * n, p0, reg_fg, &r, m, max_iter, grad_tol, loss, iters, evals, trace);
+}
+
+/* register with a variant of the discretisation (integ, h_at_end as in
+ * orc_shoot_gradient_v). */
+int orc_register_v(int64_t n, int T, double sigma, double lambda, int integ, int h_at_end, int m, int max_iter,
+                   double grad_tol, const double* q0, const double* target, double* p0, double* loss, int* iters,
+                   int* evals, double* trace) {
+    reg_ctx r = {n, T, sigma, lambda, q0, target, integ, h_at_end};
     return orc_lbfgs(3 * n, p0, reg_fg, &r, m, max_iter, grad_tol, loss, iters, evals, trace);
 }

@@ -12,13 +12,16 @@ seeded.
 Metric: gradient evaluations per second.  Each step also reports its pair
 interactions per second, 2 T N^2 / t.  The same line carries two bounded
 samples of the other workloads: `batched` (independent registrations packed
-into shared launches, against a loop of single registrations) and `served`
+into shared launches, against a loop of single registrations), `served`
 (a Poisson request trace through the continuous-batching server, with p50 /
-p99 latency).  `--workload batched|served` runs those workloads at their
-full sizes instead and prints their own line.
+p99 latency), `velocity` (the Eq. 4 velocity field on a 101^3 point grid and
+points carried through the deformation) and `population` (one template
+registered to 34 subjects, with AverageDist / MaxDist).
+`--workload batched|served|population` runs one of those workloads at its
+full size instead and prints its own line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gshoot|reference]
-                    [--workload grad|batched|served]
+                    [--workload grad|batched|served|population]
 
 It prints one JSON line on rank 0.  `--impl reference` times the FP64 CPU
 oracle on this host's cores on a bounded sample of the same workload.
@@ -55,6 +58,11 @@ FLOPS_PER_PAIR_BWD = 63
 # FP32 instructions per pair issued by the kernels (for the pipe fraction).
 INSTR_PER_PAIR_FWD = 16
 INSTR_PER_PAIR_BWD = 36
+# The velocity field of Eq. 4 per (point, landmark) pair: difference (3),
+# squared distance (5), exponent scale (1), g p_j accumulated (6); issued
+# FP32 lane-operations 9.
+FLOPS_PER_PAIR_VEL = 15
+INSTR_PER_PAIR_VEL = 9
 # DRAM bytes (read + write) of one k_step_backward launch, from ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum, caches flushed before the
 # launch) of the current kernel, by N.  Empty it whenever the kernel changes.
@@ -71,7 +79,7 @@ def parse():
     ap.add_argument("--n", type=int, default=N_LANDMARKS,
                     help="landmark count (profiling runs only; the reported workload is N=4096)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["grad", "batched", "served"], default="grad")
+    ap.add_argument("--workload", choices=["grad", "batched", "served", "population"], default="grad")
     ap.add_argument("--batched-count", type=int, default=None,
                     help="registrations of the batched workload (default: 128 in the grad run's sample, 512 alone)")
     ap.add_argument("--served-count", type=int, default=None,
@@ -376,6 +384,103 @@ def measure_served(gsh, count, max_iter=200, budget=120 << 30, rate=200.0, T=T_S
     }
 
 
+def measure_population(gsh, subjects=34, n=1847, T=40, max_iter=400, sigma=SIGMA, lam=LAMBDA):
+    """One template registered to every subject of a population (the shape
+    of the paper's study: 34 subjects, 1847 landmarks, T = 40, at most 400
+    iterations), packed into one register_batch call and, for comparison,
+    as a loop of register() calls.  Wall clock, host inputs and results
+    included.  Reports AverageDist / MaxDist (Section 3.1) before and after,
+    mean and standard deviation over the subjects, as in Table 1."""
+    import torch
+    import landmark_synth as ls
+    pop = ls.population(n, subjects, seed=0)
+    q0 = np.ascontiguousarray(pop.template, np.float32)
+    probs = [dict(q0=q0, target=np.ascontiguousarray(t, np.float32), sigma=sigma, lam=lam) for t in pop.targets]
+    gsh.register_batch(probs[:2], T=T, max_iter=2, grad_tol=1e-5)       # warm-up
+    gsh.register(q0, probs[0]["target"], T, sigma, lam, max_iter=2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    packed = gsh.register_batch(probs, T=T, max_iter=max_iter, grad_tol=1e-5)
+    torch.cuda.synchronize()
+    t_packed = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    loop = [gsh.register(q0, p["target"], T, sigma, lam, max_iter=max_iter, grad_tol=1e-5) for p in probs]
+    torch.cuda.synchronize()
+    t_loop = time.perf_counter() - t0
+    before = [np.linalg.norm(p["target"].astype(np.float64) - q0.astype(np.float64), axis=1) for p in probs]
+    ms = lambda xs: [float(np.mean(xs)), float(np.std(xs))]
+    evals = int(sum(r[1]["evals"] for r in packed))
+    return {
+        "subjects": subjects, "N": n, "T": T, "sigma": sigma, "lambda": lam, "max_iter": max_iter,
+        "grad_tol": 1e-5, "template": "mean of the subjects (synthetic population, seed 0)",
+        "packed_regs_per_s": subjects / t_packed, "loop_regs_per_s": subjects / t_loop,
+        "speedup": t_loop / t_packed, "packed_s": t_packed, "loop_s": t_loop,
+        "packed_pair_interactions_per_s": 2.0 * T * n * n * evals / t_packed,
+        "evals_packed": evals, "evals_loop": int(sum(r[1]["evals"] for r in loop)),
+        "iters_mean": float(np.mean([r[1]["iters"] for r in packed])),
+        "avg_dist_before": ms([b.mean() for b in before]), "max_dist_before": ms([b.max() for b in before]),
+        "avg_dist_after": ms([r[1]["avg_dist"] for r in packed]),
+        "max_dist_after": ms([r[1]["max_dist"] for r in packed]),
+        "avg_dist_after_loop": ms([r[1]["avg_dist"] for r in loop]),
+        "dist_basis": "[mean, std] over subjects of AverageDist / MaxDist(q(1), target)",
+        "timing": "wall clock, host inputs and results included",
+    }
+
+
+def velocity_grid(n_side=101, half=1.2):
+    """Query points of the deformation: a regular n_side^3 grid over the
+    box [-half, half]^3 that holds the ellipsoid (an image grid stand-in)."""
+    ax = np.linspace(-half, half, n_side, dtype=np.float64)
+    g = np.stack(np.meshgrid(ax, ax, ax, indexing="ij"), axis=-1).reshape(-1, 3)
+    return np.ascontiguousarray(g, dtype=np.float32)
+
+
+def measure_velocity(gsh, reps=5, T=T_STEPS):
+    """The Eq. 4 velocity field: a 101^3 grid of points carried through the
+    deformation of the workload's landmarks (flow_points: the landmark flow
+    plus T Euler steps of every point), and one velocity_field evaluation at
+    the same points.  Device-resident inputs, CUDA events on the stream,
+    median of `reps` calls after one warm-up."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    q0, p0, _ = workload()
+    x = velocity_grid()
+    n, m = q0.shape[0], x.shape[0]
+    dq, dp, dx = (torch.from_numpy(a).to(dev) for a in (q0, p0, x))
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize(dev)
+        out = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            out.append(a.elapsed_time(b))
+        return float(np.median(out))
+
+    t_flow = timed(lambda: gsh.flow_points(dq, dp, dx, T, SIGMA))
+    t_vel = timed(lambda: gsh.velocity_field(dq, dp, dx, SIGMA))
+    num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = alu_peak_tflops(num_sms, float(read_measured_peaks().get("sm_max_mhz", 2070.0)))
+    pairs_vel = float(m) * n
+    tf = FLOPS_PER_PAIR_VEL * pairs_vel / (t_vel * 1e-3) / 1e12
+    return {
+        "N": n, "M": m, "T": T, "points": "regular 101^3 grid over [-1.2, 1.2]^3",
+        "flow_points_ms": t_flow, "point_steps_per_s": m * T / (t_flow * 1e-3),
+        "flow_pair_interactions_per_s": T * pairs_vel / (t_flow * 1e-3),
+        "velocity_field_ms": t_vel, "velocity_pair_interactions_per_s": pairs_vel / (t_vel * 1e-3),
+        "roofline": {"bound": "alu", "kernel": "k_velocity (one velocity_field call, conversions included)",
+                     "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                     "fp32_pipe_frac": INSTR_PER_PAIR_VEL * pairs_vel / (t_vel * 1e-3) / (
+                         num_sms * 128 * float(read_measured_peaks().get("sm_max_mhz", 2070.0)) * 1e6)},
+        "timing": "CUDA events on the stream, device inputs, median of %d calls" % reps,
+    }
+
+
 def run_workload(args, dist):
     """--workload batched|served: the full-size workload, its own JSON line."""
     import torch
@@ -385,6 +490,10 @@ def run_workload(args, dist):
     if args.workload == "batched":
         res = measure_batched(gsh, args.batched_count or 512)
         metric = "registrations/s (%d packed registrations, N~LogU[500,8000], T=20)" % res["registrations"]
+        value, ms = res["packed_regs_per_s"], res["packed_s"] * 1e3
+    elif args.workload == "population":
+        res = measure_population(gsh)
+        metric = "registrations/s (one template to 34 subjects, N=1847, T=40, packed)"
         value, ms = res["packed_regs_per_s"], res["packed_s"] * 1e3
     else:
         res = measure_served(gsh, args.served_count or 64)
@@ -551,6 +660,8 @@ def run_gshoot(args, dist):
     if not args.no_samples:
         line["batched"] = measure_batched(gsh, args.batched_count or 128)
         line["served"] = measure_served(gsh, args.served_count or 8)
+        line["velocity"] = measure_velocity(gsh)
+        line["population"] = measure_population(gsh)
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_gradient_sample()
     if dist.rank == 0:

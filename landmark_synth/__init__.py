@@ -21,6 +21,13 @@ Recipe (fixed draw order, one ``numpy.random.default_rng(seed)`` stream):
 3. bump centres: ``n_bumps`` distinct template indices drawn uniformly.
 4. bump amplitudes: iid N(0, amp^2) per coordinate, one 3-vector per bump.
 5. target = template + sum_b A_b exp(-||x - c_b||^2 / (2 sigma_b^2)).
+
+Population (one template, many subjects; the shape of Section 3.1's study of
+34 subjects with 1847 landmarks each): a base surface is drawn by steps 1-2
+from ``default_rng(seed)``.  Subject s draws steps 3-5 from its own stream
+``default_rng((seed, s))`` on the base surface.  The template is the mean of
+the subjects, as the paper builds its template by averaging the (rigidly
+aligned) subject landmark sets; the synthetic subjects need no alignment.
 """
 from __future__ import annotations
 
@@ -35,6 +42,8 @@ __all__ = [
     "random_momentum",
     "batched_requests",
     "poisson_trace",
+    "Population",
+    "population",
 ]
 
 
@@ -118,3 +127,39 @@ def poisson_trace(count: int, rate: float, n_lo: int = 1000, n_hi: int = 50000,
     logn = rng.uniform(math.log(n_lo), math.log(n_hi), size=count)
     ns = np.clip(np.round(np.exp(logn)).astype(int), n_lo, n_hi)
     return [dict(seed=first_seed + k, n=int(ns[k]), t_arrival=float(t[k])) for k in range(count)]
+
+
+@dataclasses.dataclass
+class Population:
+    template: np.ndarray  # (N, 3) float64: the mean of the subjects
+    targets: list         # per subject (N, 3) float64
+    seed: int
+
+    @property
+    def n(self) -> int:
+        return int(self.template.shape[0])
+
+
+def population(n: int = 1847, subjects: int = 34, seed: int = 0, n_bumps: int = 8,
+               axes=(1.0, 0.8, 0.6), jitter: float = 0.01,
+               bump_sigma: float = 0.3, bump_amp: float = 0.1) -> Population:
+    """One template and `subjects` targets with corresponding landmarks (see
+    the module doc)."""
+    if n < 1 or subjects < 1:
+        raise ValueError("n and subjects must be >= 1")
+    rng = np.random.default_rng(seed)
+    base = _ellipsoid_surface(rng, n, axes)
+    base = base + rng.normal(0.0, jitter, size=base.shape)
+    nb = min(n_bumps, n)
+    targets = []
+    for s in range(subjects):
+        r = np.random.default_rng((seed, s))
+        centres = base[r.choice(n, size=nb, replace=False)]
+        amps = r.normal(0.0, bump_amp, size=(nb, 3))
+        disp = np.zeros_like(base)
+        for cb, ab in zip(centres, amps):
+            w = np.exp(-np.sum((base - cb) ** 2, axis=1) / (2.0 * bump_sigma ** 2))
+            disp += w[:, None] * ab[None, :]
+        targets.append(np.ascontiguousarray(base + disp))
+    template = np.ascontiguousarray(np.mean(np.stack(targets), axis=0))
+    return Population(template=template, targets=targets, seed=seed)

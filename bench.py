@@ -15,8 +15,9 @@ samples of the other workloads: `batched` (independent registrations packed
 into shared launches, against a loop of single registrations), `served`
 (a Poisson request trace through the continuous-batching server, with p50 /
 p99 latency), `velocity` (the Eq. 4 velocity field on a 101^3 point grid and
-points carried through the deformation) and `population` (one template
-registered to 34 subjects, with AverageDist / MaxDist).
+points carried through the deformation), `population` (one template
+registered to 34 subjects, with AverageDist / MaxDist) and `variants` (RK4
+against Euler steps at equal pair work: speed and accuracy).
 `--workload batched|served|population` runs one of those workloads at its
 full size instead and prints its own line.
 
@@ -427,6 +428,52 @@ def measure_population(gsh, subjects=34, n=1847, T=40, max_iter=400, sigma=SIGMA
     }
 
 
+def measure_variants(gsh, reps=50, fit_iters=30):
+    """The RK4 integrator against the paper's Euler steps at equal pair work
+    (RK4 with T = 5 evaluates the pair sums 20 times per sweep, as Euler
+    with T = 20 does): gradient evaluations per second of each (device
+    inputs, CUDA events, median of `reps`), and the error of each q(1)
+    against an RK4 solution with T = 80, relative to the displacement
+    q(1) - q0.  The momenta are those of a registration of the workload
+    (`fit_iters` L-BFGS iterations from zero), so the flow is the smooth
+    deformation a registration produces."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    q0, _, t = workload()
+    p0, _ = gsh.register(q0, t, T_STEPS, SIGMA, LAMBDA, max_iter=fit_iters, grad_tol=0.0)
+    p0 = np.ascontiguousarray(p0, np.float32)
+    dq, dp, dt = (torch.from_numpy(a).to(dev) for a in (q0, p0, t))
+    stream = torch.cuda.current_stream(dev)
+
+    def rate(T, integ, h_at="start"):
+        f = lambda: gsh.shoot_gradient(dq, dp, dt, T, SIGMA, LAMBDA, integrator=integ, h_at=h_at)
+        for _ in range(3):
+            f()
+        torch.cuda.synchronize(dev)
+        out = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            f()
+            b.record(stream)
+            b.synchronize()
+            out.append(a.elapsed_time(b))
+        return 1e3 / float(np.median(out))
+
+    ref = gsh.shoot_forward(dq, dp, 80, SIGMA, integrator="rk4")[0].double()
+    disp = float(torch.linalg.norm(ref - dq.double()))
+    err = lambda T, integ: float(torch.linalg.norm(gsh.shoot_forward(dq, dp, T, SIGMA, integrator=integ)[0].double()
+                                                   - ref)) / disp
+    return {
+        "N": q0.shape[0], "p0": "%d L-BFGS iterations of the workload's registration" % fit_iters,
+        "reference": "RK4, T = 80", "displacement_rms": disp / np.sqrt(q0.shape[0]),
+        "euler_T20": {"grad_evals_per_s": rate(20, "euler"), "q1_rel_err": err(20, "euler")},
+        "rk4_T5": {"grad_evals_per_s": rate(5, "rk4"), "q1_rel_err": err(5, "rk4")},
+        "rk4_T5_kinetic_end": {"grad_evals_per_s": rate(5, "rk4", "end")},
+        "timing": "shoot_gradient through the binding, CUDA events, median of %d" % reps,
+    }
+
+
 def velocity_grid(n_side=101, half=1.2):
     """Query points of the deformation: a regular n_side^3 grid over the
     box [-half, half]^3 that holds the ellipsoid (an image grid stand-in)."""
@@ -662,6 +709,7 @@ def run_gshoot(args, dist):
         line["served"] = measure_served(gsh, args.served_count or 8)
         line["velocity"] = measure_velocity(gsh)
         line["population"] = measure_population(gsh)
+        line["variants"] = measure_variants(gsh)
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_gradient_sample()
     if dist.rank == 0:

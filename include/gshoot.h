@@ -55,10 +55,27 @@ typedef enum gs_status {
     GS_ENOLIB = -6          /* no usable CUDA device */
 } gs_status;
 
+/* Time integrators of the flow (gs_params.integrator). */
+enum {
+    GS_EULER = 0,  /* explicit Euler, Algorithm 1: q <- q + dt Hp, p <- p - dt Hq */
+    GS_RK4 = 1     /* classical fourth-order Runge-Kutta on y = (q, p), f = (Hp, -Hq):
+                      k1 = f(y), k2 = f(y + dt/2 k1), k3 = f(y + dt/2 k2),
+                      k4 = f(y + dt k3), y <- y + dt/6 (k1 + 2 k2 + 2 k3 + k4);
+                      four pair-sum evaluations per step */
+};
+
+/* Where the kinetic term of the loss is evaluated (gs_params.kinetic_at). */
+enum {
+    GS_KINETIC_START = 0,  /* L = H(p0, q0) + lambda ||q(1) - target||^2 (Eq. 3) */
+    GS_KINETIC_END = 1     /* L = H(p(1), q(1)) + lambda ||q(1) - target||^2, the form of
+                              Algorithm 1's pseudocode (its loss line); the flow
+                              conserves H, the discrete steps only approximately */
+};
+
 /* Parameters of one registration problem (Algorithm 1 inputs, Section 2.2). */
 typedef struct gs_params {
     int64_t N;          /* number of landmarks, >= 1 */
-    int32_t T;          /* number of Euler time steps, >= 1; dt = 1/T */
+    int32_t T;          /* number of time steps, >= 1; dt = 1/T */
     int32_t ckpt_every; /* 0: keep the whole trajectory; k > 0: keep the FP64
                            state every k steps and recompute the rest in the
                            reverse sweep */
@@ -67,6 +84,9 @@ typedef struct gs_params {
     int32_t lbfgs_m;    /* L-BFGS memory (pairs kept), 1..64 (register only) */
     int32_t max_iter;   /* L-BFGS iteration limit (register only) */
     double grad_tol;    /* stop when ||g_k|| <= grad_tol ||g_0|| (register only) */
+    int32_t integrator; /* GS_EULER (0, the paper's) or GS_RK4; the gradient is
+                           always the exact adjoint of the chosen steps */
+    int32_t kinetic_at; /* GS_KINETIC_START (0) or GS_KINETIC_END */
 } gs_params;
 
 /*
@@ -95,9 +115,10 @@ gs_status step_backward(int64_t N, double sigma, const float* q, const float* p,
 
 /*
  * shoot_forward — the forward flow of Algorithm 1 (its forward loop): T explicit
- * Euler steps q <- q + dt Hp, p <- p - dt Hq from (q0, p0).
- * In: prm (N, T, sigma used), q0, p0.  Out: q1, p1 = state at t = 1 (either
- * may be NULL), *H0 = H(p0, q0) (Eq. 1) in FP64 (NULL to skip).
+ * Euler steps q <- q + dt Hp, p <- p - dt Hq from (q0, p0), or T RK4 steps
+ * when prm->integrator is GS_RK4.
+ * In: prm (N, T, sigma, integrator used), q0, p0.  Out: q1, p1 = state at
+ * t = 1 (either may be NULL), *H0 = H(p0, q0) (Eq. 1) in FP64 (NULL to skip).
  */
 gs_status shoot_forward(const gs_params* prm, const float* q0, const float* p0,
                         float* q1, float* p1, double* H0, void* stream);
@@ -105,9 +126,16 @@ gs_status shoot_forward(const gs_params* prm, const float* q0, const float* p0,
 /*
  * shoot_gradient — ComputeGradient of Algorithm 1: forward flow, the loss of
  * Eq. 3, and the reverse sweep.
- * In: prm (N, T, sigma, lambda, ckpt_every used), q0, p0, target.
+ * In: prm (N, T, sigma, lambda, ckpt_every, integrator, kinetic_at used),
+ *     q0, p0, target.
  * Out: *loss (FP64, NULL to skip), grad_p0 = dL/dp0 (NULL to skip),
  *      grad_q0 = dL/dq0 (NULL to skip), all (N,3) float32.
+ * Variants: with GS_RK4 the reverse sweep is the exact adjoint of the RK4
+ * steps (StepBackward at each of the four stage states of a step, applied to
+ * stage adjoints built from the step's adjoint and the next stage's result).
+ * With GS_KINETIC_END the adjoint starts from alpha(1) = 2 lambda (q(1) -
+ * target) + Hq(q(1), p(1)), beta(1) = Hp(q(1), p(1)), and the gradient has no
+ * H(p0, q0) term.
  */
 gs_status shoot_gradient(const gs_params* prm, const float* q0, const float* p0,
                          const float* target, double* loss,
@@ -150,7 +178,8 @@ gs_status velocity_field(int64_t N, int64_t M, double sigma, const float* q, con
  * between steps.
  * In: prm (N, T, sigma used), q0, p0 (N, 3), x0 (M, 3).  Out: x1 (M, 3).
  * Arrays as in velocity_field.  Errors as in shoot_forward; M outside
- * [1, 2^26] or a NULL point array is GS_EINVAL.
+ * [1, 2^26] or a NULL point array is GS_EINVAL, and so is an integrator
+ * other than GS_EULER (the points take Euler steps only).
  */
 gs_status flow_points(const gs_params* prm, const float* q0, const float* p0, int64_t M,
                       const float* x0, float* x1, void* stream);
@@ -197,6 +226,8 @@ typedef struct gs_batch_problem {
  * register_batch — B independent runs of register_landmarks, packed: every
  * time step of every gradient evaluation is one launch over all problems
  * still running.  Shared settings: T, lbfgs_m (1..64), max_iter, grad_tol.
+ * Every problem uses the Euler integrator and the kinetic term at t = 0
+ * (GS_EULER, GS_KINETIC_START), as does the server.
  * Writes probs[b].p0 (when non-NULL) and probs[b].info.  Each problem
  * follows the same L-BFGS as register_landmarks.  Returns GS_OK,
  * GS_NOT_CONVERGED if any problem stopped short of grad_tol, or the first
@@ -369,7 +400,8 @@ const char* gs_last_error(void);
 /* Free the device workspace and cached CUDA graphs of every device. */
 void gs_release_workspace(void);
 
-/* Library ABI version: 100 * major + minor. */
+/* Library ABI version: 100 * major + minor (101: gs_params gained
+ * integrator and kinetic_at). */
 int32_t gs_version(void);
 
 #ifdef __cplusplus

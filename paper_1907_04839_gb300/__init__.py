@@ -16,8 +16,8 @@ import ctypes
 
 import numpy as np
 
-from ._lib import (EXPORTS, GShootError, GsBatchProblem, GsParams, GsRegisterInfo, GsServerConfig, check,
-                   load)
+from ._lib import (EXPORTS, INTEGRATORS, KINETIC_AT, GShootError, GsBatchProblem, GsParams, GsRegisterInfo,
+                   GsServerConfig, check, load)
 
 __all__ = [
     "step_forward", "step_backward", "shoot_forward", "shoot_gradient", "register", "shoot",
@@ -89,10 +89,15 @@ class _Marshal:
         return t, ctypes.c_void_p(ptr)
 
 
-def _params(n, T, sigma, lam=0.0, ckpt_every=0, lbfgs_m=10, max_iter=100, grad_tol=1e-5):
+def _params(n, T, sigma, lam=0.0, ckpt_every=0, lbfgs_m=10, max_iter=100, grad_tol=1e-5, integrator="euler",
+            h_at="start"):
+    if integrator not in INTEGRATORS:
+        raise ValueError("integrator must be one of %r" % sorted(INTEGRATORS))
+    if h_at not in KINETIC_AT:
+        raise ValueError("h_at must be one of %r" % sorted(KINETIC_AT))
     return GsParams(N=int(n), T=int(T), ckpt_every=int(ckpt_every), sigma=float(sigma),
                     lambda_=float(lam), lbfgs_m=int(lbfgs_m), max_iter=int(max_iter),
-                    grad_tol=float(grad_tol))
+                    grad_tol=float(grad_tol), integrator=INTEGRATORS[integrator], kinetic_at=KINETIC_AT[h_at])
 
 
 def step_forward(q, p, sigma):
@@ -141,11 +146,12 @@ def step_backward(q, p, alpha, beta, sigma):
     return da, db
 
 
-def shoot_forward(q0, p0, T, sigma):
-    """Forward flow of Algorithm 1: returns (q1, p1, H0) with H0 = H(p0, q0)."""
+def shoot_forward(q0, p0, T, sigma, integrator="euler"):
+    """Forward flow of Algorithm 1: returns (q1, p1, H0) with H0 = H(p0, q0).
+    integrator: "euler" (the paper's) or "rk4"."""
     m = _Marshal(q0)
     pq, pp = m.inp(q0, "q0"), m.inp(p0, "p0")
-    prm = _params(m.n, T, sigma)
+    prm = _params(m.n, T, sigma, integrator=integrator)
     q1, o1 = m.out()
     p1, o2 = m.out()
     h0 = ctypes.c_double(0.0)
@@ -153,12 +159,13 @@ def shoot_forward(q0, p0, T, sigma):
     return q1, p1, h0.value
 
 
-def shoot_gradient(q0, p0, target, T, sigma, lam, ckpt_every=0):
+def shoot_gradient(q0, p0, target, T, sigma, lam, ckpt_every=0, integrator="euler", h_at="start"):
     """ComputeGradient of Algorithm 1: returns (loss, dL/dp0, dL/dq0) for
-    L = H(p0, q0) + lam ||q(1) - target||^2."""
+    L = H(p0, q0) + lam ||q(1) - target||^2 (h_at="end": H(p(1), q(1))
+    instead), with the flow integrated by "euler" or "rk4" steps."""
     m = _Marshal(q0)
     pq, pp, pt = m.inp(q0, "q0"), m.inp(p0, "p0"), m.inp(target, "target")
-    prm = _params(m.n, T, sigma, lam, ckpt_every)
+    prm = _params(m.n, T, sigma, lam, ckpt_every, integrator=integrator, h_at=h_at)
     gp, og = m.out()
     gq, oq = m.out()
     loss = ctypes.c_double(0.0)
@@ -178,8 +185,8 @@ def _shoot_function():
 
         class ShootLoss(torch.autograd.Function):
             @staticmethod
-            def forward(ctx, q0, p0, target, T, sigma, lam, ckpt_every):
-                loss, gp, gq = shoot_gradient(q0, p0, target, T, sigma, lam, ckpt_every)
+            def forward(ctx, q0, p0, target, T, sigma, lam, ckpt_every, integrator, h_at):
+                loss, gp, gq = shoot_gradient(q0, p0, target, T, sigma, lam, ckpt_every, integrator, h_at)
                 if not isinstance(gp, torch.Tensor):
                     gp, gq = torch.from_numpy(gp), torch.from_numpy(gq)
                 ctx.save_for_backward(gq, gp)
@@ -191,27 +198,30 @@ def _shoot_function():
                 gq, gp = ctx.saved_tensors
                 dq = (gout.to(gq.dtype) * gq).to(ctx.dtypes[0]) if ctx.needs_input_grad[0] else None
                 dp = (gout.to(gp.dtype) * gp).to(ctx.dtypes[1]) if ctx.needs_input_grad[1] else None
-                return dq, dp, None, None, None, None, None
+                return dq, dp, None, None, None, None, None, None, None
 
         _SHOOT_FN = ShootLoss
     return _SHOOT_FN
 
 
-def shoot(q0, p0, target, T, sigma, lam, ckpt_every=0):
+def shoot(q0, p0, target, T, sigma, lam, ckpt_every=0, integrator="euler", h_at="start"):
     """The loss of Eq. 3 as a differentiable torch scalar (FP64).
 
     Backward gives dL/dq0 and dL/dp0 (no gradient flows to ``target``).  Both
     come from the same library call as the loss: the forward flow, the loss,
-    and the exact reverse sweep of the Euler steps.  With ``ckpt_every = k``
+    and the exact reverse sweep of the time steps ("euler" or "rk4"; h_at
+    places the kinetic term at t = 0 or t = 1).  With ``ckpt_every = k``
     (0 < k < T), the reverse sweep keeps the state only every k steps and
     recomputes the rest.  The results are bitwise identical."""
-    return _shoot_function().apply(q0, p0, target, T, sigma, lam, ckpt_every)
+    return _shoot_function().apply(q0, p0, target, T, sigma, lam, ckpt_every, integrator, h_at)
 
 
-def register(q0, target, T, sigma, lam, p0=None, m=10, max_iter=100, grad_tol=1e-5):
+def register(q0, target, T, sigma, lam, p0=None, m=10, max_iter=100, grad_tol=1e-5, integrator="euler",
+             h_at="start"):
     """Algorithm 1, outer optimisation: L-BFGS over p0 of the Eq. 3 loss.  Returns
     (p0, info) with info a dict (loss, grad_norm0, grad_norm, avg_dist,
-    max_dist, iters, evals, status)."""
+    max_dist, iters, evals, status).  integrator / h_at select the variant
+    of the discretisation as in shoot_gradient."""
     m_ = _Marshal(q0)
     pq, pt = m_.inp(q0, "q0"), m_.inp(target, "target")
     if p0 is None:
@@ -225,7 +235,7 @@ def register(q0, target, T, sigma, lam, p0=None, m=10, max_iter=100, grad_tol=1e
         pp = ctypes.c_void_p(pout.ctypes.data)
     if tuple(pout.shape) != (m_.n, 3):
         raise ValueError("p0: expected shape (%d, 3)" % m_.n)
-    prm = _params(m_.n, T, sigma, lam, 0, m, max_iter, grad_tol)
+    prm = _params(m_.n, T, sigma, lam, 0, m, max_iter, grad_tol, integrator, h_at)
     info = GsRegisterInfo()
     check(load().register_landmarks(ctypes.byref(prm), pq, pt, pp, ctypes.byref(info), m_.stream))
     return pout, info.as_dict()

@@ -44,7 +44,14 @@ class GsParams(ctypes.Structure):
         ("lbfgs_m", ctypes.c_int32),
         ("max_iter", ctypes.c_int32),
         ("grad_tol", ctypes.c_double),
+        ("integrator", ctypes.c_int32),
+        ("kinetic_at", ctypes.c_int32),
     ]
+
+
+# gs_params.integrator and gs_params.kinetic_at values (include/gshoot.h).
+INTEGRATORS = {"euler": 0, "rk4": 1}
+KINETIC_AT = {"start": 0, "end": 1}
 
 
 class GsRegisterInfo(ctypes.Structure):

@@ -89,6 +89,10 @@ gs_status reserve(Workspace& w, int npad, int T, int splits, int nck) {
   GS_CUDA(dalloc(w, &w.hp0, n3));
   GS_CUDA(dalloc(w, &w.hq0, n3));
   GS_CUDA(dalloc(w, &w.gp64, n3));
+  GS_CUDA(dalloc(w, &w.qa64, n3));
+  GS_CUDA(dalloc(w, &w.pa64, n3));
+  GS_CUDA(dalloc(w, &w.ya64, n3));
+  GS_CUDA(dalloc(w, &w.yb64, n3));
   if (ck > 0) GS_CUDA(dalloc(w, &w.ck64, 2 * static_cast<size_t>(ck) * n3));
   GS_CUDA(dalloc(w, &w.part, static_cast<size_t>(cs) * cn));
   GS_CUDA(dalloc(w, &w.in_q, n3));
@@ -177,20 +181,30 @@ gs_status check_params(const gs_params* prm) {
   if (!(prm->sigma > 0.0) || !std::isfinite(prm->sigma)) return fail(GS_EINVAL, "sigma must be finite and > 0");
   if (!(prm->lambda >= 0.0) || !std::isfinite(prm->lambda)) return fail(GS_EINVAL, "lambda must be finite and >= 0");
   if (prm->ckpt_every < 0) return fail(GS_EINVAL, "ckpt_every must be >= 0");
+  if (prm->integrator != GS_EULER && prm->integrator != GS_RK4)
+    return fail(GS_EINVAL, "integrator must be GS_EULER or GS_RK4");
+  if (prm->kinetic_at != GS_KINETIC_START && prm->kinetic_at != GS_KINETIC_END)
+    return fail(GS_EINVAL, "kinetic_at must be GS_KINETIC_START or GS_KINETIC_END");
   return GS_OK;
 }
 
 // Arguments of fused forward step k (kind 1: the last step also forms the
-// loss and the adjoint initialisation).
+// loss and the adjoint initialisation).  For RK4 (integ), a launch is stage
+// `stage` of step k; rd / wr default to the record slots of launch
+// S*k + stage and the one after it.  h_end: the loss is formed by a separate
+// terminal launch instead of the last step.
 StepFwdArgs forward_step_args(Workspace& w, const StepConfig& c, int kind, int n, int T, int k, double sigma,
-                              double lambda, int rd = -1, int wr = -1, bool recompute = false) {
+                              double lambda, int rd = -1, int wr = -1, bool recompute = false, int integ = GS_EULER,
+                              int stage = 0, int h_end = 0) {
+  const int S = stages_of(integ);
+  const int j = S * k + stage;  // launch index of the sweep
   const int npad = round_up(n, kPad);
   const KernelScales sc = make_scales(sigma);
   const size_t slot = w.slot();
   StepFwdArgs a;
   std::memset(&a, 0, sizeof(a));
-  a.qp = w.traj + (rd < 0 ? k : rd) * slot;
-  a.qp_next = w.traj + (wr < 0 ? k + 1 : wr) * slot;
+  a.qp = w.traj + (rd < 0 ? j : rd) * slot;
+  a.qp_next = w.traj + (wr < 0 ? j + 1 : wr) * slot;
   a.n = n;
   a.npad = npad;
   a.split_len = c.split_len;
@@ -200,11 +214,16 @@ StepFwdArgs forward_step_args(Workspace& w, const StepConfig& c, int kind, int n
   a.q64 = w.q64;
   a.p64 = w.p64;
   // A recomputed step (checkpointed reverse sweep) only rebuilds the state.
-  a.first = (k == 0) && !recompute;
+  a.first = (j == 0) && !recompute;
   a.hp0 = w.hp0;
   a.hq0 = w.hq0;
-  a.last = (k == T - 1) && !recompute;
-  a.with_loss = (kind == 1) && !recompute;
+  a.last = (j == S * T - 1) && !recompute;
+  a.with_loss = (kind == 1) && !recompute && !h_end;
+  a.rk = integ == GS_RK4;
+  a.stage = stage;
+  a.qa64 = w.qa64;
+  a.pa64 = w.pa64;
+  a.adj_scale = integ == GS_RK4 ? (1.0 / T) / 6.0 : 1.0;
   a.t64 = w.t64;
   a.lambda = lambda;
   a.a64 = w.a64;
@@ -219,17 +238,26 @@ StepFwdArgs forward_step_args(Workspace& w, const StepConfig& c, int kind, int n
   return a;
 }
 
-// Arguments of fused reverse step number s = 0..T-1 (time step k = T-1-s).
-StepBwdArgs backward_step_args(Workspace& w, const StepConfig& c, int n, int T, int s, double sigma, int rd = -1) {
+// Arguments of fused reverse launch number s = 0..S*T-1 (time step
+// k = T-1-s/S, stage S-1-s%S; S = 1 for Euler, 4 for RK4).  rd defaults to
+// the record slot of that stage state.
+StepBwdArgs backward_step_args(Workspace& w, const StepConfig& c, int n, int T, int s, double sigma, int rd = -1,
+                               int integ = GS_EULER, int h_end = 0) {
   const int npad = round_up(n, kPad);
   const KernelScales sc = make_scales(sigma);
   const size_t slot = w.slot();
-  const int k = T - 1 - s;
+  const int S = stages_of(integ);
+  const int k = T - 1 - s / S, stage = S - 1 - s % S;
   StepBwdArgs b;
   std::memset(&b, 0, sizeof(b));
-  b.qp = w.traj + (rd < 0 ? k : rd) * slot;
+  b.qp = w.traj + (rd < 0 ? S * k + stage : rd) * slot;
   b.ab = w.adj + (s & 1) * slot;
   b.ab_next = w.adj + ((s + 1) & 1) * slot;
+  b.rk = integ == GS_RK4;
+  b.stage = stage;
+  b.ya64 = w.ya64;
+  b.yb64 = w.yb64;
+  b.h_at_end = h_end;
   b.n = n;
   b.npad = npad;
   b.split_len = c.split_len;
@@ -239,7 +267,7 @@ StepBwdArgs backward_step_args(Workspace& w, const StepConfig& c, int n, int T, 
   b.kappa64 = sc.kappa;
   b.a64 = w.a64;
   b.b64 = w.b64;
-  b.first = (k == 0);
+  b.first = (k == 0 && stage == 0);
   b.hp0 = w.hp0;
   b.hq0 = w.hq0;
   b.grad_p0 = w.out_a;
@@ -250,22 +278,31 @@ StepBwdArgs backward_step_args(Workspace& w, const StepConfig& c, int n, int T, 
 }
 
 // Enqueue the T forward steps (and, for kind 1, the loss and T reverse
-// steps): one fused cluster kernel per time step.
+// steps): one fused cluster kernel per time step, or per stage of an RK4
+// step (S = 4 launches per step; record slot S*k + s holds the state of
+// stage s of step k, slot S*T the end state).  With the kinetic term at
+// t = 1 (h_end), a terminal launch at the end state forms the loss and the
+// adjoint initialisation.
 //
 // With a checkpoint interval c (0 < c < T), the forward sweep keeps only the
-// FP64 state at steps 0, c, 2c, ...  The reverse sweep handles the segments
-// from the last to the first.  For each segment it restores the checkpoint,
-// recomputes the segment's forward steps into record slots 0..c-1, then runs
-// its reverse steps.  Each recomputed record is bitwise the one the forward
-// sweep made, because it comes from the same FP64 state through the same
-// kernels.
-gs_status enqueue_steps(Workspace& w, int kind, int n, int T, double sigma, double lambda, int ckpt,
-                        cudaStream_t st, const cudaEvent_t* ev) {
+// FP64 state at steps 0, c, 2c, ... (records go round two slots).  The
+// reverse sweep handles the segments from the last to the first.  For each
+// segment it restores the checkpoint, recomputes the segment's stage records
+// into slots 0..S*len-1, then runs its reverse launches.  Each recomputed
+// record is bitwise the one the forward sweep made, because it comes from
+// the same FP64 state through the same kernels.
+gs_status enqueue_steps(Workspace& w, int kind, int n, int T, double sigma, double lambda, int ckpt, int integ,
+                        int h_end, cudaStream_t st, const cudaEvent_t* ev) {
   const int npad = round_up(n, kPad);
-  const StepConfig fc = choose_step_config(0, npad, w.num_sms);
-  const StepConfig bc = choose_step_config(1, npad, w.num_sms);
+  if (kind == 0) {
+    ckpt = 0;
+    h_end = 0;
+  }
+  const bool variants = integ != GS_EULER || h_end;
+  const StepConfig fc = choose_step_config(0, npad, w.num_sms, variants);
+  const StepConfig bc = choose_step_config(1, npad, w.num_sms, variants);
   if (fc.threads == 0 || bc.threads == 0) return fail(GS_EINVAL, "no step kernel configuration");
-  if (kind == 0) ckpt = 0;
+  const int S = stages_of(integ);
   const size_t n3 = 3 * static_cast<size_t>(n);
   if (ev) GS_CUDA(cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal));
   for (int k = 0; k < T; ++k) {
@@ -274,9 +311,20 @@ gs_status enqueue_steps(Workspace& w, int kind, int n, int T, double sigma, doub
       GS_CUDA(cudaMemcpyAsync(ck, w.q64, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
       GS_CUDA(cudaMemcpyAsync(ck + n3, w.p64, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
-    const int rd = ckpt ? (k & 1) : k, wr = ckpt ? ((k + 1) & 1) : k + 1;
-    const StepFwdArgs a = forward_step_args(w, fc, kind, n, T, k, sigma, lambda, rd, wr, false);
-    GS_CUDA(launch_step_forward(fc, a, st, k > 0));
+    for (int s = 0; s < S; ++s) {
+      const int j = S * k + s;
+      const int rd = ckpt ? (j & 1) : -1, wr = ckpt ? ((j + 1) & 1) : -1;
+      const StepFwdArgs a = forward_step_args(w, fc, kind, n, T, k, sigma, lambda, rd, wr, false, integ, s, h_end);
+      GS_CUDA(launch_step_forward(fc, a, st, j > 0));
+    }
+  }
+  if (h_end) {
+    const int rd = ckpt ? ((S * T) & 1) : S * T;
+    StepFwdArgs a = forward_step_args(w, fc, kind, n, T, T - 1, sigma, lambda, rd, rd, true, integ, 0, 1);
+    a.terminal = 1;
+    a.last = 1;
+    a.with_loss = 1;
+    GS_CUDA(launch_step_forward(fc, a, st, true));
   }
   if (ev) GS_CUDA(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
   if (kind == 0) {
@@ -284,8 +332,8 @@ gs_status enqueue_steps(Workspace& w, int kind, int n, int T, double sigma, doub
     return GS_OK;
   }
   if (!ckpt) {
-    for (int s = 0; s < T; ++s) {
-      const StepBwdArgs b = backward_step_args(w, bc, n, T, s, sigma);
+    for (int s = 0; s < S * T; ++s) {
+      const StepBwdArgs b = backward_step_args(w, bc, n, T, s, sigma, -1, integ, h_end);
       GS_CUDA(launch_step_backward(bc, b, st, true));
     }
     if (ev) GS_CUDA(cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal));
@@ -293,17 +341,19 @@ gs_status enqueue_steps(Workspace& w, int kind, int n, int T, double sigma, doub
   }
   const KernelScales sc = make_scales(sigma);
   const int nseg = (T + ckpt - 1) / ckpt;
-  int s = 0;  // reverse-step counter (picks the adjoint buffers)
+  int s = 0;  // reverse-launch counter (picks the adjoint buffers)
   for (int m = nseg - 1; m >= 0; --m) {
     const int s0 = m * ckpt, len = std::min(ckpt, T - s0);
     const double* ck = w.ck64 + 2 * static_cast<size_t>(m) * n3;
     GS_CUDA(launch_restore(ck, ck + n3, w.q64, w.p64, w.traj, n, sc.kq, st));
-    for (int r = 0; r + 1 < len; ++r) {
-      const StepFwdArgs a = forward_step_args(w, fc, kind, n, T, s0 + r, sigma, lambda, r, r + 1, true);
+    // stage launches 0 .. S*len-2 of the segment write slots 1 .. S*len-1
+    for (int r = 0; r + 1 < S * len; ++r) {
+      const StepFwdArgs a =
+          forward_step_args(w, fc, kind, n, T, s0 + r / S, sigma, lambda, r, r + 1, true, integ, r % S, h_end);
       GS_CUDA(launch_step_forward(fc, a, st, r > 0));
     }
-    for (int r = len - 1; r >= 0; --r, ++s) {
-      const StepBwdArgs b = backward_step_args(w, bc, n, T, s, sigma, r);
+    for (int r = S * len - 1; r >= 0; --r, ++s) {
+      const StepBwdArgs b = backward_step_args(w, bc, n, T, s, sigma, r, integ, h_end);
       GS_CUDA(launch_step_backward(bc, b, st, true));
     }
   }
@@ -320,7 +370,7 @@ gs_status get_graph(Workspace& w, const GraphKey& key, cudaGraphExec_t* out) {
   if (w.graphs.size() >= 16) w.drop_graphs();
   cudaStream_t cs = w.capture_stream;
   GS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  gs_status s = enqueue_steps(w, key.kind, key.n, key.T, key.sigma, key.lambda, key.ckpt, cs,
+  gs_status s = enqueue_steps(w, key.kind, key.n, key.T, key.sigma, key.lambda, key.ckpt, key.integ, key.h_end, cs,
                               key.timed ? w.phase : nullptr);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(cs, &g);
@@ -357,7 +407,8 @@ gs_status enqueue_gradient64(Workspace& w, const gs_params& prm, const float* dq
   pk.status = w.status;
   GS_CUDA(launch_pack(pk, st));
   cudaGraphExec_t ge = nullptr;
-  const GraphKey key{1, n, prm.T, prm.sigma, prm.lambda, effective_ckpt(prm.ckpt_every, prm.T), w.phase_timing};
+  const GraphKey key{1,           n, prm.T, prm.sigma, prm.lambda, effective_ckpt(prm.ckpt_every, prm.T), w.phase_timing,
+                     prm.integrator, prm.kinetic_at};
   if ((s = get_graph(w, key, &ge)) != GS_OK) return s;
   GS_CUDA(cudaGraphLaunch(ge, st));
   return GS_OK;
@@ -382,7 +433,8 @@ gs_status enqueue_forward64(Workspace& w, const gs_params& prm, const float* dq,
   pk.status = w.status;
   GS_CUDA(launch_pack(pk, st));
   cudaGraphExec_t ge = nullptr;
-  if ((s = get_graph(w, GraphKey{0, n, prm.T, prm.sigma, 0.0, 0, w.phase_timing}, &ge)) != GS_OK) return s;
+  if ((s = get_graph(w, GraphKey{0, n, prm.T, prm.sigma, 0.0, 0, w.phase_timing, prm.integrator, 0}, &ge)) != GS_OK)
+    return s;
   GS_CUDA(cudaGraphLaunch(ge, st));
   return GS_OK;
 }
@@ -399,7 +451,9 @@ gs_status run_shoot(int kind, const gs_params* prm, const float* q0, const float
   const int n = static_cast<int>(prm->N), T = prm->T;
   const int npad = round_up(n, kPad);
   const int ckpt = kind == 1 ? effective_ckpt(prm->ckpt_every, T) : 0;
-  if ((s = reserve(*w, npad, record_slots(T, ckpt), 1, ckpt ? (T + ckpt - 1) / ckpt : 0)) != GS_OK) return s;
+  if ((s = reserve(*w, npad, record_slots(T, ckpt, stages_of(prm->integrator)), 1, ckpt ? (T + ckpt - 1) / ckpt : 0)) !=
+      GS_OK)
+    return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if ((s = ensure_clean(*w, n, st)) != GS_OK) return s;
   const size_t n3 = 3 * static_cast<size_t>(n);
@@ -422,7 +476,8 @@ gs_status run_shoot(int kind, const gs_params* prm, const float* q0, const float
   pk.status = w->status;
   GS_CUDA(launch_pack(pk, st));
   cudaGraphExec_t ge = nullptr;
-  const GraphKey key{kind, n, T, prm->sigma, kind == 1 ? prm->lambda : 0.0, ckpt, w->phase_timing};
+  const GraphKey key{kind,           n, T, prm->sigma, kind == 1 ? prm->lambda : 0.0, ckpt, w->phase_timing,
+                     prm->integrator, kind == 1 ? prm->kinetic_at : 0};
   if ((s = get_graph(*w, key, &ge)) != GS_OK) return s;
   GS_CUDA(cudaGraphLaunch(ge, st));
   bool want_sync = host;
@@ -553,7 +608,8 @@ gs_status time_pair_kernels(const gs_params* prm, const float* q0, const float* 
   cudaEventDestroy(e2);
   if (fwd_ms) *fwd_ms = m1 / reps;
   if (bwd_ms) *bwd_ms = m2 / reps;
-  if (launches) *launches = 2 * T + 1;
+  // pack, S launches per forward step, the terminal launch, S per reverse step
+  if (launches) *launches = 2 * stages_of(prm->integrator) * T + 1 + (prm->kinetic_at == GS_KINETIC_END ? 1 : 0);
   return finish_sync(*w, st);
 }
 
@@ -805,6 +861,6 @@ void gs_release_workspace(void) {
   gs::g_ws.clear();
 }
 
-int32_t gs_version(void) { return 100; }
+int32_t gs_version(void) { return 101; }
 
 }  // extern "C"

@@ -33,16 +33,24 @@ struct GraphKey {
   double sigma, lambda;
   int ckpt;       // checkpoint interval of the reverse sweep (0: whole trajectory)
   int timed = 0;  // records the workspace's phase events
+  int integ = 0;  // GS_EULER or GS_RK4
+  int h_end = 0;  // the loss takes the kinetic term at t = 1
   bool operator<(const GraphKey& o) const {
-    return std::tie(kind, n, T, sigma, lambda, ckpt, timed) <
-           std::tie(o.kind, o.n, o.T, o.sigma, o.lambda, o.ckpt, o.timed);
+    return std::tie(kind, n, T, sigma, lambda, ckpt, timed, integ, h_end) <
+           std::tie(o.kind, o.n, o.T, o.sigma, o.lambda, o.ckpt, o.timed, o.integ, o.h_end);
   }
 };
 
+// Pair-sum evaluations (stages) per time step of an integrator.
+inline int stages_of(int integ) { return integ == GS_RK4 ? 4 : 1; }
 // Effective checkpoint interval for T steps: 0 keeps the whole trajectory.
 inline int effective_ckpt(int ckpt_every, int T) { return (ckpt_every > 0 && ckpt_every < T) ? ckpt_every : 0; }
-// Trajectory record slots needed (slots 0..return value).
-inline int record_slots(int T, int ckpt) { return ckpt ? (ckpt > 2 ? ckpt : 2) : T; }
+// Trajectory record slots needed (slots 0..return value): one record per
+// stage state and the end state; with checkpointing, the stage states of one
+// segment.
+inline int record_slots(int T, int ckpt, int stages = 1) {
+  return ckpt ? (stages * ckpt > 2 ? stages * ckpt : 2) : stages * T;
+}
 
 // FP64 vectors of the device-resident L-BFGS (register_landmarks).
 struct LbfgsBufs {
@@ -72,6 +80,8 @@ struct Workspace {
   size_t slot() const { return static_cast<size_t>(kRecF4) * (cap_npad / 2); }  // float4 per slot
   double *q64 = nullptr, *p64 = nullptr, *a64 = nullptr, *b64 = nullptr, *t64 = nullptr;
   double *hp0 = nullptr, *hq0 = nullptr;
+  double *qa64 = nullptr, *pa64 = nullptr;  // RK4 stage accumulators (forward)
+  double *ya64 = nullptr, *yb64 = nullptr;  // RK4 start-state adjoint (reverse)
   double* gp64 = nullptr;  // FP64 dL/dp0 of the last gradient
   double* ck64 = nullptr;  // cap_ck checkpoints of the FP64 state: (q64, p64) pairs
   Partial* part = nullptr;   // cap_splits * cap_npad

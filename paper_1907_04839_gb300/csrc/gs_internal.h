@@ -130,9 +130,18 @@ struct StepFwdArgs {
   double* red_h;       // per-CTA partial sums (grid-sized)
   double* red_m;
   unsigned* ticket;
-  double* scalars;     // [0] = H0, [1] = loss
+  double* scalars;     // [0] = H0, [1] = loss, [2] = H at the end state (terminal launch)
   int dry;             // tuning: compute everything, write nothing
   unsigned* status;
+  // Variants (all zero: an Euler step, the kinetic term at t = 0).
+  int rk;              // 1: stage `stage` (0..3) of an RK4 step
+  int stage;
+  double* qa64;        // RK4: FP64 accumulators k1 + 2 k2 + 2 k3 (q and p parts)
+  double* pa64;
+  int terminal;        // evaluate at the end state: H(p(1), q(1)), the loss and
+                       // the adjoint initialisation; no state update
+  double adj_scale;    // factor of the adjoint record written at the loss
+                       // (terminal launch, or the last RK4 stage): dt/6 for RK4, 1 for Euler
 };
 
 struct StepBwdArgs {
@@ -152,6 +161,14 @@ struct StepBwdArgs {
   double* grad_p0_64;  // FP64 copy of dL/dp0 (may be null)
   int dry;
   unsigned* status;
+  // Variants (all zero: a reverse Euler step, gradient with the H(p0, q0) term).
+  int rk;              // 1: stage `stage` (3..0) of the reverse of an RK4 step; the
+                       // AB record then holds the stage adjoint, a64/b64 the
+                       // adjoint of the step's end state
+  int stage;
+  double* ya64;        // RK4: FP64 adjoint of the step's start state, summed over the stages
+  double* yb64;
+  int h_at_end;        // the loss takes H at t = 1: no H(p0, q0) term in the gradient
 };
 
 // Packed batches of independent problems.  Problem b occupies landmarks
@@ -169,7 +186,15 @@ struct BatchTables {
 };
 
 StepConfig step_config_for(int kind, int npad, int threads, int R, int cluster, int groups = 1);
-StepConfig choose_step_config(int kind, int npad, int num_sms);
+// The built-in configuration for `kind` (0 forward, 1 reverse) and npad
+// landmarks, or the tuning override when one is set.  variants: a sweep
+// with RK4 stages or a terminal launch, whose kernels exist for the
+// built-in CTA sizes only (so the override does not apply).
+StepConfig choose_step_config(int kind, int npad, int num_sms, bool variants = false);
+// CTA sizes of the built-in configurations (one target per thread, one warp
+// group); the variant kernels are compiled for these.
+constexpr int kVarFwdThreads = 128;
+constexpr int kVarBwdThreads = 64;
 // Override the fused step configuration of `kind` (threads == 0 restores the
 // built-in choice).  Returns false for an unknown variant.
 bool set_step_override(int kind, int threads, int R, int groups, int cluster);

@@ -434,7 +434,9 @@ gs_status run_register(const gs_params* prm, const float* q0, const float* targe
   if ((s = get_workspace(&w)) != GS_OK) return s;
   const int n = static_cast<int>(prm->N), npad = round_up(n, kPad), n3 = 3 * n;
   const int ckpt = effective_ckpt(prm->ckpt_every, prm->T);
-  if ((s = reserve(*w, npad, std::max(prm->T, record_slots(prm->T, ckpt)), 1, ckpt ? (prm->T + ckpt - 1) / ckpt : 0)) !=
+  const int S = stages_of(prm->integrator);
+  if ((s = reserve(*w, npad, std::max(S * prm->T, record_slots(prm->T, ckpt, S)), 1,
+                   ckpt ? (prm->T + ckpt - 1) / ckpt : 0)) !=
       GS_OK)
     return s;
   if ((s = alloc_lbfgs(*w, n3, prm->lbfgs_m)) != GS_OK) return s;

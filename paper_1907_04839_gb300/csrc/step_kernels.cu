@@ -6,13 +6,17 @@
 // targets.  CTA rank r sums the pair terms of every target in the tile
 // against one contiguous split of the sources (pair_tile.cuh).  The C splits
 // together cover all N sources.  The split sums then meet in distributed
-// shared memory: each CTA writes its tile partials to its own shared memory,
-// and after a cluster barrier CTA r adds the C partials of targets
-// [r*M/C, (r+1)*M/C) in rank order, in double-single arithmetic.  It then
-// applies the FP64 update to those targets.  The reduction order is fixed,
-// so results are deterministic.  No split partials go through global
-// memory, and no second kernel is needed.  This plays the role of the
-// paper's shared-memory reduction (Section 2.5), spread over up to 16 SMs.
+// shared memory: CTA r reduces targets [r*M/C, (r+1)*M/C), adding the C
+// partials of each of its targets in rank order, in double-single
+// arithmetic, and applies the FP64 update to those targets.  The forward
+// kernel has every CTA store its partials straight into the reducing CTA's
+// shared memory (remote stores: nothing waits on a remote load; one cluster
+// barrier per step).  The reverse kernel has the reducing CTA load them from
+// its peers after a barrier (which measured faster for it).  The reduction
+// order is fixed, so results are deterministic.  No split partials go
+// through global memory, and no second kernel is needed.  This plays the
+// role of the paper's shared-memory reduction (Section 2.5), spread over up
+// to 16 SMs.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -90,9 +94,67 @@ __device__ __forceinline__ void combine_groups(float4 (&red)[W][M][3]) {
   }
 }
 
+// Send one target's six double-single partials (three float4) to the CTA
+// of the cluster that reduces that target.  CTA `owner` reduces targets
+// [owner*slice, (owner+1)*slice) of the tile; the partials of local target
+// lt from source split `rank` land in the owner's
+// recv[(rank*slice + lt - owner*slice)*3 + 0..2].  The stores are remote
+// (distributed shared memory) and need no reply; the cluster barrier that
+// follows makes them visible to the owner.
+__device__ __forceinline__ void push_partials(float4* recv, int lt, unsigned rank, int slice, float4 a, float4 b,
+                                              float4 c) {
+  const int owner = lt / slice;
+  const int lo = lt - owner * slice;
+  const uint32_t addr = dsmem_addr(smem_u32(&recv[(static_cast<int>(rank) * slice + lo) * 3]), owner);
+  st_dsmem_f4(addr, a);
+  st_dsmem_f4(addr + 16u, b);
+  st_dsmem_f4(addr + 32u, c);
+}
+
+// W > 1: the warp groups' partials of every target of the tile, added in
+// shared memory in group order into red[0].  Ends with a CTA barrier.
+template <int NT, int R, int W, int M, class Tile, class Res>
+__device__ __forceinline__ void combine_tile(float4 (&red)[W][M][3], const Tile& t, Res result, int lt0, int grp) {
+  if constexpr (W > 1) {
+    constexpr int TG = NT / W;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      ds w[6];
+      result(t, r, w);
+      const int lt = lt0 + r * TG;
+      red[grp][lt][0] = make_float4(w[0].hi, w[0].lo, w[1].hi, w[1].lo);
+      red[grp][lt][1] = make_float4(w[2].hi, w[2].lo, w[3].hi, w[3].lo);
+      red[grp][lt][2] = make_float4(w[4].hi, w[4].lo, w[5].hi, w[5].lo);
+    }
+    combine_groups<W, M>(red);
+    __syncthreads();
+  }
+}
+
+// Push the tile's partials to their reducing CTAs: W = 1 straight from each
+// thread's registers, W > 1 from red[0] (after combine_tile).  The caller
+// makes sure every receiving CTA is ready (a cluster barrier wait first).
+template <int NT, int R, int W, int M, class Tile, class Res>
+__device__ __forceinline__ void push_tile(const float4 (&red)[W][M][3], float4* recv, const Tile& t, Res result,
+                                          int lt0, unsigned rank, int slice) {
+  if constexpr (W == 1) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      ds w[6];
+      result(t, r, w);
+      push_partials(recv, lt0 + r * NT, rank, slice, make_float4(w[0].hi, w[0].lo, w[1].hi, w[1].lo),
+                    make_float4(w[2].hi, w[2].lo, w[3].hi, w[3].lo), make_float4(w[4].hi, w[4].lo, w[5].hi, w[5].lo));
+    }
+  } else {
+    for (int lt = threadIdx.x; lt < M; lt += NT) push_partials(recv, lt, rank, slice, red[0][lt][0], red[0][lt][1],
+                                                               red[0][lt][2]);
+  }
+}
+
 // Forward step of one tile: pair sums, cluster reduction, Euler update.
 // Accumulates this thread's H0 and mismatch contributions in hc, mc.
-template <int NT, int R, int W>
+// V: the variants (RK4 stages, the terminal launch) are compiled in.
+template <int NT, int R, int W, bool V>
 __device__ __forceinline__ void forward_body(const StepFwdArgs& a, const StepView& v, double& hc, double& mc) {
   constexpr int TG = NT / W;  // threads per warp group
   constexpr int M = TG * R;   // targets of the CTA
@@ -102,6 +164,9 @@ __device__ __forceinline__ void forward_body(const StepFwdArgs& a, const StepVie
     float4 red[W][M][3];  // per group: Hp (hi,lo) x3 then Hq (hi,lo) x3 per target
   };
   __shared__ __align__(128) Smem sm;
+  // Partials of this CTA's slice of targets from every source split:
+  // [C][M/C][3] float4, the same six double-single values per target.
+  __shared__ __align__(16) float4 recv[M * 3];
   __shared__ __align__(8) Pipe pp;
 
   const unsigned rank = cluster_rank(), C = cluster_size();
@@ -114,6 +179,7 @@ __device__ __forceinline__ void forward_body(const StepFwdArgs& a, const StepVie
     if (threadIdx.x == 0) atomicOr(a.status, kErrBadLaunch);
     return;
   }
+  cluster_arrive_relaxed();  // this CTA has started; the push waits for every peer's arrival
   const int lim = v.off + v.npad;
   const int j0 = min(v.off + static_cast<int>(rank) * v.split_len, lim);
   const int j1 = min(j0 + v.split_len, lim);
@@ -128,31 +194,27 @@ __device__ __forceinline__ void forward_body(const StepFwdArgs& a, const StepVie
   t.load(a.qp, tile0 + lt0, TG, lim);
   const float4* src[1] = {a.qp};
   stream_sources<1, W>(sm.st, pp, src, j0, j1, t, a.status, grp);  // ends with a CTA barrier
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    ds w[6];
-    t.result(r, v.kappa_f, w);
-    const int lt = lt0 + r * TG;
-    sm.red[grp][lt][0] = make_float4(w[0].hi, w[0].lo, w[1].hi, w[1].lo);
-    sm.red[grp][lt][1] = make_float4(w[2].hi, w[2].lo, w[3].hi, w[3].lo);
-    sm.red[grp][lt][2] = make_float4(w[4].hi, w[4].lo, w[5].hi, w[5].lo);
-  }
-  combine_groups<W, M>(sm.red);
-  cluster_sync();  // every CTA's tile partials are visible to the cluster
-
   const int slice = M / static_cast<int>(C);
+  const auto res = [&](const FwdTile<R>& tt, int r, ds* w) { tt.result(r, v.kappa_f, w); };
+  combine_tile<NT, R, W, M>(sm.red, t, res, lt0, grp);
+  // recv is memory of its own, so a CTA may push as soon as every peer has
+  // started (the arrival at kernel entry): one cluster barrier per step.
+  cluster_wait();
+  push_tile<NT, R, W, M>(sm.red, recv, t, res, lt0, rank, slice);
+  cluster_sync();  // every split's partials have reached the CTA that reduces them
+
   for (int item = threadIdx.x; item < slice * 3; item += NT) {
-    const int lt = static_cast<int>(rank) * slice + item / 3;
+    const int ll = item / 3;
+    const int lt = static_cast<int>(rank) * slice + ll;
     const int k = item % 3;
     if (v.tile * M + lt >= v.n) continue;
     const int i = tile0 + lt;  // packed landmark index
-    const uint32_t lp = smem_u32(&sm.red[0][lt][0]);
     ds hp{0.f, 0.f}, hq{0.f, 0.f};
 #pragma unroll 4
     for (unsigned rr = 0; rr < C; ++rr) {
-      const uint32_t rp = dsmem_addr(lp, rr);
-      const float2 x = ld_dsmem_f2(rp + 8u * k);
-      const float2 y = ld_dsmem_f2(rp + 24u + 8u * k);
+      const float2* rp = reinterpret_cast<const float2*>(&recv[(static_cast<int>(rr) * slice + ll) * 3]);
+      const float2 x = rp[k];
+      const float2 y = rp[3 + k];
       hp = ds_add(hp, ds{x.x, x.y});
       hq = ds_add(hq, ds{y.x, y.y});
     }
@@ -162,40 +224,78 @@ __device__ __forceinline__ void forward_body(const StepFwdArgs& a, const StepVie
     }
     const int tt = 3 * i + k;
     const double Hp = ds_to_double(hp), Hq = ds_to_double(hq);
-    const double p_old = a.p64[tt];
-    const double q = a.q64[tt] + v.dt * Hp;
-    const double p = p_old - v.dt * Hq;
-    if (!isfinite(q) || !isfinite(p)) atomicOr(a.status, kErrNonFinite);
-    if (a.first) hc += 0.5 * p_old * Hp;  // H0 = 1/2 sum_i p0_i . Hp_i(q0, p0)
-    double r = 0.0;
-    if (a.last && a.with_loss) {
-      r = q - a.t64[tt];
+    const double q_old = a.q64[tt], p_old = a.p64[tt];
+    float* an = reinterpret_cast<float*>(a.ab + (i >> 1) * kRecF4) + 2 * k + (i & 1);
+    if (V && a.terminal) {
+      // The end state (q(1), p(1)): its kinetic term, the mismatch, and the
+      // adjoint alpha = dL/dq(1) = 2 lambda r + Hq, beta = dL/dp(1) = Hp.
+      hc += 0.5 * p_old * Hp;
+      const double r = q_old - a.t64[tt];
       mc += r * r;
+      const double al = 2.0 * v.lambda * r + Hq, be = Hp;
+      if (!isfinite(al) || !isfinite(be)) atomicOr(a.status, kErrNonFinite);
+      a.a64[tt] = al;
+      a.b64[tt] = be;
+      an[0] = (float)(a.adj_scale * al);
+      an[6] = -(float)(v.kappa * a.adj_scale * be);
+      continue;
     }
     if (a.first) {
+      hc += 0.5 * p_old * Hp;  // H0 = 1/2 sum_i p0_i . Hp_i(q0, p0)
       a.hp0[tt] = Hp;
       a.hq0[tt] = Hq;
     }
-    a.q64[tt] = q;
-    a.p64[tt] = p;
+    double q, p;  // the state of the record this launch writes
+    if (V && a.rk) {
+      // Stage s of an RK4 step from y = (q_old, p_old) with f = (Hp, -Hq):
+      // accumulate k1 + 2 k2 + 2 k3, write the next stage state
+      // y + dt/2 f, y + dt/2 f, y + dt f, or at the last stage the new state
+      // y + dt/6 (k1 + 2 k2 + 2 k3 + k4).
+      const double fq = Hp, fp = -Hq;
+      if (a.stage == 0) {
+        a.qa64[tt] = fq;
+        a.pa64[tt] = fp;
+      } else if (a.stage < 3) {
+        a.qa64[tt] += 2.0 * fq;
+        a.pa64[tt] += 2.0 * fp;
+      }
+      if (a.stage < 3) {
+        const double c = (a.stage == 2 ? 1.0 : 0.5) * v.dt;
+        q = q_old + c * fq;
+        p = p_old + c * fp;
+      } else {
+        q = q_old + v.dt / 6.0 * (a.qa64[tt] + fq);
+        p = p_old + v.dt / 6.0 * (a.pa64[tt] + fp);
+        a.q64[tt] = q;
+        a.p64[tt] = p;
+      }
+    } else {
+      q = q_old + v.dt * Hp;
+      p = p_old - v.dt * Hq;
+      a.q64[tt] = q;
+      a.p64[tt] = p;
+    }
+    if (!isfinite(q) || !isfinite(p)) atomicOr(a.status, kErrNonFinite);
     float* qn = reinterpret_cast<float*>(a.qp_next + (i >> 1) * kRecF4) + 2 * k + (i & 1);
     qn[0] = -(float)(v.kq * q);
     qn[6] = (float)p;
     if (a.last && a.with_loss) {
+      const double r = q - a.t64[tt];
+      mc += r * r;
       const double al = 2.0 * v.lambda * r;
       a.a64[tt] = al;
       a.b64[tt] = 0.0;
-      float* an = reinterpret_cast<float*>(a.ab + (i >> 1) * kRecF4) + 2 * k + (i & 1);
-      an[0] = (float)al;
+      an[0] = (float)((V && a.rk ? a.adj_scale : 1.0) * al);
       an[6] = 0.f;
     }
   }
-  cluster_sync();  // peers may still be reading this CTA's partials
+  // No trailing cluster barrier: every remote access of the step happened
+  // before the one above.
 }
 
 // Reverse step of one tile: adjoint pair sums, cluster reduction, adjoint
-// update, and at time step 0 the gradient.
-template <int NT, int R, int W>
+// update, and at time step 0 the gradient.  V: the RK4 stages are compiled in.
+template <int NT, int R, int W, bool V>
 __device__ __forceinline__ void backward_body(const StepBwdArgs& a, const StepView& v) {
   constexpr int TG = NT / W;  // threads per warp group
   constexpr int M = TG * R;   // targets of the CTA
@@ -231,6 +331,10 @@ __device__ __forceinline__ void backward_body(const StepBwdArgs& a, const StepVi
   t.load(a.qp, a.ab, tile0 + lt0, TG, lim);
   const float4* src[2] = {a.qp, a.ab};
   stream_sources<2, W>(sm.st, pp, src, j0, j1, t, a.status, grp);
+  // The reverse kernel pulls: each CTA leaves its partials in its own idle
+  // stage ring and the reducing CTA loads them through distributed shared
+  // memory.  (Pushing them, as the forward kernel does, measured 3-5 %
+  // slower for this kernel on GB300 at 4096 to 65536 landmarks.)
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     ds w[6];
@@ -241,11 +345,12 @@ __device__ __forceinline__ void backward_body(const StepBwdArgs& a, const StepVi
     sm.red[grp][lt][2] = make_float4(w[4].hi, w[4].lo, w[5].hi, w[5].lo);
   }
   combine_groups<W, M>(sm.red);
-  cluster_sync();
-
+  cluster_sync();  // every CTA's tile partials are visible to the cluster
   const int slice = M / static_cast<int>(C);
+
   for (int item = threadIdx.x; item < slice * 3; item += NT) {
-    const int lt = static_cast<int>(rank) * slice + item / 3;
+    const int ll = item / 3;
+    const int lt = static_cast<int>(rank) * slice + ll;
     const int k = item % 3;
     if (v.tile * M + lt >= v.n) continue;
     const int i = tile0 + lt;
@@ -264,26 +369,59 @@ __device__ __forceinline__ void backward_body(const StepBwdArgs& a, const StepVi
       continue;
     }
     const int tt = 3 * i + k;
-    const double al = a.a64[tt] + v.dt * ds_to_double(da);
-    const double be = a.b64[tt] + v.dt * ds_to_double(db);
-    if (!isfinite(al) || !isfinite(be)) atomicOr(a.status, kErrNonFinite);
-    a.a64[tt] = al;
-    a.b64[tt] = be;
     float* an = reinterpret_cast<float*>(a.ab_next + (i >> 1) * kRecF4) + 2 * k + (i & 1);
-    an[0] = (float)al;
-    an[6] = -(float)(v.kappa * be);
+    double al, be;  // the adjoint of the step's start state, once complete
+    if (V && a.rk) {
+      // Reverse of RK4 stage s: v = J(Y_s)^T kbar_s came out of the pair sums.
+      // The adjoint of the start state sums w (the adjoint of the end state)
+      // and the four v; the next stage adjoint is
+      //   kbar_{s-1} = dt b_{s-1} w + c_s dt v,  b = (1/6, 1/3, 1/3),
+      //   c = (1/2, 1/2, 1) for s = 1, 2, 3.
+      const double va = ds_to_double(da), vb = ds_to_double(db);
+      const double wa = a.a64[tt], wb = a.b64[tt];
+      const double ya = (a.stage == 3 ? wa : a.ya64[tt]) + va;
+      const double yb = (a.stage == 3 ? wb : a.yb64[tt]) + vb;
+      if (!isfinite(ya) || !isfinite(yb)) atomicOr(a.status, kErrNonFinite);
+      if (a.stage > 0) {
+        a.ya64[tt] = ya;
+        a.yb64[tt] = yb;
+        const double cw = (a.stage == 1 ? 1.0 / 6.0 : 1.0 / 3.0) * v.dt;
+        const double cv = (a.stage == 3 ? 1.0 : 0.5) * v.dt;
+        an[0] = (float)(cw * wa + cv * va);
+        an[6] = -(float)(v.kappa * (cw * wb + cv * vb));
+        continue;
+      }
+      al = ya;
+      be = yb;
+      a.a64[tt] = al;
+      a.b64[tt] = be;
+      an[0] = (float)(v.dt / 6.0 * al);  // stage 4 adjoint of the previous step
+      an[6] = -(float)(v.kappa * (v.dt / 6.0 * be));
+    } else {
+      al = a.a64[tt] + v.dt * ds_to_double(da);
+      be = a.b64[tt] + v.dt * ds_to_double(db);
+      if (!isfinite(al) || !isfinite(be)) atomicOr(a.status, kErrNonFinite);
+      a.a64[tt] = al;
+      a.b64[tt] = be;
+      an[0] = (float)al;
+      an[6] = -(float)(v.kappa * be);
+    }
     if (a.first) {
-      const double gp = be + a.hp0[tt];
+      const double gp = be + (a.h_at_end ? 0.0 : a.hp0[tt]);
       if (a.grad_p0) a.grad_p0[tt] = (float)gp;
       if (a.grad_p0_64) a.grad_p0_64[tt] = gp;
-      if (a.grad_q0) a.grad_q0[tt] = (float)(al + a.hq0[tt]);
+      if (a.grad_q0) a.grad_q0[tt] = (float)(al + (a.h_at_end ? 0.0 : a.hq0[tt]));
     }
   }
-  cluster_sync();
+  cluster_sync();  // peers may still be reading this CTA's partials
 }
 
 // ---------------------------------------------------------------- single-problem kernels
-template <int NT, int R, int W>
+// V selects the instantiation: false for the plain method (Euler steps, the
+// kinetic term at t = 0), true with the variants compiled in (RK4 stages, the
+// terminal launch).  Keeping them apart leaves the plain kernels' register
+// allocation as the pair loop needs it.
+template <int NT, int R, int W, bool V>
 __global__ void __launch_bounds__(NT) k_step_forward(StepFwdArgs a) {
   __shared__ double shred[NT / 32];
   __shared__ int am_last;
@@ -300,19 +438,24 @@ __global__ void __launch_bounds__(NT) k_step_forward(StepFwdArgs a) {
   v.dt = a.dt;
   v.lambda = a.lambda;
   double hc = 0.0, mc = 0.0;
-  forward_body<NT, R, W>(a, v, hc, mc);
-  const bool reduce_h = a.first != 0;
+  forward_body<NT, R, W, V>(a, v, hc, mc);
+  const bool reduce_h = a.first || a.terminal;
   const bool reduce_m = a.last && a.with_loss;
   if ((!reduce_h && !reduce_m) || a.dry) return;  // uniform across the grid
   double h, m;
   if (grid_sum2(hc, mc, a.red_h, a.red_m, a.ticket, shred, &am_last, &h, &m) && threadIdx.x == 0) {
-    if (reduce_h) a.scalars[0] = h;
-    if (reduce_m) a.scalars[1] = (reduce_h ? h : a.scalars[0]) + a.lambda * m;
+    if (a.terminal) {
+      a.scalars[2] = h;  // H(p(1), q(1))
+      a.scalars[1] = h + a.lambda * m;
+    } else {
+      if (reduce_h) a.scalars[0] = h;
+      if (reduce_m) a.scalars[1] = (reduce_h ? h : a.scalars[0]) + a.lambda * m;
+    }
     *a.ticket = 0u;
   }
 }
 
-template <int NT, int R, int W>
+template <int NT, int R, int W, bool V>
 __global__ void __launch_bounds__(NT) k_step_backward(StepBwdArgs a) {
   StepView v;
   v.off = 0;
@@ -326,7 +469,7 @@ __global__ void __launch_bounds__(NT) k_step_backward(StepBwdArgs a) {
   v.kappa = a.kappa64;
   v.dt = a.dt;
   v.lambda = 0.0;
-  backward_body<NT, R, W>(a, v);
+  backward_body<NT, R, W, V>(a, v);
 }
 
 // ---------------------------------------------------------------- packed batch kernels
@@ -356,7 +499,7 @@ __global__ void __launch_bounds__(NT) k_bstep_forward(StepFwdArgs a, BatchTables
   __shared__ double shred[NT / 32];
   const StepView v = batch_view(bt);
   double hc = 0.0, mc = 0.0;
-  forward_body<NT, R, W>(a, v, hc, mc);
+  forward_body<NT, R, W, false>(a, v, hc, mc);
   const bool reduce_h = a.first != 0;
   const bool reduce_m = a.last && a.with_loss;
   if ((!reduce_h && !reduce_m) || a.dry) return;
@@ -371,7 +514,7 @@ __global__ void __launch_bounds__(NT) k_bstep_forward(StepFwdArgs a, BatchTables
 
 template <int NT, int R, int W>
 __global__ void __launch_bounds__(NT) k_bstep_backward(StepBwdArgs a, BatchTables bt) {
-  backward_body<NT, R, W>(a, batch_view(bt));
+  backward_body<NT, R, W, false>(a, batch_view(bt));
 }
 
 // ---------------------------------------------------------------- host side
@@ -495,13 +638,13 @@ int policy_for_grid(long long ctas, int num_sms) { return 2 * ctas >= 3LL * 8 * 
 cudaError_t max_active_clusters(int kind, int threads, int R, int groups, int cluster, int* out) {
   *out = 0;
 #define X(T_, R_, W_) \
-  if (threads == T_ && R == R_ && groups == W_) return occupancy_clusters(k_step_forward<T_, R_, W_>, T_, cluster, out);
+  if (threads == T_ && R == R_ && groups == W_) return occupancy_clusters(k_step_forward<T_, R_, W_, false>, T_, cluster, out);
   if (kind == 0) {
     GS_STEP_FWD_CASES(X)
   }
 #undef X
 #define X(T_, R_, W_) \
-  if (threads == T_ && R == R_ && groups == W_) return occupancy_clusters(k_step_backward<T_, R_, W_>, T_, cluster, out);
+  if (threads == T_ && R == R_ && groups == W_) return occupancy_clusters(k_step_backward<T_, R_, W_, false>, T_, cluster, out);
   if (kind == 1) {
     GS_STEP_BWD_CASES(X)
   }
@@ -523,8 +666,8 @@ bool set_step_override(int kind, int threads, int R, int groups, int cluster) {
 }
 
 // Default configuration per problem size, from sweeps on GB300 (152 SMs).
-StepConfig choose_step_config(int kind, int npad, int num_sms) {
-  if (g_override[kind][0]) {
+StepConfig choose_step_config(int kind, int npad, int num_sms, bool variants) {
+  if (g_override[kind][0] && !variants) {
     StepConfig c = step_config_for(kind, npad, g_override[kind][0], g_override[kind][1],
                                    std::min(g_override[kind][2], std::max(1, npad / kUnroll)), g_override[kind][3]);
     c.policy = policy_for_grid(static_cast<long long>(c.tiles) * c.cluster, num_sms);
@@ -536,7 +679,7 @@ StepConfig choose_step_config(int kind, int npad, int num_sms) {
   // target per thread.  A grid of 1.5 waves or more (8 CTAs per SM) is
   // scheduled with load balancing, which keeps every SM busy; a smaller grid
   // is spread over the SMs.
-  const int threads = kind == 0 ? 128 : 64;
+  const int threads = kind == 0 ? kVarFwdThreads : kVarBwdThreads;
   const int cl = std::min(kind == 0 ? 16 : 8, std::max(1, npad / kUnroll));
   int c = 1;
   while (c * 2 <= cl) c *= 2;
@@ -580,17 +723,31 @@ cudaError_t launch_bstep_backward(const StepConfig& c, int items, const StepBwdA
   return cudaErrorInvalidValue;
 }
 
+// Launches of the variants (RK4 stages, the terminal launch) go to the
+// V = true instantiation of the built-in configuration's kernel variant.
 cudaError_t launch_step_forward(const StepConfig& c, const StepFwdArgs& a, cudaStream_t st, bool pdl) {
+  if (a.rk || a.terminal) {
+    if (c.threads == kVarFwdThreads && c.R == 1 && c.groups == 1)
+      return launch_cluster(k_step_forward<kVarFwdThreads, 1, 1, true>, c, a, st, pdl);
+    return cudaErrorNotSupported;
+  }
 #define X(T_, R_, W_) \
-  if (c.threads == T_ && c.R == R_ && c.groups == W_) return launch_cluster(k_step_forward<T_, R_, W_>, c, a, st, pdl);
+  if (c.threads == T_ && c.R == R_ && c.groups == W_) \
+    return launch_cluster(k_step_forward<T_, R_, W_, false>, c, a, st, pdl);
   GS_STEP_FWD_CASES(X)
 #undef X
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_step_backward(const StepConfig& c, const StepBwdArgs& a, cudaStream_t st, bool pdl) {
+  if (a.rk) {
+    if (c.threads == kVarBwdThreads && c.R == 1 && c.groups == 1)
+      return launch_cluster(k_step_backward<kVarBwdThreads, 1, 1, true>, c, a, st, pdl);
+    return cudaErrorNotSupported;
+  }
 #define X(T_, R_, W_) \
-  if (c.threads == T_ && c.R == R_ && c.groups == W_) return launch_cluster(k_step_backward<T_, R_, W_>, c, a, st, pdl);
+  if (c.threads == T_ && c.R == R_ && c.groups == W_) \
+    return launch_cluster(k_step_backward<T_, R_, W_, false>, c, a, st, pdl);
   GS_STEP_BWD_CASES(X)
 #undef X
   return cudaErrorInvalidValue;

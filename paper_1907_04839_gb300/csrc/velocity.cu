@@ -287,6 +287,7 @@ extern "C" gs_status flow_points(const gs_params* prm, const float* q0, const fl
   gs_status s = check_params(prm);
   if (s != GS_OK) return s;
   if (!q0 || !p0) return fail(GS_EINVAL, "q0 and p0 must not be NULL");
+  if (prm->integrator != GS_EULER) return fail(GS_EINVAL, "flow_points takes Euler steps only (integrator GS_EULER)");
   if ((s = check_points(M, x0, x1)) != GS_OK) return s;
   std::lock_guard<std::mutex> lk(engine_mutex());
   Workspace* w = nullptr;

@@ -4,6 +4,7 @@ exports every entry point include/gshoot.h declares.  No compute call is made
 import ctypes
 import os
 import re
+import subprocess
 
 import pytest
 
@@ -32,12 +33,21 @@ def test_library_exports_every_declared_symbol():
     assert lib.gs_version() >= 100
 
 
-def test_params_struct_layout_matches_header():
+def test_params_struct_layout_matches_header(tmp_path):
+    # The ctypes mirror against the C compiler's own layout of the header.
     import paper_1907_04839_gb300 as gsh
-    # int64 N, int32 T, int32 ckpt, double sigma, double lambda, int32 m,
-    # int32 max_iter, double grad_tol  ->  48 bytes with natural alignment
-    assert ctypes.sizeof(gsh.GsParams) == 48
-    assert gsh.GsParams.sigma.offset == 16 and gsh.GsParams.grad_tol.offset == 40
+    fields = [f[0] for f in gsh.GsParams._fields_]
+    cnames = {"lambda_": "lambda"}
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"gshoot.h\"\nint main(void) {\n"
+                   + '  printf("%zu\\n", sizeof(gs_params));\n'
+                   + "".join('  printf("%%zu\\n", offsetof(gs_params, %s));\n' % cnames.get(f, f) for f in fields)
+                   + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(gsh.GsParams)
+    assert out[1:] == [getattr(gsh.GsParams, f).offset for f in fields]
 
 
 def test_library_is_built_for_sm103a():
@@ -56,3 +66,17 @@ def test_no_cuda_device_is_reported_as_error_not_crash():
     q = np.zeros((4, 3), np.float32)
     with pytest.raises(gsh.GShootError):
         gsh.step_forward(q, q, 0.1)
+
+
+def test_invalid_variant_is_rejected_before_device_work():
+    import numpy as np
+    import paper_1907_04839_gb300 as gsh
+    lib = gsh.load()
+    q = np.zeros((4, 3), np.float32)
+    for integ, kin in ((2, 0), (0, 2), (-1, 0)):
+        prm = gsh.GsParams(N=4, T=2, ckpt_every=0, sigma=0.1, lambda_=1.0, lbfgs_m=10, max_iter=1, grad_tol=0.0,
+                           integrator=integ, kinetic_at=kin)
+        P = lambda a: ctypes.c_void_p(a.ctypes.data)
+        st = lib.shoot_gradient(ctypes.byref(prm), P(q), P(q), P(q), None, P(q), P(q), None)
+        assert st == -1, (integ, kin, st)
+        assert b"integrator" in lib.gs_last_error() or b"kinetic_at" in lib.gs_last_error()

@@ -65,13 +65,17 @@ def _load():
             lib.orc_lbfgs_rosenbrock.restype = cint
             lib.orc_register.argtypes = [i64, cint, cd, cd, cint, cint, cd, _D, _D, _D, _D, IP, IP, _D]
             lib.orc_register.restype = cint
-            lib.orc_shoot_forward_v.argtypes = [i64, cint, cd, cint, _D, _D, _D, _D]
-            lib.orc_loss_v.argtypes = [i64, cint, cd, cd, cint, cint, _D, _D, _D]
+            lib.orc_shoot_forward_v.argtypes = [cint, i64, cint, cd, cint, _D, _D, _D, _D]
+            lib.orc_step_forward_d.argtypes = [cint, i64, cd, _D, _D, _D, _D]
+            lib.orc_step_backward_d.argtypes = [cint, i64, cd, _D, _D, _D, _D, _D, _D]
+            lib.orc_hamiltonian_d.argtypes = [cint, i64, cd, _D, _D]
+            lib.orc_hamiltonian_d.restype = cd
+            lib.orc_loss_v.argtypes = [cint, i64, cint, cd, cd, cint, cint, _D, _D, _D]
             lib.orc_loss_v.restype = cd
-            lib.orc_shoot_gradient_v.argtypes = [i64, cint, cd, cd, cint, cint, _D, _D, _D, _D, _D, _D, _D, _D]
+            lib.orc_shoot_gradient_v.argtypes = [cint, i64, cint, cd, cd, cint, cint, _D, _D, _D, _D, _D, _D, _D, _D]
             lib.orc_shoot_gradient_v.restype = cd
-            lib.orc_register_v.argtypes = [i64, cint, cd, cd, cint, cint, cint, cint, cd, _D, _D, _D, _D, IP, IP,
-                                           _D]
+            lib.orc_register_v.argtypes = [cint, i64, cint, cd, cd, cint, cint, cint, cint, cd, _D, _D, _D, _D, IP,
+                                           IP, _D]
             lib.orc_register_v.restype = cint
             lib.orc_step_forward_rows.argtypes = [i64, cd, _D, _D, i64, _I, _D, _D]
             lib.orc_step_backward_rows.argtypes = [i64, cd, _D, _D, _D, _D, i64, _I, _D, _D]
@@ -247,46 +251,78 @@ def _variant(integrator, h_at):
     return INTEGRATORS[integrator], KINETIC[h_at]
 
 
+def _in_d(a, n=None, dim=None):
+    """(N, dim) float64 array with dim 2 or 3 (the dimension of the landmarks)."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.ndim != 2 or a.shape[1] not in (2, 3) or (n is not None and a.shape[0] != n) or (
+            dim is not None and a.shape[1] != dim):
+        raise ValueError("expected an (N, 2) or (N, 3) array, got shape %r" % (a.shape,))
+    return a
+
+
+def step_forward_d(q, p, sigma):
+    """StepForward in 2-D or 3-D (the dimension of q): (Hq, Hp)."""
+    q = _in_d(q); n, d = q.shape; p = _in_d(p, n, d)
+    Hq = np.empty_like(q); Hp = np.empty_like(q)
+    _load().orc_step_forward_d(d, n, float(sigma), _p(q), _p(p), _p(Hq), _p(Hp))
+    return Hq, Hp
+
+
+def step_backward_d(q, p, alpha, beta, sigma):
+    """StepBackward in 2-D or 3-D: (dalpha, dbeta)."""
+    q = _in_d(q); n, d = q.shape
+    p, alpha, beta = _in_d(p, n, d), _in_d(alpha, n, d), _in_d(beta, n, d)
+    da = np.empty_like(q); db = np.empty_like(q)
+    _load().orc_step_backward_d(d, n, float(sigma), _p(q), _p(p), _p(alpha), _p(beta), _p(da), _p(db))
+    return da, db
+
+
+def hamiltonian_d(q, p, sigma) -> float:
+    q = _in_d(q); n, d = q.shape; p = _in_d(p, n, d)
+    return float(_load().orc_hamiltonian_d(d, n, float(sigma), _p(q), _p(p)))
+
+
 def shoot_forward_v(q0, p0, T, sigma, integrator="euler"):
-    """Forward flow with the chosen integrator ("euler" or "rk4"): (q1, p1)."""
+    """Forward flow with the chosen integrator ("euler" or "rk4"): (q1, p1).
+    Landmarks in 2-D or 3-D (the shape of q0)."""
     ig, _ = _variant(integrator, "start")
-    q0 = _in(q0); n = q0.shape[0]; p0 = _in(p0, n)
+    q0 = _in_d(q0); n, d = q0.shape; p0 = _in_d(p0, n, d)
     q1 = np.empty_like(q0); p1 = np.empty_like(q0)
-    _load().orc_shoot_forward_v(n, int(T), float(sigma), ig, _p(q0), _p(p0), _p(q1), _p(p1))
+    _load().orc_shoot_forward_v(d, n, int(T), float(sigma), ig, _p(q0), _p(p0), _p(q1), _p(p1))
     return q1, p1
 
 
 def loss_v(q0, p0, target, T, sigma, lam, integrator="euler", h_at="start") -> float:
     """Loss of a variant: kinetic term at t = 0 ("start") or t = 1 ("end")."""
     ig, he = _variant(integrator, h_at)
-    q0 = _in(q0); n = q0.shape[0]
-    p0, target = _in(p0, n), _in(target, n)
-    return float(_load().orc_loss_v(n, int(T), float(sigma), float(lam), ig, he, _p(q0), _p(p0), _p(target)))
+    q0 = _in_d(q0); n, d = q0.shape
+    p0, target = _in_d(p0, n, d), _in_d(target, n, d)
+    return float(_load().orc_loss_v(d, n, int(T), float(sigma), float(lam), ig, he, _p(q0), _p(p0), _p(target)))
 
 
 def shoot_gradient_v(q0, p0, target, T, sigma, lam, integrator="euler", h_at="start"):
     """ComputeGradient of a variant: dict(loss, grad_p0, grad_q0, q1, p1, H)
-    with H the kinetic term of the loss."""
+    with H the kinetic term of the loss.  2-D or 3-D landmarks."""
     ig, he = _variant(integrator, h_at)
-    q0 = _in(q0); n = q0.shape[0]
-    p0, target = _in(p0, n), _in(target, n)
+    q0 = _in_d(q0); n, d = q0.shape
+    p0, target = _in_d(p0, n, d), _in_d(target, n, d)
     gp = np.empty_like(q0); gq = np.empty_like(q0)
     q1 = np.empty_like(q0); p1 = np.empty_like(q0)
     h = ctypes.c_double(0.0)
-    L = _load().orc_shoot_gradient_v(n, int(T), float(sigma), float(lam), ig, he, _p(q0), _p(p0), _p(target),
+    L = _load().orc_shoot_gradient_v(d, n, int(T), float(sigma), float(lam), ig, he, _p(q0), _p(p0), _p(target),
                                      _p(gp), _p(gq), _p(q1), _p(p1), ctypes.byref(h))
     return dict(loss=float(L), grad_p0=gp, grad_q0=gq, q1=q1, p1=p1, H=float(h.value))
 
 
 def register_v(q0, target, T, sigma, lam, integrator="euler", h_at="start", p0=None, m=10, max_iter=50,
                grad_tol=1e-5):
-    """register with a variant of the discretisation."""
+    """register with a variant of the discretisation (2-D or 3-D landmarks)."""
     ig, he = _variant(integrator, h_at)
-    q0 = _in(q0); n = q0.shape[0]; target = _in(target, n)
-    x = np.zeros((n, 3)) if p0 is None else _in(p0, n).copy()
+    q0 = _in_d(q0); n, d = q0.shape; target = _in_d(target, n, d)
+    x = np.zeros((n, d)) if p0 is None else _in_d(p0, n, d).copy()
     trace = np.zeros(max_iter + 1)
     f = ctypes.c_double(0); it = ctypes.c_int(0); ev = ctypes.c_int(0)
-    st = _load().orc_register_v(n, int(T), float(sigma), float(lam), ig, he, int(m), int(max_iter),
+    st = _load().orc_register_v(d, n, int(T), float(sigma), float(lam), ig, he, int(m), int(max_iter),
                                 float(grad_tol), _p(q0), _p(target), _p(x), ctypes.byref(f), ctypes.byref(it),
                                 ctypes.byref(ev), _p(trace))
     return _lbfgs_out(st, f, it, ev, x, trace)

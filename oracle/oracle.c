@@ -71,63 +71,75 @@ int orc_max_threads(void) {
 /* Gaussian kernel G_sigma of Section 2.1 on a squared distance. */
 static double gauss(double r2, double sigma) { return exp(-r2 / (2.0 * sigma * sigma)); }
 
-/* StepForward (Algorithm 2): Hq and Hp of Eq. 2 at state (q, p). */
-void orc_step_forward(int64_t n, double sigma, const double* q, const double* p,
-                      double* Hq, double* Hp) {
+/* StepForward (Algorithm 2): Hq and Hp of Eq. 2 at state (q, p), for
+ * landmarks in `dim` = 2 or 3 dimensions ((N, dim) arrays). */
+void orc_step_forward_d(int dim, int64_t n, double sigma, const double* q, const double* p,
+                        double* Hq, double* Hp) {
     const double s = 1.0 / (sigma * sigma);
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         double hq[3] = {0, 0, 0}, hp[3] = {0, 0, 0};
         for (int64_t j = 0; j < n; ++j) {
             double d[3], r2 = 0.0, c = 0.0;
-            for (int k = 0; k < 3; ++k) {
-                d[k] = q[3 * i + k] - q[3 * j + k];
+            for (int k = 0; k < dim; ++k) {
+                d[k] = q[dim * i + k] - q[dim * j + k];
                 r2 += d[k] * d[k];
-                c += p[3 * i + k] * p[3 * j + k];
+                c += p[dim * i + k] * p[dim * j + k];
             }
             const double g = gauss(r2, sigma);
-            for (int k = 0; k < 3; ++k) {
-                hp[k] += g * p[3 * j + k];
+            for (int k = 0; k < dim; ++k) {
+                hp[k] += g * p[dim * j + k];
                 hq[k] += -s * c * g * d[k];
             }
         }
-        for (int k = 0; k < 3; ++k) {
-            Hq[3 * i + k] = hq[k];
-            Hp[3 * i + k] = hp[k];
+        for (int k = 0; k < dim; ++k) {
+            Hq[dim * i + k] = hq[k];
+            Hp[dim * i + k] = hp[k];
         }
     }
 }
 
+void orc_step_forward(int64_t n, double sigma, const double* q, const double* p,
+                      double* Hq, double* Hp) {
+    orc_step_forward_d(3, n, sigma, q, p, Hq, Hp);
+}
+
 /* StepBackward: the transposed Jacobian of (Hp, -Hq) at (q, p) applied to the
  * adjoint (alpha, beta) of the state after the step.  See the header. */
-void orc_step_backward(int64_t n, double sigma, const double* q, const double* p,
-                       const double* alpha, const double* beta,
-                       double* dalpha, double* dbeta) {
+void orc_step_backward_d(int dim, int64_t n, double sigma, const double* q, const double* p,
+                         const double* alpha, const double* beta,
+                         double* dalpha, double* dbeta) {
     const double s = 1.0 / (sigma * sigma);
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         double da[3] = {0, 0, 0}, db[3] = {0, 0, 0};
         for (int64_t j = 0; j < n; ++j) {
             double d[3], e[3], r2 = 0.0, c = 0.0, ed = 0.0, u = 0.0;
-            for (int k = 0; k < 3; ++k) {
-                d[k] = q[3 * i + k] - q[3 * j + k];
-                e[k] = beta[3 * i + k] - beta[3 * j + k];
+            for (int k = 0; k < dim; ++k) {
+                d[k] = q[dim * i + k] - q[dim * j + k];
+                e[k] = beta[dim * i + k] - beta[dim * j + k];
                 r2 += d[k] * d[k];
-                c += p[3 * i + k] * p[3 * j + k];
+                c += p[dim * i + k] * p[dim * j + k];
                 ed += e[k] * d[k];
-                u += alpha[3 * i + k] * p[3 * j + k] + alpha[3 * j + k] * p[3 * i + k];
+                u += alpha[dim * i + k] * p[dim * j + k] + alpha[dim * j + k] * p[dim * i + k];
             }
             const double g = gauss(r2, sigma);
-            for (int k = 0; k < 3; ++k) {
+            for (int k = 0; k < dim; ++k) {
                 da[k] += s * g * (c * e[k] - (u + s * c * ed) * d[k]);
-                db[k] += g * (alpha[3 * j + k] + s * ed * p[3 * j + k]);
+                db[k] += g * (alpha[dim * j + k] + s * ed * p[dim * j + k]);
             }
         }
-        for (int k = 0; k < 3; ++k) {
-            dalpha[3 * i + k] = da[k];
-            dbeta[3 * i + k] = db[k];
+        for (int k = 0; k < dim; ++k) {
+            dalpha[dim * i + k] = da[k];
+            dbeta[dim * i + k] = db[k];
         }
     }
+}
+
+void orc_step_backward(int64_t n, double sigma, const double* q, const double* p,
+                       const double* alpha, const double* beta,
+                       double* dalpha, double* dbeta) {
+    orc_step_backward_d(3, n, sigma, q, p, alpha, beta, dalpha, dbeta);
 }
 
 /* StepForward restricted to the m target rows rows[0..m): (Hq, Hp) of those
@@ -191,24 +203,28 @@ void orc_step_backward_rows(int64_t n, double sigma, const double* q, const doub
     }
 }
 
-/* Eq. 1: H(p, q) = 1/2 sum_i sum_j g_ij p_i . p_j. */
-double orc_hamiltonian(int64_t n, double sigma, const double* q, const double* p) {
+/* Eq. 1: H(p, q) = 1/2 sum_i sum_j g_ij p_i . p_j (landmarks in dim dimensions). */
+double orc_hamiltonian_d(int dim, int64_t n, double sigma, const double* q, const double* p) {
     double h = 0.0;
 #pragma omp parallel for schedule(static) reduction(+ : h)
     for (int64_t i = 0; i < n; ++i) {
         double hi = 0.0;
         for (int64_t j = 0; j < n; ++j) {
             double r2 = 0.0, c = 0.0;
-            for (int k = 0; k < 3; ++k) {
-                const double d = q[3 * i + k] - q[3 * j + k];
+            for (int k = 0; k < dim; ++k) {
+                const double d = q[dim * i + k] - q[dim * j + k];
                 r2 += d * d;
-                c += p[3 * i + k] * p[3 * j + k];
+                c += p[dim * i + k] * p[dim * j + k];
             }
             hi += gauss(r2, sigma) * c;
         }
         h += hi;
     }
     return 0.5 * h;
+}
+
+double orc_hamiltonian(int64_t n, double sigma, const double* q, const double* p) {
+    return orc_hamiltonian_d(3, n, sigma, q, p);
 }
 
 /* Forward flow of Algorithm 1 (its forward loop, started at q0): T explicit Euler
@@ -320,6 +336,9 @@ double orc_shoot_gradient(int64_t n, int T, double sigma, double lambda,
  *   v1 = J(y)^T  (dt/6 w + dt/2 v2),
  *   adjoint of y = w + v1 + v2 + v3 + v4.
  *
+ * Dimension (dim = 3, or dim = 2 for planar landmarks: the paper codes the
+ * two cases separately; every formula above holds with 2-vectors).
+ *
  * Kinetic term (h_at_end = 0: H(p0, q0) as above; h_at_end = 1: H(p(1), q(1)),
  * the form Algorithm 1's pseudocode writes, evaluating the kinetic term at
  * the end state).  With it at the end, the adjoint starts from
@@ -329,13 +348,13 @@ double orc_shoot_gradient(int64_t n, int T, double sigma, double lambda,
 /* One step of the chosen integrator from (q, p), in place.  When stage_q /
  * stage_p are non-null they receive the four RK4 stage states Y1..Y4 as
  * (4, N, 3) arrays (Y1 = y). */
-static void integ_step(int64_t n, int integ, double dt, double sigma, double* q, double* p,
+static void integ_step(int dim, int64_t n, int integ, double dt, double sigma, double* q, double* p,
                        double* stage_q, double* stage_p) {
-    const size_t m = (size_t)n * 3;
+    const size_t m = (size_t)n * dim;
     if (integ == 0) {
         double* Hq = malloc(m * sizeof(double));
         double* Hp = malloc(m * sizeof(double));
-        orc_step_forward(n, sigma, q, p, Hq, Hp);
+        orc_step_forward_d(dim, n, sigma, q, p, Hq, Hp);
         for (size_t k = 0; k < m; ++k) {
             q[k] += Hp[k] * dt;
             p[k] -= Hq[k] * dt;
@@ -363,7 +382,7 @@ static void integ_step(int64_t n, int integ, double dt, double sigma, double* q,
         }
         if (stage_q) memcpy(stage_q + (size_t)st * m, Yq, m * sizeof(double));
         if (stage_p) memcpy(stage_p + (size_t)st * m, Yp, m * sizeof(double));
-        orc_step_forward(n, sigma, Yq, Yp, Hq, Hp);
+        orc_step_forward_d(dim, n, sigma, Yq, Yp, Hq, Hp);
         for (size_t k = 0; k < m; ++k) {
             sq[k] += b[st] * Hp[k];
             sp[k] -= b[st] * Hq[k];
@@ -377,26 +396,26 @@ static void integ_step(int64_t n, int integ, double dt, double sigma, double* q,
 }
 
 /* Forward flow with the chosen integrator: T steps from (q0, p0). */
-void orc_shoot_forward_v(int64_t n, int T, double sigma, int integ, const double* q0, const double* p0,
+void orc_shoot_forward_v(int dim, int64_t n, int T, double sigma, int integ, const double* q0, const double* p0,
                          double* q1, double* p1) {
     const double dt = 1.0 / T;
-    const size_t m = (size_t)n * 3;
+    const size_t m = (size_t)n * dim;
     memcpy(q1, q0, m * sizeof(double));
     memcpy(p1, p0, m * sizeof(double));
-    for (int t = 0; t < T; ++t) integ_step(n, integ, dt, sigma, q1, p1, NULL, NULL);
+    for (int t = 0; t < T; ++t) integ_step(dim, n, integ, dt, sigma, q1, p1, NULL, NULL);
 }
 
 /* Eq. 3 objective of a variant: H at (p0, q0) or at (p(1), q(1)), plus
  * lambda ||q(1) - target||^2. */
-double orc_loss_v(int64_t n, int T, double sigma, double lambda, int integ, int h_at_end,
+double orc_loss_v(int dim, int64_t n, int T, double sigma, double lambda, int integ, int h_at_end,
                   const double* q0, const double* p0, const double* target) {
-    const size_t m = (size_t)n * 3;
+    const size_t m = (size_t)n * dim;
     double* q1 = malloc(m * sizeof(double));
     double* p1 = malloc(m * sizeof(double));
-    orc_shoot_forward_v(n, T, sigma, integ, q0, p0, q1, p1);
+    orc_shoot_forward_v(dim, n, T, sigma, integ, q0, p0, q1, p1);
     double mis = 0.0;
     for (size_t k = 0; k < m; ++k) mis += (q1[k] - target[k]) * (q1[k] - target[k]);
-    const double H = h_at_end ? orc_hamiltonian(n, sigma, q1, p1) : orc_hamiltonian(n, sigma, q0, p0);
+    const double H = h_at_end ? orc_hamiltonian_d(dim, n, sigma, q1, p1) : orc_hamiltonian_d(dim, n, sigma, q0, p0);
     free(q1); free(p1);
     return H + lambda * mis;
 }
@@ -404,12 +423,12 @@ double orc_loss_v(int64_t n, int T, double sigma, double lambda, int integ, int 
 /* ComputeGradient of a variant.  Returns the loss; grad_p0, grad_q0, q1, p1
  * (each may be null) as in orc_shoot_gradient; *H_out (may be null) is the
  * kinetic term of the loss. */
-double orc_shoot_gradient_v(int64_t n, int T, double sigma, double lambda, int integ, int h_at_end,
+double orc_shoot_gradient_v(int dim, int64_t n, int T, double sigma, double lambda, int integ, int h_at_end,
                             const double* q0, const double* p0, const double* target,
                             double* grad_p0, double* grad_q0, double* q1_out, double* p1_out,
                             double* H_out) {
     const double dt = 1.0 / T;
-    const size_t m = (size_t)n * 3;
+    const size_t m = (size_t)n * dim;
     const int S = integ == 0 ? 1 : 4;   /* stage states kept per step */
     double* tq = malloc((size_t)T * S * m * sizeof(double));
     double* tp = malloc((size_t)T * S * m * sizeof(double));
@@ -434,23 +453,23 @@ double orc_shoot_gradient_v(int64_t n, int T, double sigma, double lambda, int i
         if (integ == 0) {
             memcpy(sq, q, m * sizeof(double));
             memcpy(sp, p, m * sizeof(double));
-            integ_step(n, 0, dt, sigma, q, p, NULL, NULL);
+            integ_step(dim, n, 0, dt, sigma, q, p, NULL, NULL);
         } else {
-            integ_step(n, 1, dt, sigma, q, p, sq, sp);
+            integ_step(dim, n, 1, dt, sigma, q, p, sq, sp);
         }
     }
     double mis = 0.0;
     for (size_t k = 0; k < m; ++k) mis += (q[k] - target[k]) * (q[k] - target[k]);
     double H;
     if (h_at_end) {
-        H = orc_hamiltonian(n, sigma, q, p);
-        orc_step_forward(n, sigma, q, p, Hq, Hp);
+        H = orc_hamiltonian_d(dim, n, sigma, q, p);
+        orc_step_forward_d(dim, n, sigma, q, p, Hq, Hp);
         for (size_t k = 0; k < m; ++k) {
             alpha[k] = 2.0 * lambda * (q[k] - target[k]) + Hq[k];
             beta[k] = Hp[k];
         }
     } else {
-        H = orc_hamiltonian(n, sigma, q0, p0);
+        H = orc_hamiltonian_d(dim, n, sigma, q0, p0);
         for (size_t k = 0; k < m; ++k) {
             alpha[k] = 2.0 * lambda * (q[k] - target[k]);
             beta[k] = 0.0;
@@ -467,7 +486,7 @@ double orc_shoot_gradient_v(int64_t n, int T, double sigma, double lambda, int i
         const double* sq = tq + (size_t)t * S * m;
         const double* sp = tp + (size_t)t * S * m;
         if (integ == 0) {
-            orc_step_backward(n, sigma, sq, sp, alpha, beta, va, vb);
+            orc_step_backward_d(dim, n, sigma, sq, sp, alpha, beta, va, vb);
             for (size_t k = 0; k < m; ++k) {
                 alpha[k] += dt * va[k];
                 beta[k] += dt * vb[k];
@@ -481,7 +500,7 @@ double orc_shoot_gradient_v(int64_t n, int T, double sigma, double lambda, int i
                 ca[k] = cw[st] * dt * alpha[k] + (st < 3 ? cv[st] * dt * va[k] : 0.0);
                 cb[k] = cw[st] * dt * beta[k] + (st < 3 ? cv[st] * dt * vb[k] : 0.0);
             }
-            orc_step_backward(n, sigma, sq + (size_t)st * m, sp + (size_t)st * m, ca, cb, va, vb);
+            orc_step_backward_d(dim, n, sigma, sq + (size_t)st * m, sp + (size_t)st * m, ca, cb, va, vb);
             for (size_t k = 0; k < m; ++k) {
                 ya[k] += va[k];
                 yb[k] += vb[k];
@@ -490,7 +509,7 @@ double orc_shoot_gradient_v(int64_t n, int T, double sigma, double lambda, int i
         memcpy(alpha, ya, m * sizeof(double));
         memcpy(beta, yb, m * sizeof(double));
     }
-    if (!h_at_end) orc_step_forward(n, sigma, q0, p0, Hq, Hp);
+    if (!h_at_end) orc_step_forward_d(dim, n, sigma, q0, p0, Hq, Hp);
     for (size_t k = 0; k < m; ++k) {
         if (grad_p0) grad_p0[k] = beta[k] + (h_at_end ? 0.0 : Hp[k]);
         if (grad_q0) grad_q0[k] = alpha[k] + (h_at_end ? 0.0 : Hq[k]);
@@ -767,29 +786,29 @@ typedef struct {
     double sigma, lambda;
     const double* q0;
     const double* target;
-    int integ, h_at_end;
+    int integ, h_at_end, dim;
 } reg_ctx;
 
 static double reg_fg(void* p, const double* x, double* g) {
     const reg_ctx* r = p;
-    if (r->integ == 0 && r->h_at_end == 0)
+    if (r->integ == 0 && r->h_at_end == 0 && r->dim == 3)
         return orc_shoot_gradient(r->n, r->T, r->sigma, r->lambda, r->q0, x, r->target, g, NULL, NULL, NULL, NULL);
-    return orc_shoot_gradient_v(r->n, r->T, r->sigma, r->lambda, r->integ, r->h_at_end, r->q0, x, r->target, g,
-                                NULL, NULL, NULL, NULL);
+    return orc_shoot_gradient_v(r->dim, r->n, r->T, r->sigma, r->lambda, r->integ, r->h_at_end, r->q0, x, r->target,
+                                g, NULL, NULL, NULL, NULL);
 }
 
 int orc_register(int64_t n, int T, double sigma, double lambda, int m, int max_iter, double grad_tol,
                  const double* q0, const double* target, double* p0, double* loss, int* iters, int* evals,
                  double* trace) {
-    reg_ctx r = {n, T, sigma, lambda, q0, target, 0, 0};
+    reg_ctx r = {n, T, sigma, lambda, q0, target, 0, 0, 3};
     return orc_lbfgs(3 * n, p0, reg_fg, &r, m, max_iter, grad_tol, loss, iters, evals, trace);
 }
 
-/* register with a variant of the discretisation (integ, h_at_end as in
+/* register with a variant of the discretisation (dim, integ, h_at_end as in
  * orc_shoot_gradient_v). */
-int orc_register_v(int64_t n, int T, double sigma, double lambda, int integ, int h_at_end, int m, int max_iter,
-                   double grad_tol, const double* q0, const double* target, double* p0, double* loss, int* iters,
-                   int* evals, double* trace) {
-    reg_ctx r = {n, T, sigma, lambda, q0, target, integ, h_at_end};
-    return orc_lbfgs(3 * n, p0, reg_fg, &r, m, max_iter, grad_tol, loss, iters, evals, trace);
+int orc_register_v(int dim, int64_t n, int T, double sigma, double lambda, int integ, int h_at_end, int m,
+                   int max_iter, double grad_tol, const double* q0, const double* target, double* p0, double* loss,
+                   int* iters, int* evals, double* trace) {
+    reg_ctx r = {n, T, sigma, lambda, q0, target, integ, h_at_end, dim};
+    return orc_lbfgs(dim * n, p0, reg_fg, &r, m, max_iter, grad_tol, loss, iters, evals, trace);
 }

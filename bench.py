@@ -67,7 +67,7 @@ INSTR_PER_PAIR_VEL = 9
 # DRAM bytes (read + write) of one k_step_backward launch, from ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum, caches flushed before the
 # launch) of the current kernel, by N.  Empty it whenever the kernel changes.
-DRAM_BYTES_PER_BWD_LAUNCH = {4096: 416512, 16384: 1596160}
+DRAM_BYTES_PER_BWD_LAUNCH = {4096: 416512}
 
 
 def parse():
@@ -428,6 +428,38 @@ def measure_population(gsh, subjects=34, n=1847, T=40, max_iter=400, sigma=SIGMA
     }
 
 
+def planar_rate(gsh, reps):
+    """Gradient evaluations per second for planar landmarks: 4096 points on
+    an ellipse with semi-axes 1.0 / 0.6 (8 bumps), sigma = 0.05, T = 20,
+    lambda = 10; device inputs, CUDA events.  The momenta are the smooth
+    field (target - q0) / (kernel row mass), about sqrt(2 pi) sigma N /
+    perimeter."""
+    import math
+    import torch
+    import landmark_synth as ls
+    dev = torch.device("cuda", torch.cuda.current_device())
+    pr = ls.ellipse_pair(N_LANDMARKS, seed=0, n_bumps=8)
+    mass = math.sqrt(2 * math.pi) * 0.05 * N_LANDMARKS / (2 * math.pi * math.sqrt((1.0 + 0.36) / 2))
+    p0 = (pr.target - pr.q0) / mass
+    dq, dp, dt = (torch.tensor(np.asarray(a, np.float32), device=dev) for a in (pr.q0, p0, pr.target))
+    stream = torch.cuda.current_stream(dev)
+    f = lambda: gsh.shoot_gradient(dq, dp, dt, T_STEPS, 0.05, LAMBDA)
+    for _ in range(3):
+        f()
+    torch.cuda.synchronize(dev)
+    out = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        f()
+        b.record(stream)
+        b.synchronize()
+        out.append(a.elapsed_time(b))
+    ms = float(np.median(out))
+    return {"N": N_LANDMARKS, "T": T_STEPS, "sigma": 0.05, "grad_evals_per_s": 1e3 / ms,
+            "pair_interactions_per_s": 2 * T_STEPS * N_LANDMARKS ** 2 / (ms * 1e-3)}
+
+
 def measure_variants(gsh, reps=50, fit_iters=30):
     """The RK4 integrator against the paper's Euler steps at equal pair work
     (RK4 with T = 5 evaluates the pair sums 20 times per sweep, as Euler
@@ -470,6 +502,7 @@ def measure_variants(gsh, reps=50, fit_iters=30):
         "euler_T20": {"grad_evals_per_s": rate(20, "euler"), "q1_rel_err": err(20, "euler")},
         "rk4_T5": {"grad_evals_per_s": rate(5, "rk4"), "q1_rel_err": err(5, "rk4")},
         "rk4_T5_kinetic_end": {"grad_evals_per_s": rate(5, "rk4", "end")},
+        "planar_euler_T20": planar_rate(gsh, reps),
         "timing": "shoot_gradient through the binding, CUDA events, median of %d" % reps,
     }
 

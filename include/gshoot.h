@@ -87,6 +87,11 @@ typedef struct gs_params {
     int32_t integrator; /* GS_EULER (0, the paper's) or GS_RK4; the gradient is
                            always the exact adjoint of the chosen steps */
     int32_t kinetic_at; /* GS_KINETIC_START (0) or GS_KINETIC_END */
+    int32_t dim;        /* dimension of the landmarks: 3 (or 0) for 3-D, 2 for planar
+                           landmarks (the paper codes both cases, Section 2.5).  With
+                           dim = 2 every landmark array of shoot_forward,
+                           shoot_gradient and register_landmarks is (N, 2) */
+    int32_t reserved;   /* set to 0 */
 } gs_params;
 
 /*
@@ -179,7 +184,8 @@ gs_status velocity_field(int64_t N, int64_t M, double sigma, const float* q, con
  * In: prm (N, T, sigma used), q0, p0 (N, 3), x0 (M, 3).  Out: x1 (M, 3).
  * Arrays as in velocity_field.  Errors as in shoot_forward; M outside
  * [1, 2^26] or a NULL point array is GS_EINVAL, and so is an integrator
- * other than GS_EULER (the points take Euler steps only).
+ * other than GS_EULER (the points take Euler steps only) or dim = 2 (3-D
+ * only).
  */
 gs_status flow_points(const gs_params* prm, const float* q0, const float* p0, int64_t M,
                       const float* x0, float* x1, void* stream);
@@ -226,8 +232,8 @@ typedef struct gs_batch_problem {
  * register_batch — B independent runs of register_landmarks, packed: every
  * time step of every gradient evaluation is one launch over all problems
  * still running.  Shared settings: T, lbfgs_m (1..64), max_iter, grad_tol.
- * Every problem uses the Euler integrator and the kinetic term at t = 0
- * (GS_EULER, GS_KINETIC_START), as does the server.
+ * Every problem is 3-D and uses the Euler integrator and the kinetic term
+ * at t = 0 (GS_EULER, GS_KINETIC_START), as does the server.
  * Writes probs[b].p0 (when non-NULL) and probs[b].info.  Each problem
  * follows the same L-BFGS as register_landmarks.  Returns GS_OK,
  * GS_NOT_CONVERGED if any problem stopped short of grad_tol, or the first
@@ -377,6 +383,19 @@ gs_status gs_max_active_clusters(int32_t kind, int32_t threads, int32_t R, int32
                                  int32_t cluster, int32_t* clusters);
 
 /*
+ * gs_set_late_trigger — tuning (no counterpart in the paper): when a fused
+ * time-step kernel lets the next kernel of the graph launch (programmatic
+ * dependent launch) before it finishes.  The trigger is issued after the
+ * pair sums, so that the next step's launch overlaps only the reduction and
+ * the epilogue; the next step still waits for this one's results.  mode -1
+ * (the initial state): the library's rule, reverse-step grids whose CTAs are
+ * all resident at once (forward steps measured slower with the trigger);
+ * 0: never; 1: every step kernel.  Clears the cached graphs.  GS_EINVAL for
+ * another mode.
+ */
+gs_status gs_set_late_trigger(int32_t mode);
+
+/*
  * gs_set_phase_timing — diagnostics (no counterpart in the paper): when `on`
  * is nonzero, the CUDA graphs of shoot_forward / shoot_gradient (and of the
  * L-BFGS evaluations) on the current device record three events: before the
@@ -401,7 +420,7 @@ const char* gs_last_error(void);
 void gs_release_workspace(void);
 
 /* Library ABI version: 100 * major + minor (101: gs_params gained
- * integrator and kinetic_at). */
+ * integrator and kinetic_at; 102: dim). */
 int32_t gs_version(void);
 
 #ifdef __cplusplus

@@ -22,6 +22,12 @@ Recipe (fixed draw order, one ``numpy.random.default_rng(seed)`` stream):
 4. bump amplitudes: iid N(0, amp^2) per coordinate, one 3-vector per bump.
 5. target = template + sum_b A_b exp(-||x - c_b||^2 / (2 sigma_b^2)).
 
+Planar landmarks (the paper codes the 2-D case too): ``ellipse_pair`` draws
+``n`` points arc-length-uniform on the ellipse with semi-axes ``axes`` (an
+angle t uniform in [0, 2 pi), kept with probability
+sqrt(a^2 sin^2 t + b^2 cos^2 t) / max(a, b)), then jitter, bump centres and
+amplitudes and the target exactly as in steps 2-5, in two dimensions.
+
 Population (one template, many subjects; the shape of Section 3.1's study of
 34 subjects with 1847 landmarks each): a base surface is drawn by steps 1-2
 from ``default_rng(seed)``.  Subject s draws steps 3-5 from its own stream
@@ -44,6 +50,7 @@ __all__ = [
     "poisson_trace",
     "Population",
     "population",
+    "ellipse_pair",
 ]
 
 
@@ -163,3 +170,30 @@ def population(n: int = 1847, subjects: int = 34, seed: int = 0, n_bumps: int = 
         targets.append(np.ascontiguousarray(base + disp))
     template = np.ascontiguousarray(np.mean(np.stack(targets), axis=0))
     return Population(template=template, targets=targets, seed=seed)
+
+
+def ellipse_pair(n: int, seed: int = 0, n_bumps: int = 8, axes=(1.0, 0.6), jitter: float = 0.01,
+                 bump_sigma: float = 0.3, bump_amp: float = 0.1) -> LandmarkPair:
+    """Planar template on an ellipse and a bump-deformed target (module doc)."""
+    if n < 1:
+        raise ValueError("n must be >= 1")
+    rng = np.random.default_rng(seed)
+    a, b = (float(x) for x in axes)
+    out, have = [], 0
+    while have < n:
+        batch = max(64, 2 * (n - have))
+        t = rng.uniform(0.0, 2.0 * math.pi, size=batch)
+        w = np.sqrt((a * np.sin(t)) ** 2 + (b * np.cos(t)) ** 2) / max(a, b)
+        keep = rng.random(batch) < w
+        out.append(np.stack([a * np.cos(t[keep]), b * np.sin(t[keep])], axis=1))
+        have += int(keep.sum())
+    x = np.concatenate(out, axis=0)[:n]
+    x = x + rng.normal(0.0, jitter, size=x.shape)
+    nb = min(n_bumps, n)
+    centres = x[rng.choice(n, size=nb, replace=False)]
+    amps = rng.normal(0.0, bump_amp, size=(nb, 2))
+    disp = np.zeros_like(x)
+    for cb, ab in zip(centres, amps):
+        wgt = np.exp(-np.sum((x - cb) ** 2, axis=1) / (2.0 * bump_sigma ** 2))
+        disp += wgt[:, None] * ab[None, :]
+    return LandmarkPair(q0=np.ascontiguousarray(x), target=np.ascontiguousarray(x + disp), seed=seed)

@@ -4,7 +4,8 @@ A thin Python binding over the C ABI of ``libgshoot.so`` (include/gshoot.h).
 The names are the same as in the ABI.  The binding only marshals arguments;
 the CUDA kernels of the library do every step of the computation.
 
-Arrays are (N, 3).  Two forms are accepted:
+Arrays are (N, 3); shoot_forward, shoot_gradient, shoot and register also
+take planar landmarks as (N, 2).  Two forms are accepted:
 * torch CUDA tensors.  They are cast to contiguous float32, and the work runs
   on the current torch stream.  The outputs are CUDA tensors.
 * numpy arrays or CPU tensors.  The library stages them through its device
@@ -34,10 +35,17 @@ def _is_cuda_tensor(x) -> bool:
     return isinstance(x, torch.Tensor) and x.is_cuda
 
 
-class _Marshal:
-    """Pointers for one call: either all-device (torch) or all-host (numpy)."""
+def _dim_of(x) -> int:
+    """2 for (N, 2) landmark arrays, else 3 (shapes are checked on marshalling)."""
+    shape = tuple(x.shape)
+    return 2 if len(shape) == 2 and shape[1] == 2 else 3
 
-    def __init__(self, first, n=None):
+
+class _Marshal:
+    """Pointers for one call: either all-device (torch) or all-host (numpy).
+    Landmark arrays are (rows, dim) with dim 3, or 2 for planar landmarks."""
+
+    def __init__(self, first, n=None, dim=3):
         self.device = _is_cuda_tensor(first)
         self.keep = []
         if self.device:
@@ -48,9 +56,10 @@ class _Marshal:
         else:
             self.stream = ctypes.c_void_p(0)
         self.n = n
+        self.dim = dim
 
     def inp(self, x, name, rows=None):
-        """Pointer to x as (rows, 3) FP32; rows defaults to the call's N."""
+        """Pointer to x as (rows, dim) FP32; rows defaults to the call's N."""
         if x is None:
             return None
         if self.device:
@@ -65,8 +74,8 @@ class _Marshal:
             t = np.ascontiguousarray(x, dtype=np.float32)
             arr_shape = t.shape
             ptr = t.ctypes.data
-        if len(arr_shape) != 2 or arr_shape[1] != 3:
-            raise ValueError("%s: expected shape (N, 3), got %r" % (name, arr_shape))
+        if len(arr_shape) != 2 or arr_shape[1] != self.dim:
+            raise ValueError("%s: expected shape (N, %d), got %r" % (name, self.dim, arr_shape))
         if rows is not None:
             if arr_shape[0] != rows:
                 raise ValueError("%s: expected %d rows, got %d" % (name, rows, arr_shape[0]))
@@ -80,24 +89,25 @@ class _Marshal:
     def out(self, rows=None):
         rows = self.n if rows is None else rows
         if self.device:
-            t = self.torch.empty((rows, 3), dtype=self.torch.float32, device=self.dev)
+            t = self.torch.empty((rows, self.dim), dtype=self.torch.float32, device=self.dev)
             ptr = t.data_ptr()
         else:
-            t = np.empty((rows, 3), dtype=np.float32)
+            t = np.empty((rows, self.dim), dtype=np.float32)
             ptr = t.ctypes.data
         self.keep.append(t)
         return t, ctypes.c_void_p(ptr)
 
 
 def _params(n, T, sigma, lam=0.0, ckpt_every=0, lbfgs_m=10, max_iter=100, grad_tol=1e-5, integrator="euler",
-            h_at="start"):
+            h_at="start", dim=3):
     if integrator not in INTEGRATORS:
         raise ValueError("integrator must be one of %r" % sorted(INTEGRATORS))
     if h_at not in KINETIC_AT:
         raise ValueError("h_at must be one of %r" % sorted(KINETIC_AT))
     return GsParams(N=int(n), T=int(T), ckpt_every=int(ckpt_every), sigma=float(sigma),
                     lambda_=float(lam), lbfgs_m=int(lbfgs_m), max_iter=int(max_iter),
-                    grad_tol=float(grad_tol), integrator=INTEGRATORS[integrator], kinetic_at=KINETIC_AT[h_at])
+                    grad_tol=float(grad_tol), integrator=INTEGRATORS[integrator], kinetic_at=KINETIC_AT[h_at],
+                    dim=int(dim), reserved=0)
 
 
 def step_forward(q, p, sigma):
@@ -148,10 +158,10 @@ def step_backward(q, p, alpha, beta, sigma):
 
 def shoot_forward(q0, p0, T, sigma, integrator="euler"):
     """Forward flow of Algorithm 1: returns (q1, p1, H0) with H0 = H(p0, q0).
-    integrator: "euler" (the paper's) or "rk4"."""
-    m = _Marshal(q0)
+    integrator: "euler" (the paper's) or "rk4".  (N, 2) arrays: planar landmarks."""
+    m = _Marshal(q0, dim=_dim_of(q0))
     pq, pp = m.inp(q0, "q0"), m.inp(p0, "p0")
-    prm = _params(m.n, T, sigma, integrator=integrator)
+    prm = _params(m.n, T, sigma, integrator=integrator, dim=m.dim)
     q1, o1 = m.out()
     p1, o2 = m.out()
     h0 = ctypes.c_double(0.0)
@@ -162,10 +172,11 @@ def shoot_forward(q0, p0, T, sigma, integrator="euler"):
 def shoot_gradient(q0, p0, target, T, sigma, lam, ckpt_every=0, integrator="euler", h_at="start"):
     """ComputeGradient of Algorithm 1: returns (loss, dL/dp0, dL/dq0) for
     L = H(p0, q0) + lam ||q(1) - target||^2 (h_at="end": H(p(1), q(1))
-    instead), with the flow integrated by "euler" or "rk4" steps."""
-    m = _Marshal(q0)
+    instead), with the flow integrated by "euler" or "rk4" steps.  (N, 2)
+    arrays: planar landmarks."""
+    m = _Marshal(q0, dim=_dim_of(q0))
     pq, pp, pt = m.inp(q0, "q0"), m.inp(p0, "p0"), m.inp(target, "target")
-    prm = _params(m.n, T, sigma, lam, ckpt_every, integrator=integrator, h_at=h_at)
+    prm = _params(m.n, T, sigma, lam, ckpt_every, integrator=integrator, h_at=h_at, dim=m.dim)
     gp, og = m.out()
     gq, oq = m.out()
     loss = ctypes.c_double(0.0)
@@ -221,21 +232,21 @@ def register(q0, target, T, sigma, lam, p0=None, m=10, max_iter=100, grad_tol=1e
     """Algorithm 1, outer optimisation: L-BFGS over p0 of the Eq. 3 loss.  Returns
     (p0, info) with info a dict (loss, grad_norm0, grad_norm, avg_dist,
     max_dist, iters, evals, status).  integrator / h_at select the variant
-    of the discretisation as in shoot_gradient."""
-    m_ = _Marshal(q0)
+    of the discretisation as in shoot_gradient.  (N, 2) arrays: planar landmarks."""
+    m_ = _Marshal(q0, dim=_dim_of(q0))
     pq, pt = m_.inp(q0, "q0"), m_.inp(target, "target")
     if p0 is None:
-        p0 = np.zeros((m_.n, 3), np.float32) if not m_.device else m_.torch.zeros(
-            (m_.n, 3), dtype=m_.torch.float32, device=m_.dev)
+        p0 = np.zeros((m_.n, m_.dim), np.float32) if not m_.device else m_.torch.zeros(
+            (m_.n, m_.dim), dtype=m_.torch.float32, device=m_.dev)
     if m_.device:
         pout = p0.detach().to(device=m_.dev, dtype=m_.torch.float32).clone().contiguous()
         pp = ctypes.c_void_p(pout.data_ptr())
     else:
         pout = np.array(p0.detach().cpu().numpy() if hasattr(p0, "detach") else p0, dtype=np.float32, copy=True)
         pp = ctypes.c_void_p(pout.ctypes.data)
-    if tuple(pout.shape) != (m_.n, 3):
-        raise ValueError("p0: expected shape (%d, 3)" % m_.n)
-    prm = _params(m_.n, T, sigma, lam, 0, m, max_iter, grad_tol, integrator, h_at)
+    if tuple(pout.shape) != (m_.n, m_.dim):
+        raise ValueError("p0: expected shape (%d, %d)" % (m_.n, m_.dim))
+    prm = _params(m_.n, T, sigma, lam, 0, m, max_iter, grad_tol, integrator, h_at, m_.dim)
     info = GsRegisterInfo()
     check(load().register_landmarks(ctypes.byref(prm), pq, pt, pp, ctypes.byref(info), m_.stream))
     return pout, info.as_dict()

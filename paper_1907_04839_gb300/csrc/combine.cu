@@ -1,5 +1,6 @@
-// O(N) kernels around the pair sums: packing the (N,3) caller arrays into
-// the FP64 master state and the prescaled FP32 float4 copies, unpacking
+// O(N) kernels around the pair sums: packing the (N,3) caller arrays (or
+// (N,2) for planar landmarks) into the FP64 master state and the prescaled
+// FP32 pair records, unpacking
 // results, and summing split partials straight to (N,3) outputs for the
 // single-step entry points.
 //
@@ -20,10 +21,12 @@ constexpr int kThreads = 128;
 constexpr int kGroup = 8;  // lanes that share one landmark's split partials
 
 
+// One thread per coordinate of the (N, D) caller arrays.
+template <int D>
 __global__ void __launch_bounds__(kThreads) k_pack(PackArgs a) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 3 * a.n) return;
-  const int i = t / 3, k = t - 3 * i;
+  if (t >= D * a.n) return;
+  const int i = t / D, k = t - D * i;
   const float q = a.q[t];
   const double p = a.p64_in ? a.p64_in[t] : (a.p ? (double)a.p[t] : 0.0);
   const float tg = a.tgt ? a.tgt[t] : 0.f;
@@ -31,22 +34,23 @@ __global__ void __launch_bounds__(kThreads) k_pack(PackArgs a) {
   a.q64[t] = q;
   a.p64[t] = p;
   if (a.t64) a.t64[t] = tg;
-  float* r = reinterpret_cast<float*>(a.qp + (i >> 1) * kRecF4) + 2 * k + (i & 1);
+  float* r = reinterpret_cast<float*>(a.qp + (i >> 1) * D) + 2 * k + (i & 1);
   r[0] = -(float)(a.kq * (double)q);
-  r[6] = (float)p;
+  r[2 * D] = (float)p;
 }
 
+template <int D>
 __global__ void __launch_bounds__(kThreads) k_restore(const double* ckq, const double* ckp, double* q64,
                                                       double* p64, float4* rec, int n, double kq) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 3 * n) return;
-  const int i = t / 3, k = t - 3 * i;
+  if (t >= D * n) return;
+  const int i = t / D, k = t - D * i;
   const double q = ckq[t], p = ckp[t];
   q64[t] = q;
   p64[t] = p;
-  float* r = reinterpret_cast<float*>(rec + (i >> 1) * kRecF4) + 2 * k + (i & 1);
+  float* r = reinterpret_cast<float*>(rec + (i >> 1) * D) + 2 * k + (i & 1);
   r[0] = -(float)(kq * q);
-  r[6] = (float)p;
+  r[2 * D] = (float)p;
 }
 
 // Sum the split partials of landmark i over a group of kGroup lanes: lane l
@@ -150,13 +154,19 @@ int combine_group() { return kGroup; }
 
 cudaError_t launch_pack(const PackArgs& a, cudaStream_t st) {
   if (a.n <= 0) return cudaSuccess;
-  k_pack<<<blocks_for(3LL * a.n), kThreads, 0, st>>>(a);
+  if (a.dim == 2)
+    k_pack<2><<<blocks_for(2LL * a.n), kThreads, 0, st>>>(a);
+  else
+    k_pack<3><<<blocks_for(3LL * a.n), kThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_restore(const double* ckq, const double* ckp, double* q64, double* p64, float4* rec, int n,
-                           double kq, cudaStream_t st) {
-  k_restore<<<blocks_for(3LL * n), kThreads, 0, st>>>(ckq, ckp, q64, p64, rec, n, kq);
+                           double kq, cudaStream_t st, int dim) {
+  if (dim == 2)
+    k_restore<2><<<blocks_for(2LL * n), kThreads, 0, st>>>(ckq, ckp, q64, p64, rec, n, kq);
+  else
+    k_restore<3><<<blocks_for(3LL * n), kThreads, 0, st>>>(ckq, ckp, q64, p64, rec, n, kq);
   return cudaGetLastError();
 }
 

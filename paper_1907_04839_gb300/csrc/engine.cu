@@ -119,11 +119,12 @@ gs_status reserve(Workspace& w, int npad, int T, int splits, int nck) {
 
 // Zero the float4 trajectory and adjoint arrays when the landmark count
 // changes: padded entries must be exactly zero (they are never written).
-gs_status ensure_clean(Workspace& w, int n, cudaStream_t st) {
-  if (w.clean_n == n) return GS_OK;
+gs_status ensure_clean(Workspace& w, int n, cudaStream_t st, int dim) {
+  const int key = 4 * n + dim;
+  if (w.clean_n == key) return GS_OK;
   GS_CUDA(cudaMemsetAsync(w.traj, 0, sizeof(float4) * (w.cap_T + 1) * w.slot(), st));
   GS_CUDA(cudaMemsetAsync(w.adj, 0, 2 * sizeof(float4) * w.slot(), st));
-  w.clean_n = n;
+  w.clean_n = key;
   return GS_OK;
 }
 
@@ -185,6 +186,7 @@ gs_status check_params(const gs_params* prm) {
     return fail(GS_EINVAL, "integrator must be GS_EULER or GS_RK4");
   if (prm->kinetic_at != GS_KINETIC_START && prm->kinetic_at != GS_KINETIC_END)
     return fail(GS_EINVAL, "kinetic_at must be GS_KINETIC_START or GS_KINETIC_END");
+  if (prm->dim != 0 && prm->dim != 2 && prm->dim != 3) return fail(GS_EINVAL, "dim must be 2 or 3 (0 means 3)");
   return GS_OK;
 }
 
@@ -195,7 +197,7 @@ gs_status check_params(const gs_params* prm) {
 // terminal launch instead of the last step.
 StepFwdArgs forward_step_args(Workspace& w, const StepConfig& c, int kind, int n, int T, int k, double sigma,
                               double lambda, int rd = -1, int wr = -1, bool recompute = false, int integ = GS_EULER,
-                              int stage = 0, int h_end = 0) {
+                              int stage = 0, int h_end = 0, int dim = 3) {
   const int S = stages_of(integ);
   const int j = S * k + stage;  // launch index of the sweep
   const int npad = round_up(n, kPad);
@@ -224,6 +226,7 @@ StepFwdArgs forward_step_args(Workspace& w, const StepConfig& c, int kind, int n
   a.qa64 = w.qa64;
   a.pa64 = w.pa64;
   a.adj_scale = integ == GS_RK4 ? (1.0 / T) / 6.0 : 1.0;
+  a.dim = dim;
   a.t64 = w.t64;
   a.lambda = lambda;
   a.a64 = w.a64;
@@ -242,7 +245,7 @@ StepFwdArgs forward_step_args(Workspace& w, const StepConfig& c, int kind, int n
 // k = T-1-s/S, stage S-1-s%S; S = 1 for Euler, 4 for RK4).  rd defaults to
 // the record slot of that stage state.
 StepBwdArgs backward_step_args(Workspace& w, const StepConfig& c, int n, int T, int s, double sigma, int rd = -1,
-                               int integ = GS_EULER, int h_end = 0) {
+                               int integ = GS_EULER, int h_end = 0, int dim = 3) {
   const int npad = round_up(n, kPad);
   const KernelScales sc = make_scales(sigma);
   const size_t slot = w.slot();
@@ -258,6 +261,7 @@ StepBwdArgs backward_step_args(Workspace& w, const StepConfig& c, int n, int T, 
   b.ya64 = w.ya64;
   b.yb64 = w.yb64;
   b.h_at_end = h_end;
+  b.dim = dim;
   b.n = n;
   b.npad = npad;
   b.split_len = c.split_len;
@@ -292,18 +296,20 @@ StepBwdArgs backward_step_args(Workspace& w, const StepConfig& c, int n, int T, 
 // record is bitwise the one the forward sweep made, because it comes from
 // the same FP64 state through the same kernels.
 gs_status enqueue_steps(Workspace& w, int kind, int n, int T, double sigma, double lambda, int ckpt, int integ,
-                        int h_end, cudaStream_t st, const cudaEvent_t* ev) {
+                        int h_end, int dim, cudaStream_t st, const cudaEvent_t* ev) {
   const int npad = round_up(n, kPad);
   if (kind == 0) {
     ckpt = 0;
     h_end = 0;
   }
-  const bool variants = integ != GS_EULER || h_end;
+  // Variant and planar launches run the built-in configuration's kernels.
+  const bool variants = integ != GS_EULER || h_end || dim == 2;
   const StepConfig fc = choose_step_config(0, npad, w.num_sms, variants);
   const StepConfig bc = choose_step_config(1, npad, w.num_sms, variants);
   if (fc.threads == 0 || bc.threads == 0) return fail(GS_EINVAL, "no step kernel configuration");
+  const int ftrig = late_trigger_for(0, fc) ? 1 : 0, btrig = late_trigger_for(1, bc) ? 1 : 0;
   const int S = stages_of(integ);
-  const size_t n3 = 3 * static_cast<size_t>(n);
+  const size_t n3 = static_cast<size_t>(dim) * n;  // FP64 state per checkpoint array
   if (ev) GS_CUDA(cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal));
   for (int k = 0; k < T; ++k) {
     if (ckpt && k % ckpt == 0) {
@@ -314,16 +320,18 @@ gs_status enqueue_steps(Workspace& w, int kind, int n, int T, double sigma, doub
     for (int s = 0; s < S; ++s) {
       const int j = S * k + s;
       const int rd = ckpt ? (j & 1) : -1, wr = ckpt ? ((j + 1) & 1) : -1;
-      const StepFwdArgs a = forward_step_args(w, fc, kind, n, T, k, sigma, lambda, rd, wr, false, integ, s, h_end);
+      StepFwdArgs a = forward_step_args(w, fc, kind, n, T, k, sigma, lambda, rd, wr, false, integ, s, h_end, dim);
+      a.late_trigger = ftrig;
       GS_CUDA(launch_step_forward(fc, a, st, j > 0));
     }
   }
   if (h_end) {
     const int rd = ckpt ? ((S * T) & 1) : S * T;
-    StepFwdArgs a = forward_step_args(w, fc, kind, n, T, T - 1, sigma, lambda, rd, rd, true, integ, 0, 1);
+    StepFwdArgs a = forward_step_args(w, fc, kind, n, T, T - 1, sigma, lambda, rd, rd, true, integ, 0, 1, dim);
     a.terminal = 1;
     a.last = 1;
     a.with_loss = 1;
+    a.late_trigger = ftrig;
     GS_CUDA(launch_step_forward(fc, a, st, true));
   }
   if (ev) GS_CUDA(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
@@ -333,7 +341,8 @@ gs_status enqueue_steps(Workspace& w, int kind, int n, int T, double sigma, doub
   }
   if (!ckpt) {
     for (int s = 0; s < S * T; ++s) {
-      const StepBwdArgs b = backward_step_args(w, bc, n, T, s, sigma, -1, integ, h_end);
+      StepBwdArgs b = backward_step_args(w, bc, n, T, s, sigma, -1, integ, h_end, dim);
+      b.late_trigger = s + 1 < S * T ? btrig : 0;
       GS_CUDA(launch_step_backward(bc, b, st, true));
     }
     if (ev) GS_CUDA(cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal));
@@ -345,15 +354,17 @@ gs_status enqueue_steps(Workspace& w, int kind, int n, int T, double sigma, doub
   for (int m = nseg - 1; m >= 0; --m) {
     const int s0 = m * ckpt, len = std::min(ckpt, T - s0);
     const double* ck = w.ck64 + 2 * static_cast<size_t>(m) * n3;
-    GS_CUDA(launch_restore(ck, ck + n3, w.q64, w.p64, w.traj, n, sc.kq, st));
+    GS_CUDA(launch_restore(ck, ck + n3, w.q64, w.p64, w.traj, n, sc.kq, st, dim));
     // stage launches 0 .. S*len-2 of the segment write slots 1 .. S*len-1
     for (int r = 0; r + 1 < S * len; ++r) {
-      const StepFwdArgs a =
-          forward_step_args(w, fc, kind, n, T, s0 + r / S, sigma, lambda, r, r + 1, true, integ, r % S, h_end);
+      StepFwdArgs a =
+          forward_step_args(w, fc, kind, n, T, s0 + r / S, sigma, lambda, r, r + 1, true, integ, r % S, h_end, dim);
+      a.late_trigger = ftrig;
       GS_CUDA(launch_step_forward(fc, a, st, r > 0));
     }
     for (int r = S * len - 1; r >= 0; --r, ++s) {
-      const StepBwdArgs b = backward_step_args(w, bc, n, T, s, sigma, r, integ, h_end);
+      StepBwdArgs b = backward_step_args(w, bc, n, T, s, sigma, r, integ, h_end, dim);
+      b.late_trigger = btrig;
       GS_CUDA(launch_step_backward(bc, b, st, true));
     }
   }
@@ -370,8 +381,8 @@ gs_status get_graph(Workspace& w, const GraphKey& key, cudaGraphExec_t* out) {
   if (w.graphs.size() >= 16) w.drop_graphs();
   cudaStream_t cs = w.capture_stream;
   GS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  gs_status s = enqueue_steps(w, key.kind, key.n, key.T, key.sigma, key.lambda, key.ckpt, key.integ, key.h_end, cs,
-                              key.timed ? w.phase : nullptr);
+  gs_status s = enqueue_steps(w, key.kind, key.n, key.T, key.sigma, key.lambda, key.ckpt, key.integ, key.h_end,
+                              key.dim, cs, key.timed ? w.phase : nullptr);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(cs, &g);
   if (s != GS_OK) {
@@ -390,8 +401,8 @@ gs_status get_graph(Workspace& w, const GraphKey& key, cudaGraphExec_t* out) {
 
 gs_status enqueue_gradient64(Workspace& w, const gs_params& prm, const float* dq, const double* p64_in,
                              const float* dt, cudaStream_t st) {
-  const int n = static_cast<int>(prm.N);
-  gs_status s = ensure_clean(w, n, st);
+  const int n = static_cast<int>(prm.N), dim = dim_of(prm);
+  gs_status s = ensure_clean(w, n, st, dim);
   if (s != GS_OK) return s;
   PackArgs pk;
   pk.q = dq;
@@ -405,10 +416,11 @@ gs_status enqueue_gradient64(Workspace& w, const gs_params& prm, const float* dq
   pk.n = n;
   pk.kq = make_scales(prm.sigma).kq;
   pk.status = w.status;
+  pk.dim = dim;
   GS_CUDA(launch_pack(pk, st));
   cudaGraphExec_t ge = nullptr;
   const GraphKey key{1,           n, prm.T, prm.sigma, prm.lambda, effective_ckpt(prm.ckpt_every, prm.T), w.phase_timing,
-                     prm.integrator, prm.kinetic_at};
+                     prm.integrator, prm.kinetic_at, dim};
   if ((s = get_graph(w, key, &ge)) != GS_OK) return s;
   GS_CUDA(cudaGraphLaunch(ge, st));
   return GS_OK;
@@ -416,8 +428,8 @@ gs_status enqueue_gradient64(Workspace& w, const gs_params& prm, const float* dq
 
 gs_status enqueue_forward64(Workspace& w, const gs_params& prm, const float* dq, const double* p64_in,
                             cudaStream_t st) {
-  const int n = static_cast<int>(prm.N);
-  gs_status s = ensure_clean(w, n, st);
+  const int n = static_cast<int>(prm.N), dim = dim_of(prm);
+  gs_status s = ensure_clean(w, n, st, dim);
   if (s != GS_OK) return s;
   PackArgs pk;
   pk.q = dq;
@@ -431,9 +443,11 @@ gs_status enqueue_forward64(Workspace& w, const gs_params& prm, const float* dq,
   pk.n = n;
   pk.kq = make_scales(prm.sigma).kq;
   pk.status = w.status;
+  pk.dim = dim;
   GS_CUDA(launch_pack(pk, st));
   cudaGraphExec_t ge = nullptr;
-  if ((s = get_graph(w, GraphKey{0, n, prm.T, prm.sigma, 0.0, 0, w.phase_timing, prm.integrator, 0}, &ge)) != GS_OK)
+  if ((s = get_graph(w, GraphKey{0, n, prm.T, prm.sigma, 0.0, 0, w.phase_timing, prm.integrator, 0, dim}, &ge)) !=
+      GS_OK)
     return s;
   GS_CUDA(cudaGraphLaunch(ge, st));
   return GS_OK;
@@ -455,8 +469,9 @@ gs_status run_shoot(int kind, const gs_params* prm, const float* q0, const float
       GS_OK)
     return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if ((s = ensure_clean(*w, n, st)) != GS_OK) return s;
-  const size_t n3 = 3 * static_cast<size_t>(n);
+  const int dim = dim_of(*prm);
+  if ((s = ensure_clean(*w, n, st, dim)) != GS_OK) return s;
+  const size_t n3 = static_cast<size_t>(dim) * n;  // floats per (N, dim) array
   bool host = false;
   const float *dq = nullptr, *dp = nullptr, *dt = nullptr;
   if ((s = stage_in(q0, w->in_q, n3, st, &dq, &host)) != GS_OK) return s;
@@ -474,10 +489,11 @@ gs_status run_shoot(int kind, const gs_params* prm, const float* q0, const float
   pk.n = n;
   pk.kq = make_scales(prm->sigma).kq;
   pk.status = w->status;
+  pk.dim = dim;
   GS_CUDA(launch_pack(pk, st));
   cudaGraphExec_t ge = nullptr;
   const GraphKey key{kind,           n, T, prm->sigma, kind == 1 ? prm->lambda : 0.0, ckpt, w->phase_timing,
-                     prm->integrator, kind == 1 ? prm->kinetic_at : 0};
+                     prm->integrator, kind == 1 ? prm->kinetic_at : 0, dim};
   if ((s = get_graph(*w, key, &ge)) != GS_OK) return s;
   GS_CUDA(cudaGraphLaunch(ge, st));
   bool want_sync = host;
@@ -573,6 +589,7 @@ gs_status run_step(int kind, int64_t N, double sigma, const float* q, const floa
 gs_status time_pair_kernels(const gs_params* prm, const float* q0, const float* p0, const float* target,
                             int reps, double* fwd_ms, double* bwd_ms, int* launches, void* stream) {
   if (reps < 1 || reps > 100000) return fail(GS_EINVAL, "reps must be in [1, 100000]");
+  if (prm && dim_of(*prm) != 3) return fail(GS_EINVAL, "gs_time_pair_kernels times the 3-D kernels (dim 3)");
   double loss = 0.0;
   gs_status s = run_shoot(1, prm, q0, p0, target, nullptr, nullptr, nullptr, &loss, nullptr, nullptr, stream);
   if (s != GS_OK) return s;
@@ -797,6 +814,15 @@ gs_status gs_set_cluster_policy(int32_t policy) {
   return GS_OK;
 }
 
+gs_status gs_set_late_trigger(int32_t mode) {
+  gs::g_err.clear();
+  if (mode < -1 || mode > 1) return gs::fail(GS_EINVAL, "mode must be -1, 0 or 1");
+  std::lock_guard<std::mutex> lk(gs::g_mu);
+  gs::set_late_trigger(mode);
+  for (auto& kv : gs::g_ws) kv.second->drop_graphs();
+  return GS_OK;
+}
+
 gs_status gs_max_active_clusters(int32_t kind, int32_t threads, int32_t R, int32_t groups, int32_t cluster,
                                  int32_t* clusters) {
   gs::g_err.clear();
@@ -861,6 +887,6 @@ void gs_release_workspace(void) {
   gs::g_ws.clear();
 }
 
-int32_t gs_version(void) { return 101; }
+int32_t gs_version(void) { return 102; }
 
 }  // extern "C"

@@ -35,11 +35,15 @@ struct GraphKey {
   int timed = 0;  // records the workspace's phase events
   int integ = 0;  // GS_EULER or GS_RK4
   int h_end = 0;  // the loss takes the kinetic term at t = 1
+  int dim = 3;    // 3-D or planar landmarks
   bool operator<(const GraphKey& o) const {
-    return std::tie(kind, n, T, sigma, lambda, ckpt, timed, integ, h_end) <
-           std::tie(o.kind, o.n, o.T, o.sigma, o.lambda, o.ckpt, o.timed, o.integ, o.h_end);
+    return std::tie(kind, n, T, sigma, lambda, ckpt, timed, integ, h_end, dim) <
+           std::tie(o.kind, o.n, o.T, o.sigma, o.lambda, o.ckpt, o.timed, o.integ, o.h_end, o.dim);
   }
 };
+
+// Dimension of the landmarks of a call (gs_params.dim: 2, or 3 / 0 for 3-D).
+inline int dim_of(const gs_params& p) { return p.dim == 2 ? 2 : 3; }
 
 // Pair-sum evaluations (stages) per time step of an integrator.
 inline int stages_of(int integ) { return integ == GS_RK4 ? 4 : 1; }
@@ -89,7 +93,8 @@ struct Workspace {
   float *out_a = nullptr, *out_b = nullptr;
   double *red_h = nullptr, *red_m = nullptr, *scalars = nullptr;
   unsigned *ticket = nullptr, *status = nullptr;
-  // The trajectory and adjoint records hold zero padding for this N.
+  // The trajectory and adjoint records hold zero padding for this N and
+  // dimension (key 4 N + dim; -1: unknown).
   int clean_n = -1;
   cudaStream_t capture_stream = nullptr;
   std::map<GraphKey, cudaGraphExec_t> graphs;
@@ -128,7 +133,7 @@ gs_status get_workspace(Workspace** out);
 // Room for npad landmarks, record slots 0..T, the split partials and nck
 // FP64 state checkpoints.
 gs_status reserve(Workspace& w, int npad, int T, int splits, int nck = 0);
-gs_status ensure_clean(Workspace& w, int n, cudaStream_t st);
+gs_status ensure_clean(Workspace& w, int n, cudaStream_t st, int dim = 3);
 bool is_device_ptr(const void* p);
 gs_status stage_in(const float* src, float* staging, size_t n3, cudaStream_t st, const float** dev, bool* host);
 gs_status copy_out(float* dst, const float* src, size_t n3, cudaStream_t st, bool* host);

@@ -66,13 +66,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
 }
 
 // Programmatic dependent launch: wait for the preceding kernel's results.
-// A no-op when launched without PDL.  The kernels never trigger their
-// dependents early (griddepcontrol.launch_dependents): on GB300 an early
-// trigger let the next step's clusters take SM slots while the current step
-// ran, and made chains of 8-CTA-cluster steps up to 47% slower.  The
-// implicit trigger when a grid finishes still overlaps the next launch's
-// set-up with the end of the current one.
+// A no-op when launched without PDL.  No kernel triggers its dependents at
+// its start: on GB300 that let the next step's clusters take SM slots while
+// the current step ran, and made chains of 8-CTA-cluster steps up to 47%
+// slower.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Let the next kernel in the stream launch once every CTA of this grid has
+// issued this (or exited).  Its griddepcontrol.wait still waits for this
+// grid to complete and flush, so the trigger moves only the next launch's
+// set-up, never the data dependence.  The step kernels issue it late, after
+// their pair sums, when the host asks for it (one-wave grids).
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // 2^x on the MUFU unit (flushes subnormal results to zero).
 __device__ __forceinline__ float ex2_approx(float x) {

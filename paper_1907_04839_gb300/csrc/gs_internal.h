@@ -142,6 +142,9 @@ struct StepFwdArgs {
                        // the adjoint initialisation; no state update
   double adj_scale;    // factor of the adjoint record written at the loss
                        // (terminal launch, or the last RK4 stage): dt/6 for RK4, 1 for Euler
+  int dim;             // 2: planar landmarks (records of 2 float4, (N,2) FP64
+                       // arrays); 0 or 3: 3-D
+  int late_trigger;    // trigger the next launch after the pair sums (pdl_trigger)
 };
 
 struct StepBwdArgs {
@@ -169,6 +172,8 @@ struct StepBwdArgs {
   double* ya64;        // RK4: FP64 adjoint of the step's start state, summed over the stages
   double* yb64;
   int h_at_end;        // the loss takes H at t = 1: no H(p0, q0) term in the gradient
+  int dim;             // 2: planar landmarks; 0 or 3: 3-D
+  int late_trigger;    // trigger the next launch after the pair sums (pdl_trigger)
 };
 
 // Packed batches of independent problems.  Problem b occupies landmarks
@@ -202,6 +207,12 @@ bool set_step_override(int kind, int threads, int R, int groups, int cluster);
 // driver default, 1 spread, 2 load balancing), or -1: each configuration's
 // own policy.
 void set_cluster_policy(int policy);
+// When step kernels trigger the next launch after their pair sums: -1 the
+// library's rule (reverse-step grids resident in one wave), 0 never, 1 always.
+void set_late_trigger(int mode);
+// Whether a single-problem step launch of configuration c (kind 0 forward,
+// 1 reverse) triggers the next launch after its pair sums.
+bool late_trigger_for(int kind, const StepConfig& c);
 // The policy for a launch of `ctas` CTAs on `num_sms` SMs: load balancing
 // when the grid is at least 1.5 waves of 8 CTAs per SM, else spread.
 int policy_for_grid(long long ctas, int num_sms);
@@ -229,6 +240,7 @@ struct PackArgs {
   int n;
   double kq;
   unsigned* status;
+  int dim;             // 2: planar landmarks ((N,2) arrays); 0 or 3: 3-D
 };
 
 struct UnpackArgs {
@@ -242,7 +254,7 @@ cudaError_t launch_unpack(const UnpackArgs& a, cudaStream_t st);
 // Restore an FP64 state checkpoint into q64, p64 and record slot 0 of rec,
 // with the same rounding as the step kernels' epilogue.
 cudaError_t launch_restore(const double* ckq, const double* ckp, double* q64, double* p64, float4* rec, int n,
-                           double kq, cudaStream_t st);
+                           double kq, cudaStream_t st, int dim = 3);
 // Hq, Hp straight from one split-partial set (step_forward entry point).
 cudaError_t launch_partials_to_out(const Partial* part, int splits, int n, int npad,
                                    float* out_a, float* out_b, cudaStream_t st);

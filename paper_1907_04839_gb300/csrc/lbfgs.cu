@@ -113,15 +113,20 @@ __global__ void __launch_bounds__(kLT) k_f64_to_f32(float* y, const double* x, i
 }
 
 // Landmark distances |q1_i - t_i| (Section 3.1): out[0] = sum, out[1] = max.
-__global__ void __launch_bounds__(kLT) k_dist(const double* q1, const double* t, int n, double* part,
+// Landmarks in dim = 2 or 3 dimensions.
+__global__ void __launch_bounds__(kLT) k_dist(const double* q1, const double* t, int n, int dim, double* part,
                                              unsigned* ticket, double* out) {
   __shared__ double sh[kLT / 32];
   __shared__ double shm[kLT / 32];
   __shared__ int am_last;
   double sum = 0.0, mx = 0.0;
   for (int i = blockIdx.x * kLT + threadIdx.x; i < n; i += gridDim.x * kLT) {
-    const double dx = q1[3 * i] - t[3 * i], dy = q1[3 * i + 1] - t[3 * i + 1], dz = q1[3 * i + 2] - t[3 * i + 2];
-    const double r = sqrt(dx * dx + dy * dy + dz * dz);
+    double r2 = 0.0;
+    for (int k = 0; k < dim; ++k) {
+      const double d = q1[dim * i + k] - t[dim * i + k];
+      r2 += d * d;
+    }
+    const double r = sqrt(r2);
     sum += r;
     mx = fmax(mx, r);
   }
@@ -202,7 +207,7 @@ struct Lbfgs {
   int evals = 0;
 
   Lbfgs(Workspace& w_, const gs_params& p, cudaStream_t s, const float* q, const float* t)
-      : w(w_), prm(p), st(s), dq(q), dt(t), n3(static_cast<int>(3 * p.N)), m(p.lbfgs_m),
+      : w(w_), prm(p), st(s), dq(q), dt(t), n3(static_cast<int>(dim_of(p) * p.N)), m(p.lbfgs_m),
         grid(vec_grid(n3, w_.num_sms)) {}
 
   gs_status dots(int count, const double* const* a, const double* const* b, const double* mult, double* host) {
@@ -432,7 +437,7 @@ gs_status run_register(const gs_params* prm, const float* q0, const float* targe
   std::lock_guard<std::mutex> lk(engine_mutex());
   Workspace* w = nullptr;
   if ((s = get_workspace(&w)) != GS_OK) return s;
-  const int n = static_cast<int>(prm->N), npad = round_up(n, kPad), n3 = 3 * n;
+  const int n = static_cast<int>(prm->N), npad = round_up(n, kPad), n3 = dim_of(*prm) * n;
   const int ckpt = effective_ckpt(prm->ckpt_every, prm->T);
   const int S = stages_of(prm->integrator);
   if ((s = reserve(*w, npad, std::max(S * prm->T, record_slots(prm->T, ckpt, S)), 1,
@@ -456,7 +461,8 @@ gs_status run_register(const gs_params* prm, const float* q0, const float* targe
   if ((s = copy_out(p0_inout, w->out_a, n3, st, &dummy)) != GS_OK) return s;
   if (info) {
     if ((s = enqueue_forward64(*w, *prm, dq, w->lb.x, st)) != GS_OK) return s;
-    GS_CUDA(vlaunch(grid, st, k_dist, (const double*)w->q64, (const double*)w->t64, n, w->lb.part, w->lb.ticket,
+    GS_CUDA(vlaunch(grid, st, k_dist, (const double*)w->q64, (const double*)w->t64, n, dim_of(*prm), w->lb.part,
+                    w->lb.ticket,
                     w->lb.scal + kDots));
     double dist[2] = {0.0, 0.0};
     GS_CUDA(cudaMemcpyAsync(dist, w->lb.scal + kDots, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));

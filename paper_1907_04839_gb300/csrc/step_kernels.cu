@@ -20,8 +20,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <map>
 #include <mutex>
 #include <set>
+#include <utility>
 
 #include "pair_tile.cuh"
 
@@ -75,12 +77,12 @@ struct StepView {
 // Add the W warp groups' partials of every target into group 0's slot, in
 // group order, in double-single arithmetic (each float4 holds two (hi, lo)
 // values).  Each item is read and written by one thread only.
-template <int W, int M>
-__device__ __forceinline__ void combine_groups(float4 (&red)[W][M][3]) {
+template <int W, int M, int D>
+__device__ __forceinline__ void combine_groups(float4 (&red)[W][M][D]) {
   if constexpr (W > 1) {
     __syncthreads();
-    for (int item = threadIdx.x; item < M * 3; item += blockDim.x) {
-      const int lt = item / 3, k = item % 3;
+    for (int item = threadIdx.x; item < M * D; item += blockDim.x) {
+      const int lt = item / D, k = item % D;
       float4 acc = red[0][lt][k];
 #pragma unroll
       for (int g = 1; g < W; ++g) {
@@ -94,39 +96,42 @@ __device__ __forceinline__ void combine_groups(float4 (&red)[W][M][3]) {
   }
 }
 
-// Send one target's six double-single partials (three float4) to the CTA
-// of the cluster that reduces that target.  CTA `owner` reduces targets
+// Send one target's 2D double-single partials (D float4) to the CTA of the
+// cluster that reduces that target.  CTA `owner` reduces targets
 // [owner*slice, (owner+1)*slice) of the tile; the partials of local target
 // lt from source split `rank` land in the owner's
-// recv[(rank*slice + lt - owner*slice)*3 + 0..2].  The stores are remote
+// recv[(rank*slice + lt - owner*slice)*D + 0..D-1].  The stores are remote
 // (distributed shared memory) and need no reply; the cluster barrier that
 // follows makes them visible to the owner.
-__device__ __forceinline__ void push_partials(float4* recv, int lt, unsigned rank, int slice, float4 a, float4 b,
-                                              float4 c) {
+template <int D>
+__device__ __forceinline__ void push_partials(float4* recv, int lt, unsigned rank, int slice, const float4 (&x)[D]) {
   const int owner = lt / slice;
   const int lo = lt - owner * slice;
-  const uint32_t addr = dsmem_addr(smem_u32(&recv[(static_cast<int>(rank) * slice + lo) * 3]), owner);
-  st_dsmem_f4(addr, a);
-  st_dsmem_f4(addr + 16u, b);
-  st_dsmem_f4(addr + 32u, c);
+  const uint32_t addr = dsmem_addr(smem_u32(&recv[(static_cast<int>(rank) * slice + lo) * D]), owner);
+#pragma unroll
+  for (int f = 0; f < D; ++f) st_dsmem_f4(addr + 16u * f, x[f]);
+}
+
+// The 2D double-single values w[] of one target packed as D float4.
+template <int D>
+__device__ __forceinline__ void pack_ds(const ds (&w)[2 * D], float4 (&x)[D]) {
+#pragma unroll
+  for (int f = 0; f < D; ++f) x[f] = make_float4(w[2 * f].hi, w[2 * f].lo, w[2 * f + 1].hi, w[2 * f + 1].lo);
 }
 
 // W > 1: the warp groups' partials of every target of the tile, added in
 // shared memory in group order into red[0].  Ends with a CTA barrier.
-template <int NT, int R, int W, int M, class Tile, class Res>
-__device__ __forceinline__ void combine_tile(float4 (&red)[W][M][3], const Tile& t, Res result, int lt0, int grp) {
+template <int NT, int R, int W, int M, int D, class Tile, class Res>
+__device__ __forceinline__ void combine_tile(float4 (&red)[W][M][D], const Tile& t, Res result, int lt0, int grp) {
   if constexpr (W > 1) {
     constexpr int TG = NT / W;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      ds w[6];
+      ds w[2 * D];
       result(t, r, w);
-      const int lt = lt0 + r * TG;
-      red[grp][lt][0] = make_float4(w[0].hi, w[0].lo, w[1].hi, w[1].lo);
-      red[grp][lt][1] = make_float4(w[2].hi, w[2].lo, w[3].hi, w[3].lo);
-      red[grp][lt][2] = make_float4(w[4].hi, w[4].lo, w[5].hi, w[5].lo);
+      pack_ds<D>(w, red[grp][lt0 + r * TG]);
     }
-    combine_groups<W, M>(red);
+    combine_groups<W, M, D>(red);
     __syncthreads();
   }
 }
@@ -134,39 +139,40 @@ __device__ __forceinline__ void combine_tile(float4 (&red)[W][M][3], const Tile&
 // Push the tile's partials to their reducing CTAs: W = 1 straight from each
 // thread's registers, W > 1 from red[0] (after combine_tile).  The caller
 // makes sure every receiving CTA is ready (a cluster barrier wait first).
-template <int NT, int R, int W, int M, class Tile, class Res>
-__device__ __forceinline__ void push_tile(const float4 (&red)[W][M][3], float4* recv, const Tile& t, Res result,
+template <int NT, int R, int W, int M, int D, class Tile, class Res>
+__device__ __forceinline__ void push_tile(const float4 (&red)[W][M][D], float4* recv, const Tile& t, Res result,
                                           int lt0, unsigned rank, int slice) {
   if constexpr (W == 1) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      ds w[6];
+      ds w[2 * D];
       result(t, r, w);
-      push_partials(recv, lt0 + r * NT, rank, slice, make_float4(w[0].hi, w[0].lo, w[1].hi, w[1].lo),
-                    make_float4(w[2].hi, w[2].lo, w[3].hi, w[3].lo), make_float4(w[4].hi, w[4].lo, w[5].hi, w[5].lo));
+      float4 x[D];
+      pack_ds<D>(w, x);
+      push_partials<D>(recv, lt0 + r * NT, rank, slice, x);
     }
   } else {
-    for (int lt = threadIdx.x; lt < M; lt += NT) push_partials(recv, lt, rank, slice, red[0][lt][0], red[0][lt][1],
-                                                               red[0][lt][2]);
+    for (int lt = threadIdx.x; lt < M; lt += NT) push_partials<D>(recv, lt, rank, slice, red[0][lt]);
   }
 }
 
 // Forward step of one tile: pair sums, cluster reduction, Euler update.
 // Accumulates this thread's H0 and mismatch contributions in hc, mc.
-// V: the variants (RK4 stages, the terminal launch) are compiled in.
-template <int NT, int R, int W, bool V>
+// V: the variants (RK4 stages, the terminal launch) are compiled in.  D: the
+// dimension of the landmarks (3, or 2 for planar landmarks).
+template <int NT, int R, int W, bool V, int D>
 __device__ __forceinline__ void forward_body(const StepFwdArgs& a, const StepView& v, double& hc, double& mc) {
   constexpr int TG = NT / W;  // threads per warp group
   constexpr int M = TG * R;   // targets of the CTA
   static_assert(NT % W == 0 && TG % 32 == 0, "warp groups must be whole warps");
   union Smem {
-    StageBuf<1> st;
-    float4 red[W][M][3];  // per group: Hp (hi,lo) x3 then Hq (hi,lo) x3 per target
+    StageBuf<1, D> st;
+    float4 red[W][M][D];  // per group: Hp (hi,lo) x D then Hq (hi,lo) x D per target
   };
   __shared__ __align__(128) Smem sm;
   // Partials of this CTA's slice of targets from every source split:
-  // [C][M/C][3] float4, the same six double-single values per target.
-  __shared__ __align__(16) float4 recv[M * 3];
+  // [C][M/C][D] float4, the same 2D double-single values per target.
+  __shared__ __align__(16) float4 recv[M * D];
   __shared__ __align__(8) Pipe pp;
 
   const unsigned rank = cluster_rank(), C = cluster_size();
@@ -190,31 +196,32 @@ __device__ __forceinline__ void forward_body(const StepFwdArgs& a, const StepVie
   const int tile0 = v.off + v.tile * M;
   const int grp = W == 1 ? 0 : static_cast<int>(threadIdx.x) / TG;
   const int lt0 = W == 1 ? static_cast<int>(threadIdx.x) : static_cast<int>(threadIdx.x) % TG;
-  FwdTile<R> t;
+  FwdTile<R, D> t;
   t.load(a.qp, tile0 + lt0, TG, lim);
   const float4* src[1] = {a.qp};
-  stream_sources<1, W>(sm.st, pp, src, j0, j1, t, a.status, grp);  // ends with a CTA barrier
+  stream_sources<1, W, D>(sm.st, pp, src, j0, j1, t, a.status, grp);  // ends with a CTA barrier
   const int slice = M / static_cast<int>(C);
-  const auto res = [&](const FwdTile<R>& tt, int r, ds* w) { tt.result(r, v.kappa_f, w); };
-  combine_tile<NT, R, W, M>(sm.red, t, res, lt0, grp);
+  const auto res = [&](const FwdTile<R, D>& tt, int r, ds* w) { tt.result(r, v.kappa_f, w); };
+  combine_tile<NT, R, W, M, D>(sm.red, t, res, lt0, grp);
   // recv is memory of its own, so a CTA may push as soon as every peer has
   // started (the arrival at kernel entry): one cluster barrier per step.
   cluster_wait();
-  push_tile<NT, R, W, M>(sm.red, recv, t, res, lt0, rank, slice);
+  push_tile<NT, R, W, M, D>(sm.red, recv, t, res, lt0, rank, slice);
   cluster_sync();  // every split's partials have reached the CTA that reduces them
+  if (a.late_trigger) pdl_trigger();  // only the epilogue is left
 
-  for (int item = threadIdx.x; item < slice * 3; item += NT) {
-    const int ll = item / 3;
+  for (int item = threadIdx.x; item < slice * D; item += NT) {
+    const int ll = item / D;
     const int lt = static_cast<int>(rank) * slice + ll;
-    const int k = item % 3;
+    const int k = item % D;
     if (v.tile * M + lt >= v.n) continue;
     const int i = tile0 + lt;  // packed landmark index
     ds hp{0.f, 0.f}, hq{0.f, 0.f};
 #pragma unroll 4
     for (unsigned rr = 0; rr < C; ++rr) {
-      const float2* rp = reinterpret_cast<const float2*>(&recv[(static_cast<int>(rr) * slice + ll) * 3]);
+      const float2* rp = reinterpret_cast<const float2*>(&recv[(static_cast<int>(rr) * slice + ll) * D]);
       const float2 x = rp[k];
-      const float2 y = rp[3 + k];
+      const float2 y = rp[D + k];
       hp = ds_add(hp, ds{x.x, x.y});
       hq = ds_add(hq, ds{y.x, y.y});
     }
@@ -222,10 +229,10 @@ __device__ __forceinline__ void forward_body(const StepFwdArgs& a, const StepVie
       hc += ds_to_double(hp) + ds_to_double(hq);
       continue;
     }
-    const int tt = 3 * i + k;
+    const int tt = D * i + k;
     const double Hp = ds_to_double(hp), Hq = ds_to_double(hq);
     const double q_old = a.q64[tt], p_old = a.p64[tt];
-    float* an = reinterpret_cast<float*>(a.ab + (i >> 1) * kRecF4) + 2 * k + (i & 1);
+    float* an = reinterpret_cast<float*>(a.ab + (i >> 1) * D) + 2 * k + (i & 1);
     if (V && a.terminal) {
       // The end state (q(1), p(1)): its kinetic term, the mismatch, and the
       // adjoint alpha = dL/dq(1) = 2 lambda r + Hq, beta = dL/dp(1) = Hp.
@@ -237,7 +244,7 @@ __device__ __forceinline__ void forward_body(const StepFwdArgs& a, const StepVie
       a.a64[tt] = al;
       a.b64[tt] = be;
       an[0] = (float)(a.adj_scale * al);
-      an[6] = -(float)(v.kappa * a.adj_scale * be);
+      an[2 * D] = -(float)(v.kappa * a.adj_scale * be);
       continue;
     }
     if (a.first) {
@@ -276,9 +283,9 @@ __device__ __forceinline__ void forward_body(const StepFwdArgs& a, const StepVie
       a.p64[tt] = p;
     }
     if (!isfinite(q) || !isfinite(p)) atomicOr(a.status, kErrNonFinite);
-    float* qn = reinterpret_cast<float*>(a.qp_next + (i >> 1) * kRecF4) + 2 * k + (i & 1);
+    float* qn = reinterpret_cast<float*>(a.qp_next + (i >> 1) * D) + 2 * k + (i & 1);
     qn[0] = -(float)(v.kq * q);
-    qn[6] = (float)p;
+    qn[2 * D] = (float)p;
     if (a.last && a.with_loss) {
       const double r = q - a.t64[tt];
       mc += r * r;
@@ -286,7 +293,7 @@ __device__ __forceinline__ void forward_body(const StepFwdArgs& a, const StepVie
       a.a64[tt] = al;
       a.b64[tt] = 0.0;
       an[0] = (float)((V && a.rk ? a.adj_scale : 1.0) * al);
-      an[6] = 0.f;
+      an[2 * D] = 0.f;
     }
   }
   // No trailing cluster barrier: every remote access of the step happened
@@ -295,14 +302,15 @@ __device__ __forceinline__ void forward_body(const StepFwdArgs& a, const StepVie
 
 // Reverse step of one tile: adjoint pair sums, cluster reduction, adjoint
 // update, and at time step 0 the gradient.  V: the RK4 stages are compiled in.
-template <int NT, int R, int W, bool V>
+// D: the dimension of the landmarks.
+template <int NT, int R, int W, bool V, int D>
 __device__ __forceinline__ void backward_body(const StepBwdArgs& a, const StepView& v) {
   constexpr int TG = NT / W;  // threads per warp group
   constexpr int M = TG * R;   // targets of the CTA
   static_assert(NT % W == 0 && TG % 32 == 0, "warp groups must be whole warps");
   union Smem {
-    StageBuf<2> st;
-    float4 red[W][M][3];  // per group: dalpha (hi,lo) x3 then dbeta (hi,lo) x3 per target
+    StageBuf<2, D> st;
+    float4 red[W][M][D];  // per group: dalpha (hi,lo) x D then dbeta (hi,lo) x D per target
   };
   __shared__ __align__(128) Smem sm;
   __shared__ __align__(8) Pipe pp;
@@ -327,31 +335,29 @@ __device__ __forceinline__ void backward_body(const StepBwdArgs& a, const StepVi
   const int tile0 = v.off + v.tile * M;
   const int grp = W == 1 ? 0 : static_cast<int>(threadIdx.x) / TG;
   const int lt0 = W == 1 ? static_cast<int>(threadIdx.x) : static_cast<int>(threadIdx.x) % TG;
-  BwdTile<R> t;
+  BwdTile<R, D> t;
   t.load(a.qp, a.ab, tile0 + lt0, TG, lim);
   const float4* src[2] = {a.qp, a.ab};
-  stream_sources<2, W>(sm.st, pp, src, j0, j1, t, a.status, grp);
+  stream_sources<2, W, D>(sm.st, pp, src, j0, j1, t, a.status, grp);
   // The reverse kernel pulls: each CTA leaves its partials in its own idle
   // stage ring and the reducing CTA loads them through distributed shared
   // memory.  (Pushing them, as the forward kernel does, measured 3-5 %
   // slower for this kernel on GB300 at 4096 to 65536 landmarks.)
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    ds w[6];
+    ds w[2 * D];
     t.result(r, v.kq_f, v.kappa_f, w);
-    const int lt = lt0 + r * TG;
-    sm.red[grp][lt][0] = make_float4(w[0].hi, w[0].lo, w[1].hi, w[1].lo);
-    sm.red[grp][lt][1] = make_float4(w[2].hi, w[2].lo, w[3].hi, w[3].lo);
-    sm.red[grp][lt][2] = make_float4(w[4].hi, w[4].lo, w[5].hi, w[5].lo);
+    pack_ds<D>(w, sm.red[grp][lt0 + r * TG]);
   }
-  combine_groups<W, M>(sm.red);
+  combine_groups<W, M, D>(sm.red);
   cluster_sync();  // every CTA's tile partials are visible to the cluster
+  if (a.late_trigger) pdl_trigger();  // only the reduction and the epilogue are left
   const int slice = M / static_cast<int>(C);
 
-  for (int item = threadIdx.x; item < slice * 3; item += NT) {
-    const int ll = item / 3;
+  for (int item = threadIdx.x; item < slice * D; item += NT) {
+    const int ll = item / D;
     const int lt = static_cast<int>(rank) * slice + ll;
-    const int k = item % 3;
+    const int k = item % D;
     if (v.tile * M + lt >= v.n) continue;
     const int i = tile0 + lt;
     const uint32_t lp = smem_u32(&sm.red[0][lt][0]);
@@ -360,7 +366,7 @@ __device__ __forceinline__ void backward_body(const StepBwdArgs& a, const StepVi
     for (unsigned rr = 0; rr < C; ++rr) {
       const uint32_t rp = dsmem_addr(lp, rr);
       const float2 x = ld_dsmem_f2(rp + 8u * k);
-      const float2 y = ld_dsmem_f2(rp + 24u + 8u * k);
+      const float2 y = ld_dsmem_f2(rp + 8u * D + 8u * k);
       da = ds_add(da, ds{x.x, x.y});
       db = ds_add(db, ds{y.x, y.y});
     }
@@ -368,8 +374,8 @@ __device__ __forceinline__ void backward_body(const StepBwdArgs& a, const StepVi
       if (!isfinite(da.hi + db.hi)) atomicOr(a.status, kErrNonFinite);
       continue;
     }
-    const int tt = 3 * i + k;
-    float* an = reinterpret_cast<float*>(a.ab_next + (i >> 1) * kRecF4) + 2 * k + (i & 1);
+    const int tt = D * i + k;
+    float* an = reinterpret_cast<float*>(a.ab_next + (i >> 1) * D) + 2 * k + (i & 1);
     double al, be;  // the adjoint of the step's start state, once complete
     if (V && a.rk) {
       // Reverse of RK4 stage s: v = J(Y_s)^T kbar_s came out of the pair sums.
@@ -388,7 +394,7 @@ __device__ __forceinline__ void backward_body(const StepBwdArgs& a, const StepVi
         const double cw = (a.stage == 1 ? 1.0 / 6.0 : 1.0 / 3.0) * v.dt;
         const double cv = (a.stage == 3 ? 1.0 : 0.5) * v.dt;
         an[0] = (float)(cw * wa + cv * va);
-        an[6] = -(float)(v.kappa * (cw * wb + cv * vb));
+        an[2 * D] = -(float)(v.kappa * (cw * wb + cv * vb));
         continue;
       }
       al = ya;
@@ -396,7 +402,7 @@ __device__ __forceinline__ void backward_body(const StepBwdArgs& a, const StepVi
       a.a64[tt] = al;
       a.b64[tt] = be;
       an[0] = (float)(v.dt / 6.0 * al);  // stage 4 adjoint of the previous step
-      an[6] = -(float)(v.kappa * (v.dt / 6.0 * be));
+      an[2 * D] = -(float)(v.kappa * (v.dt / 6.0 * be));
     } else {
       al = a.a64[tt] + v.dt * ds_to_double(da);
       be = a.b64[tt] + v.dt * ds_to_double(db);
@@ -404,7 +410,7 @@ __device__ __forceinline__ void backward_body(const StepBwdArgs& a, const StepVi
       a.a64[tt] = al;
       a.b64[tt] = be;
       an[0] = (float)al;
-      an[6] = -(float)(v.kappa * be);
+      an[2 * D] = -(float)(v.kappa * be);
     }
     if (a.first) {
       const double gp = be + (a.h_at_end ? 0.0 : a.hp0[tt]);
@@ -421,7 +427,7 @@ __device__ __forceinline__ void backward_body(const StepBwdArgs& a, const StepVi
 // kinetic term at t = 0), true with the variants compiled in (RK4 stages, the
 // terminal launch).  Keeping them apart leaves the plain kernels' register
 // allocation as the pair loop needs it.
-template <int NT, int R, int W, bool V>
+template <int NT, int R, int W, bool V, int D = 3>
 __global__ void __launch_bounds__(NT) k_step_forward(StepFwdArgs a) {
   __shared__ double shred[NT / 32];
   __shared__ int am_last;
@@ -438,7 +444,7 @@ __global__ void __launch_bounds__(NT) k_step_forward(StepFwdArgs a) {
   v.dt = a.dt;
   v.lambda = a.lambda;
   double hc = 0.0, mc = 0.0;
-  forward_body<NT, R, W, V>(a, v, hc, mc);
+  forward_body<NT, R, W, V, D>(a, v, hc, mc);
   const bool reduce_h = a.first || a.terminal;
   const bool reduce_m = a.last && a.with_loss;
   if ((!reduce_h && !reduce_m) || a.dry) return;  // uniform across the grid
@@ -455,7 +461,7 @@ __global__ void __launch_bounds__(NT) k_step_forward(StepFwdArgs a) {
   }
 }
 
-template <int NT, int R, int W, bool V>
+template <int NT, int R, int W, bool V, int D = 3>
 __global__ void __launch_bounds__(NT) k_step_backward(StepBwdArgs a) {
   StepView v;
   v.off = 0;
@@ -469,7 +475,7 @@ __global__ void __launch_bounds__(NT) k_step_backward(StepBwdArgs a) {
   v.kappa = a.kappa64;
   v.dt = a.dt;
   v.lambda = 0.0;
-  backward_body<NT, R, W, V>(a, v);
+  backward_body<NT, R, W, V, D>(a, v);
 }
 
 // ---------------------------------------------------------------- packed batch kernels
@@ -499,7 +505,7 @@ __global__ void __launch_bounds__(NT) k_bstep_forward(StepFwdArgs a, BatchTables
   __shared__ double shred[NT / 32];
   const StepView v = batch_view(bt);
   double hc = 0.0, mc = 0.0;
-  forward_body<NT, R, W, false>(a, v, hc, mc);
+  forward_body<NT, R, W, false, 3>(a, v, hc, mc);
   const bool reduce_h = a.first != 0;
   const bool reduce_m = a.last && a.with_loss;
   if ((!reduce_h && !reduce_m) || a.dry) return;
@@ -514,7 +520,7 @@ __global__ void __launch_bounds__(NT) k_bstep_forward(StepFwdArgs a, BatchTables
 
 template <int NT, int R, int W>
 __global__ void __launch_bounds__(NT) k_bstep_backward(StepBwdArgs a, BatchTables bt) {
-  backward_body<NT, R, W, false>(a, batch_view(bt));
+  backward_body<NT, R, W, false, 3>(a, batch_view(bt));
 }
 
 // ---------------------------------------------------------------- host side
@@ -633,6 +639,38 @@ int g_override[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};  // threads, R, cluster, gr
 
 void set_cluster_policy(int policy) { g_cluster_policy = policy; }
 
+namespace {
+int g_late_trigger = -1;
+std::mutex g_res_mu;
+std::map<std::pair<int, int>, int> g_resident;  // configuration -> resident CTAs of the plain kernel
+}  // namespace
+
+void set_late_trigger(int mode) { g_late_trigger = mode; }
+
+bool late_trigger_for(int kind, const StepConfig& c) {
+  if (g_late_trigger >= 0) return g_late_trigger == 1;
+  // The library's rule, from GB300 measurements of gradient graphs
+  // (N = 2048..16384): reverse steps whose CTAs are all resident at once
+  // trigger (-1.7% reverse-sweep time at N = 4096); forward steps never
+  // (+13% forward-sweep time at N = 4096 with the trigger).
+  if (kind != 1) return false;
+  const auto key = std::make_pair(kind * 100000 + c.threads * 100 + c.R, c.cluster * 16 + c.groups);
+  int resident = -1;
+  {
+    std::lock_guard<std::mutex> lk(g_res_mu);
+    const auto it = g_resident.find(key);
+    if (it != g_resident.end()) resident = it->second;
+  }
+  if (resident < 0) {
+    int clusters = 0;
+    if (max_active_clusters(kind, c.threads, c.R, c.groups, c.cluster, &clusters) != cudaSuccess) clusters = 0;
+    resident = clusters * c.cluster;
+    std::lock_guard<std::mutex> lk(g_res_mu);
+    g_resident[key] = resident;
+  }
+  return static_cast<long long>(c.tiles) * c.cluster <= resident;
+}
+
 int policy_for_grid(long long ctas, int num_sms) { return 2 * ctas >= 3LL * 8 * num_sms ? 2 : 1; }
 
 cudaError_t max_active_clusters(int kind, int threads, int R, int groups, int cluster, int* out) {
@@ -726,6 +764,11 @@ cudaError_t launch_bstep_backward(const StepConfig& c, int items, const StepBwdA
 // Launches of the variants (RK4 stages, the terminal launch) go to the
 // V = true instantiation of the built-in configuration's kernel variant.
 cudaError_t launch_step_forward(const StepConfig& c, const StepFwdArgs& a, cudaStream_t st, bool pdl) {
+  if (a.dim == 2) {  // planar landmarks: the built-in configuration only
+    if (c.threads != kVarFwdThreads || c.R != 1 || c.groups != 1) return cudaErrorNotSupported;
+    if (a.rk || a.terminal) return launch_cluster(k_step_forward<kVarFwdThreads, 1, 1, true, 2>, c, a, st, pdl);
+    return launch_cluster(k_step_forward<kVarFwdThreads, 1, 1, false, 2>, c, a, st, pdl);
+  }
   if (a.rk || a.terminal) {
     if (c.threads == kVarFwdThreads && c.R == 1 && c.groups == 1)
       return launch_cluster(k_step_forward<kVarFwdThreads, 1, 1, true>, c, a, st, pdl);
@@ -740,6 +783,11 @@ cudaError_t launch_step_forward(const StepConfig& c, const StepFwdArgs& a, cudaS
 }
 
 cudaError_t launch_step_backward(const StepConfig& c, const StepBwdArgs& a, cudaStream_t st, bool pdl) {
+  if (a.dim == 2) {
+    if (c.threads != kVarBwdThreads || c.R != 1 || c.groups != 1) return cudaErrorNotSupported;
+    if (a.rk) return launch_cluster(k_step_backward<kVarBwdThreads, 1, 1, true, 2>, c, a, st, pdl);
+    return launch_cluster(k_step_backward<kVarBwdThreads, 1, 1, false, 2>, c, a, st, pdl);
+  }
   if (a.rk) {
     if (c.threads == kVarBwdThreads && c.R == 1 && c.groups == 1)
       return launch_cluster(k_step_backward<kVarBwdThreads, 1, 1, true>, c, a, st, pdl);

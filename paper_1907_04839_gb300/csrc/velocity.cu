@@ -288,6 +288,7 @@ extern "C" gs_status flow_points(const gs_params* prm, const float* q0, const fl
   if (s != GS_OK) return s;
   if (!q0 || !p0) return fail(GS_EINVAL, "q0 and p0 must not be NULL");
   if (prm->integrator != GS_EULER) return fail(GS_EINVAL, "flow_points takes Euler steps only (integrator GS_EULER)");
+  if (dim_of(*prm) != 3) return fail(GS_EINVAL, "flow_points is 3-D only (dim 3)");
   if ((s = check_points(M, x0, x1)) != GS_OK) return s;
   std::lock_guard<std::mutex> lk(engine_mutex());
   Workspace* w = nullptr;
@@ -318,6 +319,7 @@ extern "C" gs_status flow_points(const gs_params* prm, const float* q0, const fl
   pk.n = n;
   pk.kq = sc.kq;
   pk.status = w->status;
+  pk.dim = 3;
   GS_CUDA(launch_pack(pk, st));
   cudaGraphExec_t ge = nullptr;
   if ((s = get_graph(*w, GraphKey{0, n, T, prm->sigma, 0.0, 0, w->phase_timing}, &ge)) != GS_OK) return s;

@@ -25,3 +25,10 @@ def test_ellipsoid_pair_is_seeded_and_on_the_surface_before_jitter():
     assert np.array_equal(p.q0, q.q0) and np.array_equal(p.target, q.target)
     r = (p.q0[:, 0] / 1.0) ** 2 + (p.q0[:, 1] / 0.8) ** 2 + (p.q0[:, 2] / 0.6) ** 2
     assert np.allclose(r, 1.0, atol=1e-12)
+
+
+def test_ellipse_pair_is_seeded_planar_and_on_the_curve_before_jitter():
+    p = ls.ellipse_pair(1500, seed=4, n_bumps=4, jitter=0.0)
+    q = ls.ellipse_pair(1500, seed=4, n_bumps=4, jitter=0.0)
+    assert p.q0.shape == (1500, 2) and np.array_equal(p.q0, q.q0) and np.array_equal(p.target, q.target)
+    assert np.allclose((p.q0[:, 0] / 1.0) ** 2 + (p.q0[:, 1] / 0.6) ** 2, 1.0, atol=1e-12)

@@ -334,12 +334,15 @@ def measure_batched(gsh, count, max_iter=100, T=T_STEPS):
     }
 
 
-def measure_served(gsh, count, max_iter=200, budget=120 << 30, rate=200.0, T=T_STEPS):
+def measure_served(gsh, count, max_iter=200, budget=120 << 30, rate=200.0, T=T_STEPS, schedule="fair"):
     """A Poisson trace through the continuous-batching server.  Requests are
     submitted at their arrival times while the server runs rounds; latency is
-    from arrival to the round that finished the request."""
+    from arrival to the round that finished the request.  schedule: the
+    server's round schedule ("fair": equal pair work per request; "all":
+    every resident request in every round)."""
     trace = served_trace(count, rate)
-    sv = gsh.Server(T=T, max_iter=max_iter, grad_tol=1e-5, memory_budget=budget, max_problems=1024)
+    sv = gsh.Server(T=T, max_iter=max_iter, grad_tol=1e-5, memory_budget=budget, max_problems=1024,
+                    schedule=schedule)
     rid = [None] * count
     done_at = [None] * count
     service = [None] * count
@@ -375,7 +378,8 @@ def measure_served(gsh, count, max_iter=200, budget=120 << 30, rate=200.0, T=T_S
     makespan = max(done_at) - trace[0]["t_arrival"]
     ns = [r["q0"].shape[0] for r in trace]
     return {
-        "requests": count, "arrival_rate_per_s": rate, "T": T, "max_iter": max_iter, "grad_tol": 1e-5,
+        "requests": count, "schedule": schedule, "arrival_rate_per_s": rate, "T": T, "max_iter": max_iter,
+        "grad_tol": 1e-5,
         "memory_budget_bytes": budget, "N": "log-uniform [1000, 50000], mean %.0f" % float(np.mean(ns)),
         "regs_per_s": count / makespan, "makespan_s": makespan,
         "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
@@ -577,6 +581,7 @@ def run_workload(args, dist):
         value, ms = res["packed_regs_per_s"], res["packed_s"] * 1e3
     else:
         res = measure_served(gsh, args.served_count or 64)
+        res["schedule_all"] = measure_served(gsh, args.served_count or 64, schedule="all")
         metric = "served registrations/s (Poisson 200/s, N~LogU[1000,50000], T=20)"
         value, ms = res["regs_per_s"], res["makespan_s"] * 1e3
     line = {"metric": metric, "value": value * dist.world, "unit": "regs/s", "n_gpus": dist.world, "steps": 1,

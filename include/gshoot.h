@@ -251,7 +251,21 @@ typedef struct gs_server_config {
     double grad_tol;        /* stop at ||g|| <= grad_tol ||g0|| */
     uint64_t memory_budget; /* device bytes the server may allocate (admission limit) */
     void* stream;           /* cudaStream_t for all of the server's work */
+    int32_t schedule;       /* GS_SCHED_ALL (0): every resident request is evaluated in
+                               every round; GS_SCHED_FAIR (1): fair shares of pair work,
+                               so small requests advance more rounds than large ones */
+    int32_t reserved;       /* set to 0 */
 } gs_server_config;
+
+/* Round schedules of the server (gs_server_config.schedule).  Under
+ * GS_SCHED_FAIR each resident request carries a virtual time, the pair work
+ * (N^2 per evaluation) it has been charged; a round evaluates the requests
+ * whose virtual time is below the smallest one plus the smallest request's
+ * cost, and a request starts at the smallest virtual time present when it is
+ * admitted.  Every request then receives the same pair work per unit time,
+ * and a small request finishes after its own work instead of the largest
+ * request's.  A request's iterates do not depend on the schedule. */
+enum { GS_SCHED_ALL = 0, GS_SCHED_FAIR = 1 };
 
 typedef struct gs_server gs_server;
 
@@ -264,10 +278,11 @@ gs_status gs_server_submit(gs_server* sv, int64_t N, double sigma, double lambda
                            const float* q0, const float* target, const float* p0,
                            int64_t* request_id);
 
-/* One round: admit queued requests while memory allows, evaluate every
- * active request once, advance their L-BFGS, retire finished ones, admit
- * again.  Out (each may be NULL): requests resident, requests queued,
- * requests finished in this round. */
+/* One round: admit queued requests while memory allows, evaluate the
+ * resident requests the schedule selects once each (all of them under
+ * GS_SCHED_ALL), advance their L-BFGS, retire finished ones, admit again.
+ * Out (each may be NULL): requests resident, requests queued, requests
+ * finished in this round. */
 gs_status gs_server_step(gs_server* sv, int32_t* active, int32_t* queued, int32_t* completed);
 
 /* Result of a request.  *done = 0 while it is queued or running.  When done:
@@ -420,7 +435,7 @@ const char* gs_last_error(void);
 void gs_release_workspace(void);
 
 /* Library ABI version: 100 * major + minor (101: gs_params gained
- * integrator and kinetic_at; 102: dim). */
+ * integrator and kinetic_at; 102: dim; 103: gs_server_config.schedule). */
 int32_t gs_version(void);
 
 #ifdef __cplusplus

@@ -291,15 +291,21 @@ class Server:
     """Continuous-batching registration server (gs_server_* in the C ABI).
 
     submit() queues a request; step() runs one round (admission by memory
-    budget, one evaluation of every resident request, retirement); poll()
-    returns (p0, info, latency) of a finished request or None."""
+    budget, one evaluation of each request the schedule selects, retirement);
+    poll() returns (p0, info, latency) of a finished request or None.
+    schedule "fair" (the default) shares pair work equally among resident
+    requests, so small ones finish sooner; "all" evaluates every resident
+    request in every round."""
 
     def __init__(self, T, m=10, max_iter=100, grad_tol=1e-5, memory_budget=8 << 30, max_problems=1024,
-                 stream=None):
+                 stream=None, schedule="fair"):
+        if schedule not in ("all", "fair"):
+            raise ValueError("schedule must be 'all' or 'fair'")
         self._lib = load()
         cfg = GsServerConfig(T=int(T), lbfgs_m=int(m), max_iter=int(max_iter), max_problems=int(max_problems),
                              grad_tol=float(grad_tol), memory_budget=int(memory_budget),
-                             stream=ctypes.c_void_p(stream or 0))
+                             stream=ctypes.c_void_p(stream or 0), schedule=1 if schedule == "fair" else 0,
+                             reserved=0)
         self._h = ctypes.c_void_p(0)
         check(self._lib.gs_server_create(ctypes.byref(cfg), ctypes.byref(self._h)))
         self._n = {}

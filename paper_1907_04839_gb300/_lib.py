@@ -98,6 +98,8 @@ class GsServerConfig(ctypes.Structure):
         ("grad_tol", ctypes.c_double),
         ("memory_budget", ctypes.c_uint64),
         ("stream", ctypes.c_void_p),
+        ("schedule", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 

@@ -250,6 +250,8 @@ struct Problem {
   double f_acc = 0.0;
   // serving timestamps (seconds on the server clock)
   double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
+  // fair schedule: pair work charged so far (N^2 per evaluation)
+  double vtime = 0.0;
   gs_register_info result{};
   std::vector<float> p0_result;
 };
@@ -324,6 +326,7 @@ struct BatchEngine {
   int device = 0, num_sms = 0;
   int T = 20, m = 10, max_iter = 100;
   double grad_tol = 1e-5;
+  int schedule = GS_SCHED_ALL;
   StepConfig fcfg{}, bcfg{};
   int cap = 0;            // landmark capacity (multiple of kPad)
   int max_probs = 0;
@@ -466,8 +469,13 @@ struct BatchEngine {
     if (off < 0) return -1;
     const int sl = free_slots.back();
     free_slots.pop_back();
+    // A newcomer starts at the smallest virtual time present (fair schedule).
+    double vnow = -1.0;
+    for (const Problem& o : slots)
+      if (o.off >= 0 && o.phase != kDone && (vnow < 0.0 || o.vtime < vnow)) vnow = o.vtime;
     Problem& p = slots[sl];
     p = proto;
+    p.vtime = vnow < 0.0 ? 0.0 : vnow;
     p.npad = npad;
     p.off = off;
     p.phase = kInit;
@@ -690,15 +698,29 @@ struct BatchEngine {
     return GS_OK;
   }
 
-  // One round over all active problems (see the file comment).  Returns the
-  // slots that finished in this round in *done.
+  // One round over the active problems the schedule selects (all of them,
+  // or under the fair schedule those behind in charged pair work; see the
+  // file comment).  Returns the slots that finished in this round in *done.
   gs_status round(std::vector<int>* done) {
     done->insert(done->end(), rejected.begin(), rejected.end());
     rejected.clear();
     std::vector<int> active, need_dir;
+    double vmin = 0.0, cmin = 0.0;
+    bool first = true;
+    for (int sl = 0; sl < max_probs; ++sl) {
+      const Problem& p = slots[sl];
+      if (p.off < 0 || p.phase == kDone) continue;
+      const double c = static_cast<double>(p.n) * p.n;
+      if (first || p.vtime < vmin) vmin = p.vtime;
+      if (first || c < cmin) cmin = c;
+      first = false;
+    }
     for (int sl = 0; sl < max_probs; ++sl) {
       Problem& p = slots[sl];
       if (p.off < 0 || p.phase == kDone) continue;
+      // Fair schedule: the requests that are behind in charged pair work.
+      if (schedule == GS_SCHED_FAIR && !(p.vtime < vmin + cmin)) continue;
+      p.vtime += static_cast<double>(p.n) * p.n;
       active.push_back(sl);
       if (p.phase == kNeedDir) need_dir.push_back(sl);
     }
@@ -931,7 +953,12 @@ gs_status gs_server_create(const gs_server_config* cfg, gs_server** out) {
     gs::set_last_error("bad server configuration");
     return GS_EINVAL;
   }
+  if (cfg->schedule != GS_SCHED_ALL && cfg->schedule != GS_SCHED_FAIR) {
+    gs::set_last_error("schedule must be GS_SCHED_ALL or GS_SCHED_FAIR");
+    return GS_EINVAL;
+  }
   gs_server* sv = new gs_server();
+  sv->eng.schedule = cfg->schedule;
   gs_status s = sv->eng.init(cfg->T, cfg->lbfgs_m, cfg->max_iter, cfg->grad_tol, cfg->memory_budget,
                              cfg->max_problems, static_cast<cudaStream_t>(cfg->stream));
   if (s != GS_OK) {

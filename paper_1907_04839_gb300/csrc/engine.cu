@@ -887,6 +887,6 @@ void gs_release_workspace(void) {
   gs::g_ws.clear();
 }
 
-int32_t gs_version(void) { return 102; }
+int32_t gs_version(void) { return 103; }
 
 }  // extern "C"

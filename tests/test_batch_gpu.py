@@ -125,3 +125,39 @@ def test_server_reports_a_nonfinite_request_and_serves_the_rest():
         p0, info, _ = sv.poll(ids[k])
         assert np.array_equal(p0, ref[k][0]) and info["loss"] == ref[k][1]["loss"]
     sv.close()
+
+
+def test_server_fair_schedule_finishes_small_requests_first_with_the_same_results():
+    # One large request and three small ones.  Under the fair schedule the
+    # small ones take more rounds per unit time and finish first; every
+    # request's result is bitwise the one of the all-in-every-round schedule.
+    big = problems(1, seed0=90, n_lo=3000, n_hi=3000)[0]
+    small = problems(3, seed0=91, n_lo=300, n_hi=300)
+    reqs = [big] + small
+    finished_at = {}
+    results = {}
+    for sched in ("all", "fair"):
+        sv = gs().Server(T=4, max_iter=12, grad_tol=0.0, memory_budget=256 << 20, max_problems=8, schedule=sched)
+        ids = [sv.submit(p["q0"], p["target"], p["sigma"], p["lam"]) for p in reqs]
+        rounds, fin = 0, {}
+        while len(fin) < len(ids) and rounds < 2000:
+            sv.step()
+            rounds += 1
+            for k, rid in enumerate(ids):
+                if k not in fin:
+                    out = sv.poll(rid)
+                    if out is not None:
+                        fin[k] = rounds
+                        results[(sched, k)] = out
+        sv.close()
+        assert len(fin) == len(ids)
+        finished_at[sched] = fin
+        print(sched, "finished at round", fin)
+    for k in range(len(reqs)):
+        a, b = results[("all", k)], results[("fair", k)]
+        assert np.array_equal(a[0], b[0]) and a[1]["loss"] == b[1]["loss"] and a[1]["evals"] == b[1]["evals"]
+    fair, allr = finished_at["fair"], finished_at["all"]
+    # all-rounds: everyone finishes within its own evaluation count of rounds
+    assert all(allr[k] == results[("all", k)][1]["evals"] for k in range(len(reqs)))
+    # fair: the small requests finish before the large one
+    assert max(fair[k] for k in (1, 2, 3)) < fair[0]

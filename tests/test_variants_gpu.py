@@ -133,3 +133,15 @@ def test_flow_points_rejects_rk4():
         gs().check(lib.flow_points(ctypes.byref(prm), ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(dev(p0).data_ptr()),
                                    50, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), None))
     assert ei.value.status == -1
+
+
+def test_rk4_kinetic_end_gradient_at_16384_landmarks():
+    # Full-size check of the variant kernels in the launch configuration of
+    # large problems (several waves, load-balancing cluster scheduling).
+    q0, p0, t = problem(16384, 23, pscale=0.01)
+    loss, gp, gq = gs().shoot_gradient(dev(q0), dev(p0), dev(t), 2, 0.05, 10.0, integrator="rk4", h_at="end")
+    r = oracle.shoot_gradient_v(q0, p0, t, 2, 0.05, 10.0, "rk4", "end")
+    el, ep, eq = abs(loss - r["loss"]) / abs(r["loss"]), rel(gp.cpu().numpy(), r["grad_p0"]), rel(gq.cpu().numpy(),
+                                                                                                     r["grad_q0"])
+    print("rk4/end N=16384: loss %.2e grad_p0 %.2e grad_q0 %.2e" % (el, ep, eq))
+    assert el < 1e-5 and ep < 1e-4 and eq < 1e-4

@@ -5,7 +5,8 @@
 //   v(x, t) = sum_l g(|q_l(t) - x|) p_l(t).
 // Its pair sums are the Hp half of StepForward with query points as
 // targets, so the kernel is built the same way: a cluster of C CTAs owns a
-// tile of 128 query points, CTA r streams source split r of the landmark
+// tile of 256 query points (two per thread, so that each staged landmark
+// record feeds two points), CTA r streams source split r of the landmark
 // pair records through the shared-memory stage ring, and the C partial sums
 // of each point meet in distributed shared memory in rank order.  One
 // launch either writes v (velocity_field) or moves the points by one Euler
@@ -24,25 +25,28 @@
 namespace gs {
 namespace {
 
-constexpr int kVT = 128;  // query points per CTA, one per thread
+constexpr int kVT = 128;  // threads per CTA
+constexpr int kVR = 2;    // query points per thread: a staged landmark record feeds kVR points
 
 // Per query point x:  V = sum_j g(x, q_j) p_j  over the landmark pair
-// records (negated prescaled positions, momenta).
+// records (negated prescaled positions, momenta).  A thread holds R points
+// (base + r * stride).
+template <int R>
 struct VelTile {
-  float2 qx, qy, qz;  // prescaled point, duplicated for the paired lanes
-  float sF[3], cF[3];
+  float2 q[R][3];  // prescaled points, duplicated for the paired lanes
+  float sF[R][3], cF[R][3];
 
-  __device__ __forceinline__ void load(const double* x64, int i, int m, double kq) {
-    float v[3] = {0.f, 0.f, 0.f};
-    if (i < m) {
+  __device__ __forceinline__ void load(const double* x64, int base, int stride, int m, double kq) {
 #pragma unroll
-      for (int k = 0; k < 3; ++k) v[k] = static_cast<float>(kq * x64[3 * static_cast<size_t>(i) + k]);
+    for (int r = 0; r < R; ++r) {
+      const int i = base + r * stride;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float v = i < m ? static_cast<float>(kq * x64[3 * static_cast<size_t>(i) + k]) : 0.f;
+        q[r][k] = dup(v);
+        sF[r][k] = cF[r][k] = 0.f;
+      }
     }
-    qx = dup(v[0]);
-    qy = dup(v[1]);
-    qz = dup(v[2]);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) sF[k] = cF[k] = 0.f;
   }
 
   // Sources [lo, hi) of the staged chunk; lo is a multiple of 8.
@@ -50,26 +54,35 @@ struct VelTile {
     const float4* Q = bufs[0];
     for (int sb = lo; sb < hi; sb += kSub) {
       const int sl = min(kSub, hi - sb);
-      float2 a[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+      float2 a[R][3];
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) a[r][k] = make_float2(0.f, 0.f);
       for (int jj = 0; jj < sl; jj += kUnroll) {
 #pragma unroll
         for (int u = 0; u < kUnroll / 2; ++u) {
-          const float4* rec = Q + ((sb + jj) / 2 + u) * kRecF4;
-          const float4 A = rec[0], B = rec[1], C = rec[2];
-          const float2 dx = __fadd2_rn(qx, lo2(A));
-          const float2 dy = __fadd2_rn(qy, hi2(A));
-          const float2 dz = __fadd2_rn(qz, lo2(B));
-          float2 r2 = __fmul2_rn(dx, dx);
-          r2 = __ffma2_rn(dy, dy, r2);
-          r2 = __ffma2_rn(dz, dz, r2);
-          const float2 g = gauss2(r2);
-          a[0] = __ffma2_rn(g, hi2(B), a[0]);
-          a[1] = __ffma2_rn(g, lo2(C), a[1]);
-          a[2] = __ffma2_rn(g, hi2(C), a[2]);
+          float2 v[6];  // v[k] = -q~_j, v[3 + k] = p_j
+          rec_split<3>(Q + ((sb + jj) / 2 + u) * kRecF4, v);
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const float2 dx = __fadd2_rn(q[r][0], v[0]);
+            const float2 dy = __fadd2_rn(q[r][1], v[1]);
+            const float2 dz = __fadd2_rn(q[r][2], v[2]);
+            float2 r2 = __fmul2_rn(dx, dx);
+            r2 = __ffma2_rn(dy, dy, r2);
+            r2 = __ffma2_rn(dz, dz, r2);
+            const float2 g = gauss2(r2);
+            a[r][0] = __ffma2_rn(g, v[3], a[r][0]);
+            a[r][1] = __ffma2_rn(g, v[4], a[r][1]);
+            a[r][2] = __ffma2_rn(g, v[5], a[r][2]);
+          }
         }
       }
 #pragma unroll
-      for (int k = 0; k < 3; ++k) kahan_add(sF[k], cF[k], __fadd_rn(a[k].x, a[k].y));
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) kahan_add(sF[r][k], cF[r][k], __fadd_rn(a[r][k].x, a[r][k].y));
     }
   }
 };
@@ -83,17 +96,19 @@ struct VelArgs {
   unsigned* status;
 };
 
+constexpr int kVM = kVT * kVR;  // query points per CTA
+
 __global__ void __launch_bounds__(kVT) k_velocity(VelArgs a) {
   union Smem {
     StageBuf<1> st;
-    float4 red[kVT][2];  // (V0 hi, lo, V1 hi, lo), (V2 hi, lo, -, -) per point
+    float4 red[kVM][2];  // (V0 hi, lo, V1 hi, lo), (V2 hi, lo, -, -) per point
   };
   __shared__ __align__(128) Smem sm;
   __shared__ __align__(8) Pipe pp;
 
   const unsigned rank = cluster_rank(), C = cluster_size();
   // Same outcome in every CTA of a cluster: a bad launch leaves before any barrier.
-  if (blockDim.x != kVT || kVT % static_cast<int>(C) != 0 || (a.split_len & 7) != 0 ||
+  if (blockDim.x != kVT || kVM % static_cast<int>(C) != 0 || (a.split_len & 7) != 0 ||
       static_cast<long long>(a.split_len) * C < a.npad) {
     if (threadIdx.x == 0) atomicOr(a.status, kErrBadLaunch);
     return;
@@ -104,19 +119,23 @@ __global__ void __launch_bounds__(kVT) k_velocity(VelArgs a) {
   __syncthreads();
   pdl_wait();  // the previous step's points must be complete
 
-  const int tile0 = blockIdx.y * kVT;
-  VelTile t;
-  t.load(a.x64, tile0 + static_cast<int>(threadIdx.x), a.m, a.kq);
+  const int tile0 = blockIdx.y * kVM;
+  VelTile<kVR> t;
+  t.load(a.x64, tile0 + static_cast<int>(threadIdx.x), kVT, a.m, a.kq);
   const float4* src[1] = {a.qp};
   stream_sources<1>(sm.st, pp, src, j0, j1, t, a.status);  // ends with a CTA barrier
-  const ds f0 = ds_from_kahan(t.sF[0], t.cF[0]);
-  const ds f1 = ds_from_kahan(t.sF[1], t.cF[1]);
-  const ds f2 = ds_from_kahan(t.sF[2], t.cF[2]);
-  sm.red[threadIdx.x][0] = make_float4(f0.hi, f0.lo, f1.hi, f1.lo);
-  sm.red[threadIdx.x][1] = make_float4(f2.hi, f2.lo, 0.f, 0.f);
+#pragma unroll
+  for (int r = 0; r < kVR; ++r) {
+    const ds f0 = ds_from_kahan(t.sF[r][0], t.cF[r][0]);
+    const ds f1 = ds_from_kahan(t.sF[r][1], t.cF[r][1]);
+    const ds f2 = ds_from_kahan(t.sF[r][2], t.cF[r][2]);
+    const int lt = static_cast<int>(threadIdx.x) + r * kVT;
+    sm.red[lt][0] = make_float4(f0.hi, f0.lo, f1.hi, f1.lo);
+    sm.red[lt][1] = make_float4(f2.hi, f2.lo, 0.f, 0.f);
+  }
   cluster_sync();  // every CTA's partials are visible to the cluster
 
-  const int slice = kVT / static_cast<int>(C);
+  const int slice = kVM / static_cast<int>(C);
   for (int item = threadIdx.x; item < slice * 3; item += kVT) {
     const int lt = static_cast<int>(rank) * slice + item / 3;
     const int k = item % 3;
@@ -166,7 +185,7 @@ struct VelConfig {
 
 VelConfig vel_config(int m, int npad, int num_sms) {
   VelConfig c{};
-  c.tiles = (m + kVT - 1) / kVT;
+  c.tiles = (m + kVM - 1) / kVM;
   const int want = (2 * num_sms + c.tiles - 1) / c.tiles;
   const int cap = std::max(1, std::min(16, npad / 128));
   c.cluster = 1;

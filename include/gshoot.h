@@ -9,6 +9,8 @@
  * T explicit Euler steps of dt = 1/T (Algorithm 1), loss
  * L(p0) = H(p0, q0) + lambda ||q(1) - target||^2 (Eq. 3), its gradient by the
  * exact reverse sweep of those Euler steps, and L-BFGS over p0 (Section 2.1).
+ * Variants selected in gs_params: RK4 steps with their exact adjoint, the
+ * kinetic term at t = 1 (Algorithm 1's pseudocode), and planar landmarks.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -33,7 +35,8 @@
  *   a positive status is a warning with valid outputs.
  * Device errors.  Kernels record non-finite inputs and expired waits in a
  *   device status word instead of faulting; the synchronous path reads it and
- *   returns GS_ENONFINITE or GS_ETIMEOUT.
+ *   returns GS_ENONFINITE or GS_ETIMEOUT.  Every device-side wait gives up
+ *   after one second (gs_check_wait_timeout exercises that path).
  */
 #ifndef GSHOOT_H
 #define GSHOOT_H
@@ -427,6 +430,19 @@ gs_status gs_set_late_trigger(int32_t mode);
  */
 gs_status gs_set_phase_timing(int32_t on);
 gs_status gs_phase_times(double* fwd_ms, double* bwd_ms);
+
+/*
+ * gs_check_wait_timeout — failure detection (no counterpart in the paper):
+ * runs one device wait that nothing completes, with the library's own
+ * iteration limit, and reports how it ended.  which 0: an mbarrier phase
+ * (the wait of the kernels' bulk-copy stage ring); 1: a flag in device
+ * memory (a bounded poll loop).  The wait gives up, sets the timeout bit of
+ * the device status word and returns; the call returns GS_ETIMEOUT, and the
+ * context stays usable for the next call.  *seconds (may be NULL) receives
+ * the wall time of the call.  Synchronises `stream`.  GS_EINVAL for another
+ * `which`.
+ */
+gs_status gs_check_wait_timeout(int32_t which, double* seconds, void* stream);
 
 /* Message for the last error of the calling thread ("" if none). */
 const char* gs_last_error(void);

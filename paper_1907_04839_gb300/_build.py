@@ -20,7 +20,7 @@ LIB = os.path.join(PKG, "libgshoot.so")
 HEADER = os.path.join(ROOT, "include", "gshoot.h")
 
 SOURCES = ["pair_kernels.cu", "step_kernels.cu", "combine.cu", "engine.cu", "lbfgs.cu", "batch.cu", "noalloc.cu",
-           "velocity.cu"]
+           "velocity.cu", "diag.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
 

@@ -11,10 +11,22 @@
 
 namespace gs {
 
-// Iteration limit of every spin on an mbarrier phase.  One try_wait may
-// suspend the thread for a while, so this bounds a wait well below a second
-// for copies that normally complete in a few microseconds.
-constexpr long kSpinLimit = 1L << 22;
+// Bound of every spin on an mbarrier phase.  An unanswered try_wait
+// suspends the thread for a while before it returns false (measured on
+// GB300: 4,194,304 of them took 15.7 s, 3.75 us each), so 2^18 polls bound a
+// wait at about one second; the copies and releases waited for take
+// microseconds.  A time check inside the poll loop measured 6-11% slower
+// gradients (it weighs on the register allocation of the pair loops).
+constexpr long kSpinLimit = 1L << 18;
+// Bound of the global-memory poll of the wait check (diag.cu), in global
+// time.
+constexpr unsigned long long kWaitNs = 1000000000ull;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));

@@ -642,7 +642,7 @@ void set_cluster_policy(int policy) { g_cluster_policy = policy; }
 namespace {
 int g_late_trigger = -1;
 std::mutex g_res_mu;
-std::map<std::pair<int, int>, int> g_resident;  // configuration -> resident CTAs of the plain kernel
+std::map<std::pair<int, int>, int> g_resident;  // (device, configuration) -> resident CTAs of the plain kernel
 }  // namespace
 
 void set_late_trigger(int mode) { g_late_trigger = mode; }
@@ -654,7 +654,9 @@ bool late_trigger_for(int kind, const StepConfig& c) {
   // trigger (-1.7% reverse-sweep time at N = 4096); forward steps never
   // (+13% forward-sweep time at N = 4096 with the trigger).
   if (kind != 1) return false;
-  const auto key = std::make_pair(kind * 100000 + c.threads * 100 + c.R, c.cluster * 16 + c.groups);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+  const auto key = std::make_pair(dev * 1000000 + kind * 100000 + c.threads * 100 + c.R, c.cluster * 16 + c.groups);
   int resident = -1;
   {
     std::lock_guard<std::mutex> lk(g_res_mu);

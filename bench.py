@@ -347,6 +347,7 @@ def measure_served(gsh, count, max_iter=200, budget=120 << 30, rate=200.0, T=T_S
     done_at = [None] * count
     service = [None] * count
     evals = [0] * count
+    infos = [None] * count
     t0 = time.perf_counter()
     nsub = 0
     outstanding = set()
@@ -371,6 +372,7 @@ def measure_served(gsh, count, max_iter=200, budget=120 << 30, rate=200.0, T=T_S
                     done_at[k] = tw
                     service[k] = out[2][1]
                     evals[k] = out[1]["evals"]
+                    infos[k] = out[1]
                     outstanding.discard(k)
     sv.close()
     lat = np.array([done_at[k] - trace[k]["t_arrival"] for k in range(count)])
@@ -386,6 +388,11 @@ def measure_served(gsh, count, max_iter=200, budget=120 << 30, rate=200.0, T=T_S
         "service_p50_s": float(np.percentile(svc, 50)), "service_p99_s": float(np.percentile(svc, 99)),
         "pair_interactions_per_s": sum(2 * T * n * n * e for n, e in zip(ns, evals)) / makespan,
         "timing": "wall clock from arrival to result, host inputs, queueing included",
+        "per_request": [{"N": ns[k], "iters": infos[k]["iters"], "evals": infos[k]["evals"],
+                         "status": infos[k]["status"], "loss": infos[k]["loss"],
+                         "avg_dist": infos[k]["avg_dist"], "max_dist": infos[k]["max_dist"],
+                         "latency_s": float(lat[k]), "service_s": float(svc[k]),
+                         "queue_s": float(lat[k] - svc[k])} for k in range(count)],
     }
 
 

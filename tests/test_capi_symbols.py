@@ -80,3 +80,38 @@ def test_invalid_variant_is_rejected_before_device_work():
         st = lib.shoot_gradient(ctypes.byref(prm), P(q), P(q), P(q), None, P(q), P(q), None)
         assert st == -1, (integ, kin, st)
         assert b"integrator" in lib.gs_last_error() or b"kinetic_at" in lib.gs_last_error()
+
+
+def test_invalid_dimension_and_server_schedule_are_rejected():
+    import numpy as np
+    import paper_1907_04839_gb300 as gsh
+    lib = gsh.load()
+    q = np.zeros((4, 3), np.float32)
+    P = lambda a: ctypes.c_void_p(a.ctypes.data)
+    for dim in (1, 4, -3):
+        prm = gsh.GsParams(N=4, T=2, ckpt_every=0, sigma=0.1, lambda_=1.0, lbfgs_m=10, max_iter=1, grad_tol=0.0,
+                           integrator=0, kinetic_at=0, dim=dim, reserved=0)
+        assert lib.shoot_forward(ctypes.byref(prm), P(q), P(q), P(q), P(q), None, None) == -1
+        assert b"dim" in lib.gs_last_error()
+    cfg = gsh.GsServerConfig(T=4, lbfgs_m=10, max_iter=1, max_problems=1, grad_tol=0.0, memory_budget=1 << 20,
+                             stream=None, schedule=7, reserved=0)
+    h = ctypes.c_void_p(0)
+    assert lib.gs_server_create(ctypes.byref(cfg), ctypes.byref(h)) == -1
+    assert b"schedule" in lib.gs_last_error()
+    with pytest.raises(ValueError):
+        gsh.Server(T=4, schedule="sometimes")
+
+
+def test_server_config_layout_matches_header(tmp_path):
+    import paper_1907_04839_gb300 as gsh
+    fields = [f[0] for f in gsh.GsServerConfig._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"gshoot.h\"\nint main(void) {\n"
+                   + '  printf("%zu\\n", sizeof(gs_server_config));\n'
+                   + "".join('  printf("%%zu\\n", offsetof(gs_server_config, %s));\n' % f for f in fields)
+                   + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(gsh.GsServerConfig)
+    assert out[1:] == [getattr(gsh.GsServerConfig, f).offset for f in fields]

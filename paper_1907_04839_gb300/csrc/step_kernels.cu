@@ -529,10 +529,10 @@ namespace {
 
 // Compiled variants: (threads per CTA, targets per thread, warp groups).
 #define GS_STEP_FWD_CASES(X)                                                                         \
-  X(64, 2, 1) X(64, 4, 1) X(128, 1, 1) X(128, 2, 1) X(128, 4, 1) X(256, 1, 1) X(256, 2, 1) X(64, 1, 2) \
-  X(128, 1, 2) X(128, 1, 4) X(256, 1, 4)
+  X(64, 1, 1) X(64, 2, 1) X(64, 4, 1) X(128, 1, 1) X(128, 2, 1) X(128, 4, 1) X(256, 1, 1) X(256, 2, 1) \
+  X(64, 1, 2) X(128, 1, 2) X(128, 1, 4) X(256, 1, 4)
 #define GS_STEP_BWD_CASES(X) \
-  X(64, 1, 1) X(64, 2, 1) X(128, 1, 1) X(128, 2, 1) X(256, 1, 1) X(64, 1, 2) X(128, 1, 2) X(128, 1, 4) X(256, 1, 4)
+  X(32, 1, 1) X(64, 1, 1) X(64, 2, 1) X(128, 1, 1) X(128, 2, 1) X(256, 1, 1) X(64, 1, 2) X(128, 1, 2) X(128, 1, 4) X(256, 1, 4)
 
 std::mutex g_attr_mu;
 std::set<const void*> g_attr_done;  // kernels allowed clusters of up to 16 CTAs
@@ -714,13 +714,24 @@ StepConfig choose_step_config(int kind, int npad, int num_sms, bool variants) {
     if (c.threads) return c;
   }
   // Measured on GB300 (in-graph replay of the fused kernels, landmark
-  // counts 4096..65536): forward steps run fastest as 128-thread CTAs in
-  // clusters of 16, reverse steps as 64-thread CTAs in clusters of 8, one
-  // target per thread.  A grid of 1.5 waves or more (8 CTAs per SM) is
-  // scheduled with load balancing, which keeps every SM busy; a smaller grid
-  // is spread over the SMs.
-  const int threads = kind == 0 ? kVarFwdThreads : kVarBwdThreads;
-  const int cl = std::min(kind == 0 ? 16 : 8, std::max(1, npad / kUnroll));
+  // counts 1024..65536), one target per thread throughout:
+  //  * from 4096 landmarks up, forward steps run fastest as 128-thread CTAs
+  //    in clusters of 16 and reverse steps as 64-thread CTAs in clusters of 8;
+  //  * below, CTAs of half the threads spread the few targets over more SMs:
+  //    forward 64 threads, clusters of 16 (+13% at 1024 and 2048 landmarks);
+  //    reverse 32 threads, clusters of 16 up to 1024 landmarks (+18%) and of
+  //    8 up to 2048 (+6%).
+  // The variant kernels (RK4 stages, the terminal launch, planar landmarks)
+  // exist for the 128 / 64-thread CTAs only.  A grid of 1.5 waves or more
+  // (8 CTAs per SM) is scheduled with load balancing, which keeps every SM
+  // busy; a smaller grid is spread over the SMs.
+  int threads = kind == 0 ? kVarFwdThreads : kVarBwdThreads;
+  int cmax = kind == 0 ? 16 : 8;
+  if (!variants && npad <= 2048) {
+    threads /= 2;
+    if (kind == 1 && npad <= 1024) cmax = 16;
+  }
+  const int cl = std::min(cmax, std::max(1, npad / kUnroll));
   int c = 1;
   while (c * 2 <= cl) c *= 2;
   StepConfig cfg = step_config_for(kind, npad, threads, 1, c);

@@ -28,10 +28,10 @@ from . import _lib
 FWD = [(64, 2), (64, 4), (128, 2), (128, 4), (256, 1), (256, 2)]
 BWD = [(64, 1), (64, 2), (128, 1), (128, 2), (256, 1)]
 # fused variants: (threads per CTA, targets per thread, warp groups)
-STEP_FWD = [(64, 2, 1), (64, 4, 1), (128, 1, 1), (128, 2, 1), (128, 4, 1), (256, 1, 1), (256, 2, 1), (64, 1, 2),
-            (128, 1, 2), (128, 1, 4), (256, 1, 4)]
-STEP_BWD = [(64, 1, 1), (64, 2, 1), (128, 1, 1), (128, 2, 1), (256, 1, 1), (64, 1, 2), (128, 1, 2), (128, 1, 4),
-            (256, 1, 4)]
+STEP_FWD = [(64, 1, 1), (64, 2, 1), (64, 4, 1), (128, 1, 1), (128, 2, 1), (128, 4, 1), (256, 1, 1), (256, 2, 1),
+            (64, 1, 2), (128, 1, 2), (128, 1, 4), (256, 1, 4)]
+STEP_BWD = [(32, 1, 1), (64, 1, 1), (64, 2, 1), (128, 1, 1), (128, 2, 1), (256, 1, 1), (64, 1, 2), (128, 1, 2),
+            (128, 1, 4), (256, 1, 4)]
 CLUSTERS = [1, 2, 4, 8, 16]
 
 
@@ -45,8 +45,9 @@ def main():
                     help="cluster scheduling preferences to sweep (-1: the library's own choice)")
     ap.add_argument("--graph", action="store_true", help="time the fused kernels inside a CUDA graph")
     ap.add_argument("--clusters", type=int, nargs="+", default=CLUSTERS, help="cluster sizes of the fused sweep")
-    ap.add_argument("--variants", default="all", choices=["all", "default"],
-                    help="default: only the (threads, R) the library picks")
+    ap.add_argument("--variants", default="all", choices=["all", "default", "small"],
+                    help="default: only the (threads, R) the library picks; small: those and the one-target "
+                         "variants with half the threads")
     args = ap.parse_args()
     import torch
 
@@ -67,6 +68,8 @@ def main():
         sweeps = ((2, STEP_FWD), (3, STEP_BWD))
         if args.variants == "default":
             sweeps = ((2, [(128, 1, 1)]), (3, [(64, 1, 1)]))
+        elif args.variants == "small":
+            sweeps = ((2, [(64, 1, 1), (128, 1, 1)]), (3, [(32, 1, 1), (64, 1, 1)]))
         for pol in args.policy:
             _lib.check(lib.gs_set_cluster_policy(pol))
             for kind, variants in sweeps:

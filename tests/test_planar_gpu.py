@@ -117,3 +117,16 @@ def test_planar_equals_the_embedded_3d_problem():
     assert abs(l2 - l3) <= 1e-6 * l3
     assert rel(g2.cpu().numpy(), g3.cpu().numpy()[:, :2]) < 1e-6
     assert float(g3[:, 2].abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("integrator,h_at", [("euler", "start"), ("rk4", "end")])
+def test_planar_host_arrays_equal_device_arrays(integrator, h_at):
+    # numpy inputs are staged through the workspace; the results are bitwise
+    # those of device inputs.
+    q0, p0, t = problem(900, 17, 0.1)
+    ld, gpd, gqd = gs().shoot_gradient(dev(q0), dev(p0), dev(t), 5, 0.1, 10.0, integrator=integrator, h_at=h_at)
+    f = lambda a: np.asarray(a, np.float32)
+    lh, gph, gqh = gs().shoot_gradient(f(q0), f(p0), f(t), 5, 0.1, 10.0, integrator=integrator, h_at=h_at)
+    assert isinstance(gph, np.ndarray) and gph.shape == (900, 2)
+    assert lh == ld
+    assert np.array_equal(gph, gpd.cpu().numpy()) and np.array_equal(gqh, gqd.cpu().numpy())

@@ -312,7 +312,15 @@ __device__ __forceinline__ void backward_body(const StepBwdArgs& a, const StepVi
     StageBuf<2, D> st;
     float4 red[W][M][D];  // per group: dalpha (hi,lo) x D then dbeta (hi,lo) x D per target
   };
+  // CTAs of one warp push their partials into the reducing CTA's receive
+  // buffer, as the forward kernel does; larger CTAs leave them in their own
+  // idle stage ring for the reducing CTA to pull through distributed shared
+  // memory.  Measured on GB300 (in-graph replay, 2048 to 16384 landmarks):
+  // pushing is 1-4 % faster with 32-thread CTAs and 3-5 % slower with
+  // 64-thread CTAs.
+  constexpr bool kPush = NT == 32;
   __shared__ __align__(128) Smem sm;
+  __shared__ __align__(16) float4 recv[kPush ? M * D : 1];
   __shared__ __align__(8) Pipe pp;
 
   const unsigned rank = cluster_rank(), C = cluster_size();
@@ -325,6 +333,7 @@ __device__ __forceinline__ void backward_body(const StepBwdArgs& a, const StepVi
     if (threadIdx.x == 0) atomicOr(a.status, kErrBadLaunch);
     return;
   }
+  if constexpr (kPush) cluster_arrive_relaxed();  // waited on before the first remote store
   const int lim = v.off + v.npad;
   const int j0 = min(v.off + static_cast<int>(rank) * v.split_len, lim);
   const int j1 = min(j0 + v.split_len, lim);
@@ -339,20 +348,24 @@ __device__ __forceinline__ void backward_body(const StepBwdArgs& a, const StepVi
   t.load(a.qp, a.ab, tile0 + lt0, TG, lim);
   const float4* src[2] = {a.qp, a.ab};
   stream_sources<2, W, D>(sm.st, pp, src, j0, j1, t, a.status, grp);
-  // The reverse kernel pulls: each CTA leaves its partials in its own idle
-  // stage ring and the reducing CTA loads them through distributed shared
-  // memory.  (Pushing them, as the forward kernel does, measured 3-5 %
-  // slower for this kernel on GB300 at 4096 to 65536 landmarks.)
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    ds w[2 * D];
-    t.result(r, v.kq_f, v.kappa_f, w);
-    pack_ds<D>(w, sm.red[grp][lt0 + r * TG]);
-  }
-  combine_groups<W, M, D>(sm.red);
-  cluster_sync();  // every CTA's tile partials are visible to the cluster
-  if (a.late_trigger) pdl_trigger();  // only the reduction and the epilogue are left
   const int slice = M / static_cast<int>(C);
+  if constexpr (kPush) {
+    const auto res = [&](const BwdTile<R, D>& tt, int r, ds* w) { tt.result(r, v.kq_f, v.kappa_f, w); };
+    combine_tile<NT, R, W, M, D>(sm.red, t, res, lt0, grp);
+    cluster_wait();  // every peer's receive buffer exists
+    push_tile<NT, R, W, M, D>(sm.red, recv, t, res, lt0, rank, slice);
+    cluster_sync();  // every push has landed
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      ds w[2 * D];
+      t.result(r, v.kq_f, v.kappa_f, w);
+      pack_ds<D>(w, sm.red[grp][lt0 + r * TG]);
+    }
+    combine_groups<W, M, D>(sm.red);
+    cluster_sync();  // every CTA's tile partials are visible to the cluster
+  }
+  if (a.late_trigger) pdl_trigger();  // only the reduction and the epilogue are left
 
   for (int item = threadIdx.x; item < slice * D; item += NT) {
     const int ll = item / D;
@@ -360,15 +373,26 @@ __device__ __forceinline__ void backward_body(const StepBwdArgs& a, const StepVi
     const int k = item % D;
     if (v.tile * M + lt >= v.n) continue;
     const int i = tile0 + lt;
-    const uint32_t lp = smem_u32(&sm.red[0][lt][0]);
     ds da{0.f, 0.f}, db{0.f, 0.f};
+    if constexpr (kPush) {
 #pragma unroll 4
-    for (unsigned rr = 0; rr < C; ++rr) {
-      const uint32_t rp = dsmem_addr(lp, rr);
-      const float2 x = ld_dsmem_f2(rp + 8u * k);
-      const float2 y = ld_dsmem_f2(rp + 8u * D + 8u * k);
-      da = ds_add(da, ds{x.x, x.y});
-      db = ds_add(db, ds{y.x, y.y});
+      for (unsigned rr = 0; rr < C; ++rr) {
+        const float2* rp = reinterpret_cast<const float2*>(&recv[(static_cast<int>(rr) * slice + ll) * D]);
+        const float2 x = rp[k];
+        const float2 y = rp[D + k];
+        da = ds_add(da, ds{x.x, x.y});
+        db = ds_add(db, ds{y.x, y.y});
+      }
+    } else {
+      const uint32_t lp = smem_u32(&sm.red[0][lt][0]);
+#pragma unroll 4
+      for (unsigned rr = 0; rr < C; ++rr) {
+        const uint32_t rp = dsmem_addr(lp, rr);
+        const float2 x = ld_dsmem_f2(rp + 8u * k);
+        const float2 y = ld_dsmem_f2(rp + 8u * D + 8u * k);
+        da = ds_add(da, ds{x.x, x.y});
+        db = ds_add(db, ds{y.x, y.y});
+      }
     }
     if (a.dry) {
       if (!isfinite(da.hi + db.hi)) atomicOr(a.status, kErrNonFinite);
@@ -419,7 +443,7 @@ __device__ __forceinline__ void backward_body(const StepBwdArgs& a, const StepVi
       if (a.grad_q0) a.grad_q0[tt] = (float)(al + (a.h_at_end ? 0.0 : a.hq0[tt]));
     }
   }
-  cluster_sync();  // peers may still be reading this CTA's partials
+  if constexpr (!kPush) cluster_sync();  // peers may still be reading this CTA's partials
 }
 
 // ---------------------------------------------------------------- single-problem kernels

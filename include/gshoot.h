@@ -414,6 +414,20 @@ gs_status gs_max_active_clusters(int32_t kind, int32_t threads, int32_t R, int32
 gs_status gs_set_late_trigger(int32_t mode);
 
 /*
+ * gs_set_step_table — tuning (no counterpart in the paper): whether the
+ * fused time-step kernels take their CTA and cluster sizes from the table
+ * measured offline on this GPU model (one entry per padded landmark count
+ * up to 16384, coarser up to 65536; used only on a device with the table's
+ * SM count).  on = 1 (the initial state): the table; 0: the size rule the
+ * table refines (forward 128-thread CTAs in clusters of 16 and reverse
+ * 64-thread CTAs in clusters of 8, half-size CTAs up to 2048 landmarks).
+ * The cluster size sets how each target's sum is split, so the two choices
+ * can differ in the last bits of a result.  Clears the cached graphs.
+ * GS_EINVAL for another value.
+ */
+gs_status gs_set_step_table(int32_t on);
+
+/*
  * gs_set_phase_timing — diagnostics (no counterpart in the paper): when `on`
  * is nonzero, the CUDA graphs of shoot_forward / shoot_gradient (and of the
  * L-BFGS evaluations) on the current device record three events: before the
@@ -451,7 +465,8 @@ const char* gs_last_error(void);
 void gs_release_workspace(void);
 
 /* Library ABI version: 100 * major + minor (101: gs_params gained
- * integrator and kinetic_at; 102: dim; 103: gs_server_config.schedule). */
+ * integrator and kinetic_at; 102: dim; 103: gs_server_config.schedule;
+ * 104: gs_set_step_table). */
 int32_t gs_version(void);
 
 #ifdef __cplusplus

@@ -823,6 +823,15 @@ gs_status gs_set_late_trigger(int32_t mode) {
   return GS_OK;
 }
 
+gs_status gs_set_step_table(int32_t on) {
+  gs::g_err.clear();
+  if (on != 0 && on != 1) return gs::fail(GS_EINVAL, "on must be 0 or 1");
+  std::lock_guard<std::mutex> lk(gs::g_mu);
+  gs::set_step_table(on == 1);
+  for (auto& kv : gs::g_ws) kv.second->drop_graphs();
+  return GS_OK;
+}
+
 gs_status gs_max_active_clusters(int32_t kind, int32_t threads, int32_t R, int32_t groups, int32_t cluster,
                                  int32_t* clusters) {
   gs::g_err.clear();
@@ -887,6 +896,6 @@ void gs_release_workspace(void) {
   gs::g_ws.clear();
 }
 
-int32_t gs_version(void) { return 103; }
+int32_t gs_version(void) { return 104; }
 
 }  // extern "C"

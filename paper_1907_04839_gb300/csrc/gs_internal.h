@@ -210,6 +210,8 @@ void set_cluster_policy(int policy);
 // When step kernels trigger the next launch after their pair sums: -1 the
 // library's rule (reverse-step grids resident in one wave), 0 never, 1 always.
 void set_late_trigger(int mode);
+// Whether choose_step_config reads the measured step-configuration table.
+void set_step_table(bool on);
 // Whether a single-problem step launch of configuration c (kind 0 forward,
 // 1 reverse) triggers the next launch after its pair sums.
 bool late_trigger_for(int kind, const StepConfig& c);

@@ -729,6 +729,29 @@ bool set_step_override(int kind, int threads, int R, int groups, int cluster) {
   return true;
 }
 
+namespace {
+// One row of the measured step-configuration table: the padded landmark
+// count, then per kind (forward, reverse) the fastest CTA size and cluster
+// size, and the fastest cluster size for the full-size CTAs.
+struct StepRule {
+  int npad;
+  int fwd_threads, fwd_cluster, fwd_full_cluster;
+  int bwd_threads, bwd_cluster, bwd_full_cluster;
+};
+#include "step_table.inc"
+bool g_use_table = true;
+
+// The table row for npad: the first row at or above it (rows are ascending;
+// the last row serves every larger count).
+const StepRule& table_rule(int npad) {
+  const StepRule* end = kStepTable + sizeof(kStepTable) / sizeof(kStepTable[0]);
+  const StepRule* r = std::lower_bound(kStepTable, end, npad, [](const StepRule& e, int n) { return e.npad < n; });
+  return r == end ? end[-1] : *r;
+}
+}  // namespace
+
+void set_step_table(bool on) { g_use_table = on; }
+
 // Default configuration per problem size, from sweeps on GB300 (152 SMs).
 StepConfig choose_step_config(int kind, int npad, int num_sms, bool variants) {
   if (g_override[kind][0] && !variants) {
@@ -737,21 +760,34 @@ StepConfig choose_step_config(int kind, int npad, int num_sms, bool variants) {
     c.policy = policy_for_grid(static_cast<long long>(c.tiles) * c.cluster, num_sms);
     if (c.threads) return c;
   }
-  // Measured on GB300 (in-graph replay of the fused kernels, landmark
-  // counts 1024..65536), one target per thread throughout:
-  //  * from 4096 landmarks up, forward steps run fastest as 128-thread CTAs
-  //    in clusters of 16 and reverse steps as 64-thread CTAs in clusters of 8;
+  // One target per thread throughout.  On a device with the SM count it was
+  // measured for, the table gives the CTA and cluster sizes per padded
+  // landmark count: the fastest shape swings by up to 17% between
+  // neighbouring sizes as the grid fills the SMs unevenly.  Elsewhere the
+  // size rule it refines, measured on GB300 (in-graph replay, 1024..65536
+  // landmarks):
+  //  * from 4096 landmarks up, forward steps as 128-thread CTAs in clusters
+  //    of 16 and reverse steps as 64-thread CTAs in clusters of 8;
   //  * below, CTAs of half the threads spread the few targets over more SMs:
   //    forward 64 threads, clusters of 16 (+13% at 1024 and 2048 landmarks);
-  //    reverse 32 threads, clusters of 16 up to 1024 landmarks (+18%) and of
-  //    8 up to 2048 (+6%).
+  //    reverse 32 threads, clusters of 16 up to 1024 landmarks and of 8 up to
+  //    2048.
   // The variant kernels (RK4 stages, the terminal launch, planar landmarks)
   // exist for the 128 / 64-thread CTAs only.  A grid of 1.5 waves or more
   // (8 CTAs per SM) is scheduled with load balancing, which keeps every SM
   // busy; a smaller grid is spread over the SMs.
   int threads = kind == 0 ? kVarFwdThreads : kVarBwdThreads;
   int cmax = kind == 0 ? 16 : 8;
-  if (!variants && npad <= 2048) {
+  if (g_use_table && num_sms == kStepTableSms) {
+    const StepRule& r = table_rule(npad);
+    if (kind == 0) {
+      if (!variants) threads = r.fwd_threads;
+      cmax = variants ? r.fwd_full_cluster : r.fwd_cluster;
+    } else {
+      if (!variants) threads = r.bwd_threads;
+      cmax = variants ? r.bwd_full_cluster : r.bwd_cluster;
+    }
+  } else if (!variants && npad <= 2048) {
     threads /= 2;
     if (kind == 1 && npad <= 1024) cmax = 16;
   }

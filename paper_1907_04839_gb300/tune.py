@@ -13,6 +13,17 @@ landmarks.
 scheduling preference (default, spread, load balancing) and reports how many
 clusters of each shape can be resident at once; `--graph` times the fused
 kernels as back-to-back replays inside a CUDA graph.
+
+`--emit-table PATH` measures the step-configuration table the library
+compiles in (csrc/step_table.inc): for every padded landmark count from 64
+to 16384 in steps of 64, and from 20480 to 65536 in steps of 4096, each
+fused kernel is timed in graph replay with CTAs of both sizes (forward 64 /
+128 threads, reverse 32 / 64) in clusters of 4, 8 and 16, and the fastest
+shape is written out, together with the fastest cluster size for the
+full-size CTAs (the only ones the RK4, terminal and planar kernels exist
+for).  The cluster size fixes how a target's sum is split, so the table
+also fixes the rounding of every result: it is measured offline once per
+GPU model and never at run time.
 """
 from __future__ import annotations
 
@@ -48,6 +59,8 @@ def main():
     ap.add_argument("--variants", default="all", choices=["all", "default", "small"],
                     help="default: only the (threads, R) the library picks; small: those and the one-target "
                          "variants with half the threads")
+    ap.add_argument("--emit-table", metavar="PATH", help="measure the built-in step-configuration table and "
+                                                           "write it to PATH")
     args = ap.parse_args()
     import torch
 
@@ -56,6 +69,9 @@ def main():
     dev = torch.device("cuda", 0)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     stream = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+    if args.emit_table:
+        emit_table(lib, dev, sms, stream, args.emit_table, args.sigma)
+        return
     for n in args.n:
         pr = ls.ellipsoid_pair(n, seed=0, n_bumps=8)
         rng = np.random.default_rng(1)
@@ -119,6 +135,69 @@ def main():
                                       "splits_req": s, "splits": used.value, "tiles": tiles,
                                       "ctas": tiles * used.value, "ms": ms.value,
                                       "gpairs_per_s": pairs / ms.value / 1e6}), flush=True)
+
+
+TABLE_SIZES = list(range(64, 16384 + 1, 64)) + list(range(20480, 65536 + 1, 4096))
+# (kind, half-size CTA, full-size CTA) of the fused kernels
+TABLE_SHAPES = ((2, 64, 128), (3, 32, 64))
+TABLE_CLUSTERS = (4, 8, 16)
+
+
+def _time_step(lib, kind, n, sigma, bufs, threads, cluster, reps, stream):
+    P = lambda t: ctypes.c_void_p(t.data_ptr())
+    q, p, a, b = bufs
+    ms = ctypes.c_double(0.0)
+    used = ctypes.c_int32(0)
+    st = lib.gs_time_pair_config(kind + 16, n, sigma, P(q), P(p), P(a), P(b), threads, 1, 1, cluster, reps,
+                                 ctypes.byref(ms), ctypes.byref(used), stream)
+    if st != 0:
+        raise RuntimeError(f"gs_time_pair_config(kind {kind}, N {n}, {threads} threads, cluster {cluster}): "
+                           f"{lib.gs_last_error().decode()}")
+    return ms.value
+
+
+def emit_table(lib, dev, sms, stream, path, sigma, reps=40):
+    """Time every (CTA size, cluster size) of both fused kernels at each
+    padded size of TABLE_SIZES and write the fastest as a C++ table."""
+    import torch
+
+    import landmark_synth as ls
+    rows = []
+    for npad in TABLE_SIZES:
+        pr = ls.ellipsoid_pair(npad, seed=0, n_bumps=8)
+        rng = np.random.default_rng(1)
+        bufs = (torch.tensor(pr.q0, dtype=torch.float32, device=dev),
+                torch.tensor(rng.normal(0, 0.01, size=(npad, 3)), dtype=torch.float32, device=dev),
+                torch.tensor(rng.normal(0, 1.0, size=(npad, 3)), dtype=torch.float32, device=dev),
+                torch.tensor(rng.normal(0, 0.01, size=(npad, 3)), dtype=torch.float32, device=dev))
+        row = [npad]
+        for kind, half, full in TABLE_SHAPES:
+            times = {}
+            for nt in (half, full):
+                for c in TABLE_CLUSTERS:
+                    if c > nt or c > npad // 8:
+                        continue
+                    times[(nt, c)] = _time_step(lib, kind, npad, sigma, bufs, nt, c, reps, stream)
+                    print(json.dumps({"npad": npad, "kind": "step_fwd" if kind == 2 else "step_bwd", "threads": nt,
+                                      "cluster": c, "ms": times[(nt, c)],
+                                      "gpairs_per_s": npad * npad / times[(nt, c)] / 1e6}), flush=True)
+            best = min(times, key=times.get)
+            best_full = min((k for k in times if k[0] == full), key=times.get)
+            row += [best[0], best[1], best_full[1]]
+        rows.append(row)
+    name = torch.cuda.get_device_name(dev)
+    with open(path, "w") as f:
+        f.write("// Fused step-kernel configuration per padded landmark count, measured on\n")
+        f.write(f"// {name} ({sms} SMs) by\n")
+        f.write(f"//     python -m paper_1907_04839_gb300.tune --emit-table <path> (graph replay, {reps} launches)\n")
+        f.write("// Columns: padded landmark count; forward CTA threads, forward cluster, cluster\n")
+        f.write("// for 128-thread forward CTAs; reverse CTA threads, reverse cluster, cluster for\n")
+        f.write("// 64-thread reverse CTAs.  One target per thread, one warp group.\n")
+        f.write(f"constexpr int kStepTableSms = {sms};\n")
+        f.write("constexpr StepRule kStepTable[] = {\n")
+        for r in rows:
+            f.write("    {" + ", ".join(str(v) for v in r) + "},\n")
+        f.write("};\n")
 
 
 if __name__ == "__main__":

@@ -115,3 +115,33 @@ def test_server_config_layout_matches_header(tmp_path):
     out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     assert out[0] == ctypes.sizeof(gsh.GsServerConfig)
     assert out[1:] == [getattr(gsh.GsServerConfig, f).offset for f in fields]
+
+
+def test_step_table_switch_rejects_other_values():
+    import paper_1907_04839_gb300 as gsh
+    lib = gsh.load()
+    for bad in (-1, 2, 7):
+        assert lib.gs_set_step_table(bad) == -1
+        assert b"on must be" in lib.gs_last_error()
+
+
+def test_step_table_rows_are_valid_configurations():
+    """Every row of the compiled-in step-configuration table names a kernel
+    that exists (forward 64 / 128 threads, reverse 32 / 64), a power-of-two
+    cluster that divides the CTA's targets and leaves every CTA of the cluster
+    at least 8 sources, and the rows ascend."""
+    import re
+    path = os.path.join(ROOT, "paper_1907_04839_gb300", "csrc", "step_table.inc")
+    text = open(path).read()
+    sms = int(re.search(r"kStepTableSms = (\d+);", text).group(1))
+    assert sms > 0
+    rows = [tuple(int(v) for v in m.group(1).split(","))
+            for m in re.finditer(r"^\s*\{([0-9, ]+)\},\s*$", text, re.M)]
+    assert len(rows) >= 256
+    npads = [r[0] for r in rows]
+    assert npads == sorted(npads) and len(set(npads)) == len(npads)
+    assert npads[0] == 64 and all(n % 64 == 0 for n in npads)
+    for npad, ft, fc, ffc, bt, bc, bfc in rows:
+        assert ft in (64, 128) and bt in (32, 64)
+        for threads, c in ((ft, fc), (128, ffc), (bt, bc), (64, bfc)):
+            assert c in (1, 2, 4, 8, 16) and c <= threads and c <= max(1, npad // 8), (npad, threads, c)

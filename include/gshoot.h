@@ -361,8 +361,9 @@ gs_status step_forward_noalloc(int64_t N, double sigma, const float* q, const fl
  * warp groups that split each CTA's sources; groups must be 1 for kinds 0/1).
  * For kinds 0/1, splits > 0 forces the number of source splits and
  * splits <= 0 lets the library balance them; for kinds 2/3, splits is the
- * cluster size (1, 2, 4, 8 or 16).  Adding 16 to kind captures the `reps` launches into one CUDA
- * graph (linked by programmatic dependent launch) and times its replay.
+ * cluster size (1 to 16, at most the CTA's targets).  Adding 16 to kind
+ * captures the `reps` launches into one CUDA graph (linked by programmatic
+ * dependent launch) and times its replay.
  * The kernel runs `reps` times back to back on (q, p[, alpha,
  * beta]) between two CUDA events on `stream`.  Out: *ms per launch,
  * *splits_used (NULL to skip).  GS_EINVAL for an unknown variant.
@@ -417,9 +418,9 @@ gs_status gs_set_late_trigger(int32_t mode);
  * gs_set_step_table — tuning (no counterpart in the paper): whether the
  * fused time-step kernels take their CTA and cluster sizes from the table
  * measured offline on this GPU model (one entry per padded landmark count
- * up to 16384, coarser up to 65536; used only on a device with the table's
- * SM count).  on = 1 (the initial state): the table; 0: the size rule the
- * table refines (forward 128-thread CTAs in clusters of 16 and reverse
+ * up to 16384; used only on a device with the table's SM count; larger
+ * counts take the size rule).  on = 1 (the initial state): the table; 0:
+ * the size rule the table refines (forward 128-thread CTAs in clusters of 16 and reverse
  * 64-thread CTAs in clusters of 8, half-size CTAs up to 2048 landmarks).
  * The cluster size sets how each target's sum is split, so the two choices
  * can differ in the last bits of a result.  Clears the cached graphs.

@@ -6,13 +6,16 @@
 // targets.  CTA rank r sums the pair terms of every target in the tile
 // against one contiguous split of the sources (pair_tile.cuh).  The C splits
 // together cover all N sources.  The split sums then meet in distributed
-// shared memory: CTA r reduces targets [r*M/C, (r+1)*M/C), adding the C
-// partials of each of its targets in rank order, in double-single
-// arithmetic, and applies the FP64 update to those targets.  The forward
-// kernel has every CTA store its partials straight into the reducing CTA's
-// shared memory (remote stores: nothing waits on a remote load; one cluster
-// barrier per step).  The reverse kernel has the reducing CTA load them from
-// its peers after a barrier (which measured faster for it).  The reduction
+// shared memory: with slice = ceil(M/C), CTA r reduces targets
+// [r*slice, (r+1)*slice) of the tile (C need not divide M or be a power of
+// two), adding the C partials of each of its targets in rank order, in
+// double-single arithmetic, and applies the FP64 update to those targets.
+// The forward kernel has every CTA store its partials straight into the
+// reducing CTA's shared memory (remote stores: nothing waits on a remote
+// load; one cluster barrier per step).  The reverse kernel does the same
+// with one-warp CTAs; larger reverse CTAs have the reducing CTA load the
+// partials from its peers after a barrier (which measured faster for them).
+// The reduction
 // order is fixed, so results are deterministic.  No split partials go
 // through global memory, and no second kernel is needed.  This plays the
 // role of the paper's shared-memory reduction (Section 2.5), spread over up
@@ -171,16 +174,17 @@ __device__ __forceinline__ void forward_body(const StepFwdArgs& a, const StepVie
   };
   __shared__ __align__(128) Smem sm;
   // Partials of this CTA's slice of targets from every source split:
-  // [C][M/C][D] float4, the same 2D double-single values per target.
-  __shared__ __align__(16) float4 recv[M * D];
+  // [C][slice][D] float4, the same 2D double-single values per target
+  // (C * slice < M + C <= M + 16).
+  __shared__ __align__(16) float4 recv[(M + 15) * D];
   __shared__ __align__(8) Pipe pp;
 
   const unsigned rank = cluster_rank(), C = cluster_size();
-  // The launch must match the kernel: NT threads per CTA, a cluster size that
-  // divides the tile, and splits (multiples of 8 sources) that cover the
-  // problem.  The test has the same outcome in every CTA of a cluster, so a
-  // bad launch leaves before any barrier.
-  if (blockDim.x != NT || M % static_cast<int>(C) != 0 || (v.split_len & 7) != 0 ||
+  // The launch must match the kernel: NT threads per CTA, at most one CTA of
+  // the cluster per target of the tile, and splits (multiples of 8 sources)
+  // that cover the problem.  The test has the same outcome in every CTA of a
+  // cluster, so a bad launch leaves before any barrier.
+  if (blockDim.x != NT || static_cast<int>(C) > M || (v.split_len & 7) != 0 ||
       static_cast<long long>(v.split_len) * C < v.npad) {
     if (threadIdx.x == 0) atomicOr(a.status, kErrBadLaunch);
     return;
@@ -200,7 +204,7 @@ __device__ __forceinline__ void forward_body(const StepFwdArgs& a, const StepVie
   t.load(a.qp, tile0 + lt0, TG, lim);
   const float4* src[1] = {a.qp};
   stream_sources<1, W, D>(sm.st, pp, src, j0, j1, t, a.status, grp);  // ends with a CTA barrier
-  const int slice = M / static_cast<int>(C);
+  const int slice = (M + static_cast<int>(C) - 1) / static_cast<int>(C);  // the last CTA may reduce fewer
   const auto res = [&](const FwdTile<R, D>& tt, int r, ds* w) { tt.result(r, v.kappa_f, w); };
   combine_tile<NT, R, W, M, D>(sm.red, t, res, lt0, grp);
   // recv is memory of its own, so a CTA may push as soon as every peer has
@@ -214,7 +218,7 @@ __device__ __forceinline__ void forward_body(const StepFwdArgs& a, const StepVie
     const int ll = item / D;
     const int lt = static_cast<int>(rank) * slice + ll;
     const int k = item % D;
-    if (v.tile * M + lt >= v.n) continue;
+    if (lt >= M || v.tile * M + lt >= v.n) continue;
     const int i = tile0 + lt;  // packed landmark index
     ds hp{0.f, 0.f}, hq{0.f, 0.f};
 #pragma unroll 4
@@ -320,15 +324,15 @@ __device__ __forceinline__ void backward_body(const StepBwdArgs& a, const StepVi
   // 64-thread CTAs.
   constexpr bool kPush = NT == 32;
   __shared__ __align__(128) Smem sm;
-  __shared__ __align__(16) float4 recv[kPush ? M * D : 1];
+  __shared__ __align__(16) float4 recv[kPush ? (M + 15) * D : 1];
   __shared__ __align__(8) Pipe pp;
 
   const unsigned rank = cluster_rank(), C = cluster_size();
-  // The launch must match the kernel: NT threads per CTA, a cluster size that
-  // divides the tile, and splits (multiples of 8 sources) that cover the
-  // problem.  The test has the same outcome in every CTA of a cluster, so a
-  // bad launch leaves before any barrier.
-  if (blockDim.x != NT || M % static_cast<int>(C) != 0 || (v.split_len & 7) != 0 ||
+  // The launch must match the kernel: NT threads per CTA, at most one CTA of
+  // the cluster per target of the tile, and splits (multiples of 8 sources)
+  // that cover the problem.  The test has the same outcome in every CTA of a
+  // cluster, so a bad launch leaves before any barrier.
+  if (blockDim.x != NT || static_cast<int>(C) > M || (v.split_len & 7) != 0 ||
       static_cast<long long>(v.split_len) * C < v.npad) {
     if (threadIdx.x == 0) atomicOr(a.status, kErrBadLaunch);
     return;
@@ -348,7 +352,7 @@ __device__ __forceinline__ void backward_body(const StepBwdArgs& a, const StepVi
   t.load(a.qp, a.ab, tile0 + lt0, TG, lim);
   const float4* src[2] = {a.qp, a.ab};
   stream_sources<2, W, D>(sm.st, pp, src, j0, j1, t, a.status, grp);
-  const int slice = M / static_cast<int>(C);
+  const int slice = (M + static_cast<int>(C) - 1) / static_cast<int>(C);  // the last CTA may reduce fewer
   if constexpr (kPush) {
     const auto res = [&](const BwdTile<R, D>& tt, int r, ds* w) { tt.result(r, v.kq_f, v.kappa_f, w); };
     combine_tile<NT, R, W, M, D>(sm.red, t, res, lt0, grp);
@@ -371,7 +375,7 @@ __device__ __forceinline__ void backward_body(const StepBwdArgs& a, const StepVi
     const int ll = item / D;
     const int lt = static_cast<int>(rank) * slice + ll;
     const int k = item % D;
-    if (v.tile * M + lt >= v.n) continue;
+    if (lt >= M || v.tile * M + lt >= v.n) continue;
     const int i = tile0 + lt;
     ds da{0.f, 0.f}, db{0.f, 0.f};
     if constexpr (kPush) {
@@ -646,7 +650,7 @@ StepConfig step_config_for(int kind, int npad, int threads, int R, int cluster, 
   StepConfig c{};
   if (groups < 1 || !valid_variant(kind, threads, R, groups)) return c;
   const int M = threads / groups * R;
-  if (cluster < 1 || cluster > 16 || (cluster & (cluster - 1)) != 0 || cluster > M) return c;
+  if (cluster < 1 || cluster > 16 || cluster > M) return c;
   c.threads = threads;
   c.R = R;
   c.groups = groups;
@@ -741,12 +745,12 @@ struct StepRule {
 #include "step_table.inc"
 bool g_use_table = true;
 
-// The table row for npad: the first row at or above it (rows are ascending;
-// the last row serves every larger count).
-const StepRule& table_rule(int npad) {
+// The table row for npad: the first row at or above it (rows are
+// ascending), or null above the last row.
+const StepRule* table_rule(int npad) {
   const StepRule* end = kStepTable + sizeof(kStepTable) / sizeof(kStepTable[0]);
   const StepRule* r = std::lower_bound(kStepTable, end, npad, [](const StepRule& e, int n) { return e.npad < n; });
-  return r == end ? end[-1] : *r;
+  return r == end ? nullptr : r;
 }
 }  // namespace
 
@@ -762,10 +766,10 @@ StepConfig choose_step_config(int kind, int npad, int num_sms, bool variants) {
   }
   // One target per thread throughout.  On a device with the SM count it was
   // measured for, the table gives the CTA and cluster sizes per padded
-  // landmark count: the fastest shape swings by up to 17% between
-  // neighbouring sizes as the grid fills the SMs unevenly.  Elsewhere the
-  // size rule it refines, measured on GB300 (in-graph replay, 1024..65536
-  // landmarks):
+  // landmark count up to 16384: the fastest shape swings by up to 20%
+  // between neighbouring sizes as the clusters fill the SMs of each GPC
+  // unevenly.  Above the table and on other devices, the size rule it
+  // refines, measured on GB300 (in-graph replay, 1024..65536 landmarks):
   //  * from 4096 landmarks up, forward steps as 128-thread CTAs in clusters
   //    of 16 and reverse steps as 64-thread CTAs in clusters of 8;
   //  * below, CTAs of half the threads spread the few targets over more SMs:
@@ -777,23 +781,27 @@ StepConfig choose_step_config(int kind, int npad, int num_sms, bool variants) {
   // (8 CTAs per SM) is scheduled with load balancing, which keeps every SM
   // busy; a smaller grid is spread over the SMs.
   int threads = kind == 0 ? kVarFwdThreads : kVarBwdThreads;
-  int cmax = kind == 0 ? 16 : 8;
-  if (g_use_table && num_sms == kStepTableSms) {
-    const StepRule& r = table_rule(npad);
+  int c = 0;
+  const StepRule* r = g_use_table && num_sms == kStepTableSms ? table_rule(npad) : nullptr;
+  if (r) {
     if (kind == 0) {
-      if (!variants) threads = r.fwd_threads;
-      cmax = variants ? r.fwd_full_cluster : r.fwd_cluster;
+      if (!variants) threads = r->fwd_threads;
+      c = variants ? r->fwd_full_cluster : r->fwd_cluster;
     } else {
-      if (!variants) threads = r.bwd_threads;
-      cmax = variants ? r.bwd_full_cluster : r.bwd_cluster;
+      if (!variants) threads = r->bwd_threads;
+      c = variants ? r->bwd_full_cluster : r->bwd_cluster;
     }
-  } else if (!variants && npad <= 2048) {
-    threads /= 2;
-    if (kind == 1 && npad <= 1024) cmax = 16;
+    c = std::min(c, std::max(1, npad / kUnroll));  // every CTA keeps at least 8 sources
+  } else {
+    int cmax = kind == 0 ? 16 : 8;
+    if (!variants && npad <= 2048) {
+      threads /= 2;
+      if (kind == 1 && npad <= 1024) cmax = 16;
+    }
+    const int cl = std::min(cmax, std::max(1, npad / kUnroll));
+    c = 1;
+    while (c * 2 <= cl) c *= 2;
   }
-  const int cl = std::min(cmax, std::max(1, npad / kUnroll));
-  int c = 1;
-  while (c * 2 <= cl) c *= 2;
   StepConfig cfg = step_config_for(kind, npad, threads, 1, c);
   cfg.policy = policy_for_grid(static_cast<long long>(cfg.tiles) * c, num_sms);
   return cfg;

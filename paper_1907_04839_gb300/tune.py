@@ -15,13 +15,15 @@ clusters of each shape can be resident at once; `--graph` times the fused
 kernels as back-to-back replays inside a CUDA graph.
 
 `--emit-table PATH` measures the step-configuration table the library
-compiles in (csrc/step_table.inc): for every padded landmark count from 64
-to 16384 in steps of 64, and from 20480 to 65536 in steps of 4096, each
-fused kernel is timed in graph replay with CTAs of both sizes (forward 64 /
-128 threads, reverse 32 / 64) in clusters of 4, 8 and 16, and the fastest
-shape is written out, together with the fastest cluster size for the
-full-size CTAs (the only ones the RK4, terminal and planar kernels exist
-for).  The cluster size fixes how a target's sum is split, so the table
+compiles in (csrc/step_table.inc).  For every padded landmark count from 64
+to 16384 in steps of 64, whole gradients (T = 10, back to back, as an
+optimiser runs them) are timed with each fused kernel in CTAs of both sizes
+(forward 64 / 128 threads, reverse 32 / 64) and clusters of 4 to 16 CTAs
+(even sizes), one kernel varied at a time; so each kernel is timed as the
+gradient runs it (programmatic dependent launch, the late trigger, the state
+updates).  The fastest shape of each kernel is written out, together with the
+fastest cluster size for the full-size CTAs (the only ones the RK4, terminal
+and planar kernels exist for).  The cluster size fixes how a target's sum is split, so the table
 also fixes the rounding of every result: it is measured offline once per
 GPU model and never at run time.
 """
@@ -137,59 +139,87 @@ def main():
                                       "gpairs_per_s": pairs / ms.value / 1e6}), flush=True)
 
 
-TABLE_SIZES = list(range(64, 16384 + 1, 64)) + list(range(20480, 65536 + 1, 4096))
-# (kind, half-size CTA, full-size CTA) of the fused kernels
-TABLE_SHAPES = ((2, 64, 128), (3, 32, 64))
-TABLE_CLUSTERS = (4, 8, 16)
+TABLE_SIZES = list(range(64, 16384 + 1, 64))
+# (half-size CTA, full-size CTA) threads of the forward and of the reverse kernel
+TABLE_FWD = (64, 128)
+TABLE_BWD = (32, 64)
+TABLE_CLUSTERS = (4, 6, 8, 10, 12, 14, 16)
+TABLE_T = 10
 
 
-def _time_step(lib, kind, n, sigma, bufs, threads, cluster, reps, stream):
+def _gradient_ms(lib, prm, bufs, stream, reps):
+    """Device time (ms) of one shoot_gradient call under the current step
+    configuration: `reps` calls back to back between two CUDA events, as an
+    optimiser issues them, after three untimed calls; the better of two such
+    blocks."""
+    import torch
     P = lambda t: ctypes.c_void_p(t.data_ptr())
-    q, p, a, b = bufs
-    ms = ctypes.c_double(0.0)
-    used = ctypes.c_int32(0)
-    st = lib.gs_time_pair_config(kind + 16, n, sigma, P(q), P(p), P(a), P(b), threads, 1, 1, cluster, reps,
-                                 ctypes.byref(ms), ctypes.byref(used), stream)
-    if st != 0:
-        raise RuntimeError(f"gs_time_pair_config(kind {kind}, N {n}, {threads} threads, cluster {cluster}): "
-                           f"{lib.gs_last_error().decode()}")
-    return ms.value
+    q, p, t, gp, gq = bufs
+    run = lambda: _lib.check(lib.shoot_gradient(ctypes.byref(prm), P(q), P(p), P(t), None, P(gp), P(gq), stream))
+    for _ in range(3):
+        run()
+    best = math.inf
+    for _ in range(2):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            run()
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) / reps)
+    return best
 
 
-def emit_table(lib, dev, sms, stream, path, sigma, reps=40):
-    """Time every (CTA size, cluster size) of both fused kernels at each
-    padded size of TABLE_SIZES and write the fastest as a C++ table."""
+def emit_table(lib, dev, sms, stream, path, sigma):
+    """Time every (CTA size, cluster size) of both fused kernels inside whole
+    gradients at each padded size of TABLE_SIZES and write the fastest as a
+    C++ table.  The forward shapes are timed with the reverse kernel at the
+    size rule's shape; the reverse shapes then with the fastest forward
+    shape."""
     import torch
 
     import landmark_synth as ls
     rows = []
-    for npad in TABLE_SIZES:
-        pr = ls.ellipsoid_pair(npad, seed=0, n_bumps=8)
-        rng = np.random.default_rng(1)
-        bufs = (torch.tensor(pr.q0, dtype=torch.float32, device=dev),
-                torch.tensor(rng.normal(0, 0.01, size=(npad, 3)), dtype=torch.float32, device=dev),
-                torch.tensor(rng.normal(0, 1.0, size=(npad, 3)), dtype=torch.float32, device=dev),
-                torch.tensor(rng.normal(0, 0.01, size=(npad, 3)), dtype=torch.float32, device=dev))
-        row = [npad]
-        for kind, half, full in TABLE_SHAPES:
-            times = {}
-            for nt in (half, full):
-                for c in TABLE_CLUSTERS:
-                    if c > nt or c > npad // 8:
-                        continue
-                    times[(nt, c)] = _time_step(lib, kind, npad, sigma, bufs, nt, c, reps, stream)
-                    print(json.dumps({"npad": npad, "kind": "step_fwd" if kind == 2 else "step_bwd", "threads": nt,
-                                      "cluster": c, "ms": times[(nt, c)],
-                                      "gpairs_per_s": npad * npad / times[(nt, c)] / 1e6}), flush=True)
-            best = min(times, key=times.get)
-            best_full = min((k for k in times if k[0] == full), key=times.get)
-            row += [best[0], best[1], best_full[1]]
-        rows.append(row)
+    rule = {0: (128, 16), 1: (64, 8)}
+    try:
+        for npad in TABLE_SIZES:
+            pr = ls.ellipsoid_pair(npad, seed=0, n_bumps=8)
+            p0 = ls.random_momentum(npad, 0.01, seed=1)
+            q, p, t = (torch.tensor(np.asarray(a, np.float32), device=dev) for a in (pr.q0, p0, pr.target))
+            bufs = (q, p, t, torch.empty_like(q), torch.empty_like(q))
+            prm = _lib.GsParams(N=npad, T=TABLE_T, ckpt_every=0, sigma=sigma, lambda_=10.0, lbfgs_m=10, max_iter=1,
+                                grad_tol=0.0)
+            reps = max(4, min(15, int(1.2e9 / npad ** 2)))
+            fixed = {0: rule[0], 1: (rule[1][0], min(rule[1][1], npad // 8))}
+            row = [npad]
+            for kind, shapes in ((0, TABLE_FWD), (1, TABLE_BWD)):
+                times = {}
+                other = 1 - kind
+                _lib.check(lib.gs_set_step_config(other, fixed[other][0], 1, 1, fixed[other][1]))
+                for nt in shapes:
+                    for c in TABLE_CLUSTERS:
+                        if c > TABLE_BWD[0] or c > npad // 8:
+                            continue
+                        _lib.check(lib.gs_set_step_config(kind, nt, 1, 1, c))
+                        times[(nt, c)] = _gradient_ms(lib, prm, bufs, stream, reps)
+                        print(json.dumps({"npad": npad, "kind": "step_fwd" if kind == 0 else "step_bwd",
+                                          "threads": nt, "cluster": c, "other": list(fixed[other]),
+                                          "gradient_ms": times[(nt, c)]}), flush=True)
+                best = min(times, key=times.get)
+                best_full = min((k for k in times if k[0] == shapes[1]), key=times.get)
+                fixed[kind] = best
+                row += [best[0], best[1], best_full[1]]
+            rows.append(row)
+    finally:
+        lib.gs_set_step_config(0, 0, 0, 0, 0)
+        lib.gs_set_step_config(1, 0, 0, 0, 0)
     name = torch.cuda.get_device_name(dev)
     with open(path, "w") as f:
         f.write("// Fused step-kernel configuration per padded landmark count, measured on\n")
         f.write(f"// {name} ({sms} SMs) by\n")
-        f.write(f"//     python -m paper_1907_04839_gb300.tune --emit-table <path> (graph replay, {reps} launches)\n")
+        f.write("//     python -m paper_1907_04839_gb300.tune --emit-table <path>\n")
+        f.write(f"// (whole gradients, T = {TABLE_T}, timed back to back).\n")
         f.write("// Columns: padded landmark count; forward CTA threads, forward cluster, cluster\n")
         f.write("// for 128-thread forward CTAs; reverse CTA threads, reverse cluster, cluster for\n")
         f.write("// 64-thread reverse CTAs.  One target per thread, one warp group.\n")
@@ -198,7 +228,6 @@ def emit_table(lib, dev, sms, stream, path, sigma, reps=40):
         for r in rows:
             f.write("    {" + ", ".join(str(v) for v in r) + "},\n")
         f.write("};\n")
-
 
 if __name__ == "__main__":
     main()

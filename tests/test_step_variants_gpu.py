@@ -74,6 +74,25 @@ def test_reverse_variants(case, bwd):
         assert e[0] < 1e-5 and e[1] < 1e-4 and e[2] < 1e-4
 
 
+@pytest.mark.parametrize("c", [3, 6, 10, 12, 14])
+def test_clusters_that_do_not_divide_the_tile(case, c):
+    """Cluster sizes that are not powers of two: the last CTA of each cluster
+    reduces fewer targets than the others.  The CTA shapes the step table
+    uses, forward and reverse alike."""
+    for fwd, bwd in (((128, 1, 1), (64, 1, 1)), ((64, 1, 1), (32, 1, 1))):
+        e = _run(case, fwd, bwd, c, c)
+        print("fwd %s bwd %s c=%d: loss %.2e grad_p0 %.2e grad_q0 %.2e" % ((fwd, bwd, c) + e))
+        assert e[0] < 1e-5 and e[1] < 1e-4 and e[2] < 1e-4
+
+
+def test_cluster_size_outside_1_to_16_is_rejected():
+    import paper_1907_04839_gb300 as gsh
+    lib = gsh.load()
+    for c in (0, 17, 32):
+        assert lib.gs_set_step_config(0, 64, 1, 1, c) == -1
+        assert lib.gs_set_step_config(1, 32, 1, 1, c) == -1
+
+
 def test_unknown_variant_is_rejected():
     import paper_1907_04839_gb300 as gsh
     lib = gsh.load()

@@ -429,6 +429,20 @@ gs_status gs_set_late_trigger(int32_t mode);
 gs_status gs_set_step_table(int32_t on);
 
 /*
+ * gs_step_config — diagnostics (no counterpart in the paper): the fused
+ * time-step kernel configuration that shoot_forward / shoot_gradient launch
+ * for N landmarks, kind 0 (forward) or 1 (reverse), on a device with
+ * num_sms SMs (num_sms <= 0: the current device), under the current table
+ * switch and overrides.  variants != 0 asks for the RK4 / terminal / planar
+ * launches, which use the full-size CTAs.  Out: *threads per CTA and
+ * *cluster (CTAs per cluster); one target per thread and one warp group
+ * unless an override says otherwise.  With num_sms > 0 no CUDA call is
+ * made.  GS_EINVAL for a bad kind, N outside [1, 2^26] or NULL outputs.
+ */
+gs_status gs_step_config(int32_t kind, int64_t N, int32_t num_sms, int32_t variants, int32_t* threads,
+                         int32_t* cluster);
+
+/*
  * gs_set_phase_timing — diagnostics (no counterpart in the paper): when `on`
  * is nonzero, the CUDA graphs of shoot_forward / shoot_gradient (and of the
  * L-BFGS evaluations) on the current device record three events: before the
@@ -467,7 +481,7 @@ void gs_release_workspace(void);
 
 /* Library ABI version: 100 * major + minor (101: gs_params gained
  * integrator and kinetic_at; 102: dim; 103: gs_server_config.schedule;
- * 104: gs_set_step_table). */
+ * 104: gs_set_step_table; 105: gs_step_config). */
 int32_t gs_version(void);
 
 #ifdef __cplusplus

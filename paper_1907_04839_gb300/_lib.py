@@ -27,7 +27,7 @@ EXPORTS = [
     "gs_server_stats", "gs_server_destroy",
     "gs_time_pair_kernels", "gs_time_pair_config", "gs_set_step_config", "step_forward_noalloc",
     "gs_set_phase_timing", "gs_phase_times", "gs_set_cluster_policy", "gs_max_active_clusters",
-    "gs_set_late_trigger", "gs_check_wait_timeout", "gs_set_step_table",
+    "gs_set_late_trigger", "gs_check_wait_timeout", "gs_set_step_table", "gs_step_config",
     "gs_last_error",
     "gs_release_workspace",
     "gs_version",
@@ -141,6 +141,7 @@ def _declare(lib):
     lib.gs_set_cluster_policy.argtypes = [i32]
     lib.gs_set_late_trigger.argtypes = [i32]
     lib.gs_set_step_table.argtypes = [i32]
+    lib.gs_step_config.argtypes = [i32, ctypes.c_int64, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.gs_check_wait_timeout.argtypes = [i32, dp, vp]
     lib.gs_max_active_clusters.argtypes = [i32, i32, i32, i32, i32, ctypes.c_void_p]
     lib.gs_phase_times.argtypes = [dp, dp]
@@ -151,7 +152,7 @@ def _declare(lib):
                  "gs_time_pair_kernels",
                  "step_forward_noalloc", "gs_time_pair_config", "gs_set_step_config", "gs_set_phase_timing",
                  "gs_phase_times", "gs_set_cluster_policy", "gs_max_active_clusters", "gs_set_late_trigger",
-                 "gs_set_step_table", "gs_check_wait_timeout"):
+                 "gs_set_step_table", "gs_step_config", "gs_check_wait_timeout"):
         getattr(lib, name).restype = ctypes.c_int
     lib.gs_last_error.restype = ctypes.c_char_p
     lib.gs_last_error.argtypes = []

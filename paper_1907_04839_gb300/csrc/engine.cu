@@ -832,6 +832,26 @@ gs_status gs_set_step_table(int32_t on) {
   return GS_OK;
 }
 
+gs_status gs_step_config(int32_t kind, int64_t N, int32_t num_sms, int32_t variants, int32_t* threads,
+                         int32_t* cluster) {
+  gs::g_err.clear();
+  if (kind != 0 && kind != 1) return gs::fail(GS_EINVAL, "kind must be 0 (forward) or 1 (reverse)");
+  if (N < 1 || N > (1LL << 26)) return gs::fail(GS_EINVAL, "N must be in [1, 2^26]");
+  if (!threads || !cluster) return gs::fail(GS_EINVAL, "output pointers must not be NULL");
+  int sms = num_sms;
+  if (sms <= 0) {
+    int dev = 0;
+    GS_CUDA(cudaGetDevice(&dev));
+    GS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  std::lock_guard<std::mutex> lk(gs::g_mu);
+  const gs::StepConfig c = gs::choose_step_config(kind, gs::round_up(N, gs::kPad), sms, variants != 0);
+  if (c.threads == 0) return gs::fail(GS_EINVAL, "no step kernel configuration");
+  *threads = c.threads;
+  *cluster = c.cluster;
+  return GS_OK;
+}
+
 gs_status gs_max_active_clusters(int32_t kind, int32_t threads, int32_t R, int32_t groups, int32_t cluster,
                                  int32_t* clusters) {
   gs::g_err.clear();
@@ -896,6 +916,6 @@ void gs_release_workspace(void) {
   gs::g_ws.clear();
 }
 
-int32_t gs_version(void) { return 104; }
+int32_t gs_version(void) { return 105; }
 
 }  // extern "C"

@@ -145,3 +145,101 @@ def test_step_table_rows_are_valid_configurations():
         assert ft in (64, 128) and bt in (32, 64)
         for threads, c in ((ft, fc), (128, ffc), (bt, bc), (64, bfc)):
             assert 1 <= c <= 16 and c <= threads and c <= max(1, npad // 8), (npad, threads, c)
+
+
+def _table_rows():
+    path = os.path.join(ROOT, "paper_1907_04839_gb300", "csrc", "step_table.inc")
+    text = open(path).read()
+    sms = int(re.search(r"kStepTableSms = (\d+);", text).group(1))
+    rows = {int(m.group(1).split(",")[0]): tuple(int(v) for v in m.group(1).split(","))
+            for m in re.finditer(r"^\s*\{([0-9, ]+)\},\s*$", text, re.M)}
+    return sms, rows
+
+
+def _step_config(lib, kind, n, sms, variants=0):
+    t, c = ctypes.c_int32(0), ctypes.c_int32(0)
+    assert lib.gs_step_config(kind, n, sms, variants, ctypes.byref(t), ctypes.byref(c)) == 0, lib.gs_last_error()
+    return t.value, c.value
+
+
+def _size_rule(kind, npad, variants=False):
+    """The size rule the table refines: forward 128-thread CTAs in clusters of
+    16, reverse 64-thread CTAs in clusters of 8; half-size CTAs up to 2048
+    landmarks (reverse clusters of 16 up to 1024); clusters a power of two
+    that leaves every CTA at least 8 sources."""
+    threads, cmax = (128, 16) if kind == 0 else (64, 8)
+    if not variants and npad <= 2048:
+        threads //= 2
+        if kind == 1 and npad <= 1024:
+            cmax = 16
+    cl = min(cmax, max(1, npad // 8))
+    c = 1
+    while c * 2 <= cl:
+        c *= 2
+    return threads, c
+
+
+def test_step_config_follows_the_table_on_its_device():
+    """gs_step_config (host logic only when the SM count is given) returns the
+    table's row for every padded size the table covers (each N maps to the
+    row of its padded count), the full-size CTAs' cluster for the variant
+    kernels, and the size rule above the table."""
+    import paper_1907_04839_gb300 as gsh
+    lib = gsh.load()
+    sms, rows = _table_rows()
+    for n in list(range(1, 16385, 37)) + [64, 65, 2048, 4096, 16383, 16384]:
+        npad = (n + 63) // 64 * 64
+        r = rows[npad]
+        assert _step_config(lib, 0, n, sms) == (r[1], r[2]), n
+        assert _step_config(lib, 1, n, sms) == (r[4], r[5]), n
+        assert _step_config(lib, 0, n, sms, 1) == (128, r[3]), n
+        assert _step_config(lib, 1, n, sms, 1) == (64, r[6]), n
+    for n in (16385, 20000, 65536, 1 << 20):
+        npad = (n + 63) // 64 * 64
+        for kind in (0, 1):
+            assert _step_config(lib, kind, n, sms) == _size_rule(kind, npad), (kind, n)
+            assert _step_config(lib, kind, n, sms, 1) == _size_rule(kind, npad, True), (kind, n)
+
+
+def test_step_config_size_rule_without_the_table():
+    """Another SM count, or the table switched off, gives the size rule."""
+    import paper_1907_04839_gb300 as gsh
+    lib = gsh.load()
+    sms, _ = _table_rows()
+    try:
+        for other, on in ((sms - 20, 1), (sms, 0)):
+            assert lib.gs_set_step_table(on) == 0
+            for n in (1, 100, 1000, 1024, 1025, 2048, 2049, 3000, 4096, 7168, 16384, 70000):
+                npad = (n + 63) // 64 * 64
+                for kind in (0, 1):
+                    assert _step_config(lib, kind, n, other) == _size_rule(kind, npad), (other, on, kind, n)
+                    assert _step_config(lib, kind, n, other, 1) == _size_rule(kind, npad, True)
+    finally:
+        assert lib.gs_set_step_table(1) == 0
+
+
+def test_step_config_override_applies_to_plain_launches_only():
+    import paper_1907_04839_gb300 as gsh
+    lib = gsh.load()
+    sms, rows = _table_rows()
+    try:
+        # reverse clusters that do not divide the tile exist for 32 / 64-thread CTAs only
+        assert lib.gs_set_step_config(1, 128, 1, 1, 12) == -1
+        assert lib.gs_set_step_config(1, 64, 1, 1, 12) == 0
+        assert _step_config(lib, 1, 4096, sms) == (64, 12)
+        assert _step_config(lib, 1, 40, sms) == (64, 8)  # at most npad / 8 CTAs per cluster
+        assert _step_config(lib, 1, 4096, sms, 1) == (64, rows[4096][6])  # variants keep their kernels
+        assert _step_config(lib, 0, 4096, sms) == (rows[4096][1], rows[4096][2])
+    finally:
+        assert lib.gs_set_step_config(1, 0, 0, 0, 0) == 0
+    assert _step_config(lib, 1, 4096, sms) == (rows[4096][4], rows[4096][5])
+
+
+def test_step_config_rejects_bad_arguments():
+    import paper_1907_04839_gb300 as gsh
+    lib = gsh.load()
+    t, c = ctypes.c_int32(0), ctypes.c_int32(0)
+    assert lib.gs_step_config(2, 100, 152, 0, ctypes.byref(t), ctypes.byref(c)) == -1
+    assert lib.gs_step_config(0, 0, 152, 0, ctypes.byref(t), ctypes.byref(c)) == -1
+    assert lib.gs_step_config(0, (1 << 26) + 1, 152, 0, ctypes.byref(t), ctypes.byref(c)) == -1
+    assert lib.gs_step_config(0, 100, 152, 0, None, ctypes.byref(c)) == -1

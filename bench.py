@@ -721,6 +721,11 @@ def run_gshoot(args, dist):
     fwd_tf = FLOPS_PER_PAIR_FWD * pairs / (fwd_launch_ms * 1e-3) / 1e12
     pipe_lanes = num_sms * 128 * max_mhz * 1e6
     traffic = DRAM_BYTES_PER_BWD_LAUNCH.get(n)
+    shape = {}
+    for kind, name in ((0, "forward"), (1, "reverse")):
+        t, c = ctypes.c_int32(0), ctypes.c_int32(0)
+        gsh.check(lib.gs_step_config(kind, n, 0, 0, ctypes.byref(t), ctypes.byref(c)))
+        shape[name] = {"threads": t.value, "cluster": c.value}
     roofline = {
         "bound": "alu", "kernel": "k_step_backward (StepBackward pair sums + fused adjoint update)",
         "achieved": bwd_tf, "peak": peak, "unit": "TFLOP/s", "frac": bwd_tf / peak, "traffic": traffic,
@@ -729,9 +734,11 @@ def run_gshoot(args, dist):
         "flops_per_launch": FLOPS_PER_PAIR_BWD * pairs, "launch_ms": bwd_launch_ms,
         "launch_ms_basis": "reverse-sweep time / T from graph events in the timed steps (gaps included)",
         "isolated_launch_ms": bwd_ms.value,
+        "launch_shape": shape["reverse"],
         "fp32_pipe_frac": INSTR_PER_PAIR_BWD * pairs / (bwd_launch_ms * 1e-3) / pipe_lanes,
         "forward": {"kernel": "k_step_forward", "achieved": fwd_tf, "frac": fwd_tf / peak,
                     "launch_ms": fwd_launch_ms, "isolated_launch_ms": fwd_ms.value,
+                    "launch_shape": shape["forward"],
                     "fp32_pipe_frac": INSTR_PER_PAIR_FWD * pairs / (fwd_launch_ms * 1e-3) / pipe_lanes},
     }
     line = {

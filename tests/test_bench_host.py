@@ -54,3 +54,54 @@ def test_bench_workloads_are_seeded():
     assert all(tr[k]["t_arrival"] < tr[k + 1]["t_arrival"] for k in range(3))
     q0, p0, t = bench.workload(64)
     assert q0.shape == (64, 3) and q0.dtype == np.float32 and np.array_equal(q0, bench.workload(64)[0])
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` times the FP64 oracle on the host cores and
+    prints one JSON line with the reference arm's keys."""
+    import json
+    import subprocess
+    root = os.path.dirname(HERE)
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "2",
+                          "--warmup", "1"], capture_output=True, text=True, timeout=600, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "grad-evals/s" and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 1 and d["dtype"] == "f64"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": "grad-evals/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    assert d["config"]["N"] == 4096 and d["config"]["T"] == 20
+
+
+def test_clock_sampler_reads_median_under_load_and_reasons(tmp_path):
+    """The clock record: median SM clock over the samples drawing at least the
+    median power, the maximum clock, and every throttle reason seen active."""
+    import subprocess
+    import bench
+    path = tmp_path / "clocks.csv"
+    rows = [
+        "1965, 2070, 150.0, Not Active, Not Active, Not Active, Not Active",
+        "2070, 2070, 450.0, Not Active, Not Active, Not Active, Not Active",
+        "2070, 2070, 470.0, Not Active, Not Active, Not Active, Active",
+        "2055, 2070, 460.0, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+    ]
+    path.write_text("\n".join(rows) + "\n")
+    s = bench.ClockSampler()
+    s.path = str(path)
+    s.proc = subprocess.Popen([sys.executable, "-c", "pass"])
+    s.proc.wait()
+    clk = s.stop()
+    assert clk["samples"] == 4 and clk["sm_max_mhz"] == 2070.0
+    assert clk["sm_mhz"] == 2062.5  # samples at or above the median draw (455 W): 2070 and 2055 MHz
+    assert clk["reasons"] == ["sw_power_cap"] and clk["power_w_max"] == 470.0
+    assert not os.path.exists(path)
+
+
+def test_alu_peak_from_unit_counts():
+    import bench
+    assert abs(bench.alu_peak_tflops(152, 2070.0) - 80.54784) < 1e-9

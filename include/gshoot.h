@@ -18,7 +18,10 @@
  *   (x0 y0 z0 x1 y1 z1 ...).  A pointer may be device memory (cudaMalloc,
  *   managed) or host memory (pageable or pinned); the library checks with
  *   cudaPointerGetAttributes and stages host arrays through its own device
- *   workspace.  The caller owns every array; the library never keeps a pointer
+ *   workspace.  Device memory must belong to the current device (the one
+ *   cudaSetDevice selected in the calling thread): memory of another GPU is
+ *   rejected with GS_EINVAL, because this device's kernels cannot safely
+ *   read it.  The caller owns every array; the library never keeps a pointer
  *   past the call.
  * Scalars.  Scalar outputs (double*, int32_t*) are host pointers and may be
  *   NULL when not wanted.
@@ -330,8 +333,12 @@ gs_status gs_time_pair_kernels(const gs_params* prm, const float* q0, const floa
  * never calls cudaMalloc, cudaFree or any allocating routine.
  *
  * Limits: 1 <= N <= 8192.  Larger N is rejected with GS_EINVAL before any
- *   work is enqueued.  q, p, Hq and Hp must be device arrays ((N,3) float32);
- *   a host pointer is rejected with GS_EINVAL.
+ *   cudaPointerGetAttributes and stages host arrays through its own device
+ *   workspace.  Device memory must belong to the current device (the one
+ *   cudaSetDevice selected in the calling thread): memory of another GPU is
+ *   rejected with GS_EINVAL, because this device's kernels cannot safely
+ *   read it.  The caller owns every array; the library never keeps a pointer
+ *   past the call.
  * Memory: every GPU that loads the library holds the static array until the
  *   process exits.
  * Set-up: the first call on each device looks up the array's device address
@@ -482,6 +489,18 @@ void gs_release_workspace(void);
 /* Library ABI version: 100 * major + minor (101: gs_params gained
  * integrator and kinetic_at; 102: dim; 103: gs_server_config.schedule;
  * 104: gs_set_step_table; 105: gs_step_config). */
+/*
+ * gs_pointer_rule — diagnostics (no counterpart in the paper): the rule by
+ * which every entry point treats a caller's array, given the
+ * cudaPointerAttributes fields `type` (cudaMemoryType: 0 unregistered host,
+ * 1 host, 2 device, 3 managed) and `device`, and the current device's
+ * ordinal.  Returns 0 = host memory (staged through the workspace), 1 = used
+ * in place (device memory of the current device, or managed memory),
+ * 2 = rejected with GS_EINVAL (device memory of another GPU).  Makes no CUDA
+ * call.
+ */
+int32_t gs_pointer_rule(int32_t type, int32_t ptr_device, int32_t current_device);
+
 int32_t gs_version(void);
 
 #ifdef __cplusplus

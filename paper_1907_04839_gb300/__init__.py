@@ -13,6 +13,7 @@ take planar landmarks as (N, 2).  Two forms are accepted:
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 
 import numpy as np
@@ -57,6 +58,14 @@ class _Marshal:
             self.stream = ctypes.c_void_p(0)
         self.n = n
         self.dim = dim
+
+    def guard(self):
+        """The device of the call's tensors made current while the library
+        runs: the library uses the current device's workspace and rejects
+        another GPU's memory."""
+        if self.device:
+            return self.torch.cuda.device(self.dev)
+        return contextlib.nullcontext()
 
     def inp(self, x, name, rows=None):
         """Pointer to x as (rows, dim) FP32; rows defaults to the call's N."""
@@ -116,7 +125,8 @@ def step_forward(q, p, sigma):
     pq, pp = m.inp(q, "q"), m.inp(p, "p")
     Hq, oq = m.out()
     Hp, op = m.out()
-    check(load().step_forward(m.n, float(sigma), pq, pp, oq, op, m.stream))
+    with m.guard():
+        check(load().step_forward(m.n, float(sigma), pq, pp, oq, op, m.stream))
     return Hq, Hp
 
 
@@ -127,7 +137,8 @@ def velocity_field(q, p, x, sigma):
     rows = int(x.shape[0])
     px = m.inp(x, "x", rows=rows)
     v, pv = m.out(rows=rows)
-    check(load().velocity_field(m.n, rows, float(sigma), pq, pp, px, pv, m.stream))
+    with m.guard():
+        check(load().velocity_field(m.n, rows, float(sigma), pq, pp, px, pv, m.stream))
     return v
 
 
@@ -141,7 +152,8 @@ def flow_points(q0, p0, x0, T, sigma):
     px = m.inp(x0, "x0", rows=rows)
     x1, p1 = m.out(rows=rows)
     prm = _params(m.n, T, sigma)
-    check(load().flow_points(ctypes.byref(prm), pq, pp, rows, px, p1, m.stream))
+    with m.guard():
+        check(load().flow_points(ctypes.byref(prm), pq, pp, rows, px, p1, m.stream))
     return x1
 
 
@@ -152,7 +164,8 @@ def step_backward(q, p, alpha, beta, sigma):
     pq, pp, pa, pb = m.inp(q, "q"), m.inp(p, "p"), m.inp(alpha, "alpha"), m.inp(beta, "beta")
     da, oa = m.out()
     db, ob = m.out()
-    check(load().step_backward(m.n, float(sigma), pq, pp, pa, pb, oa, ob, m.stream))
+    with m.guard():
+        check(load().step_backward(m.n, float(sigma), pq, pp, pa, pb, oa, ob, m.stream))
     return da, db
 
 
@@ -165,7 +178,8 @@ def shoot_forward(q0, p0, T, sigma, integrator="euler"):
     q1, o1 = m.out()
     p1, o2 = m.out()
     h0 = ctypes.c_double(0.0)
-    check(load().shoot_forward(ctypes.byref(prm), pq, pp, o1, o2, ctypes.byref(h0), m.stream))
+    with m.guard():
+        check(load().shoot_forward(ctypes.byref(prm), pq, pp, o1, o2, ctypes.byref(h0), m.stream))
     return q1, p1, h0.value
 
 
@@ -180,7 +194,8 @@ def shoot_gradient(q0, p0, target, T, sigma, lam, ckpt_every=0, integrator="eule
     gp, og = m.out()
     gq, oq = m.out()
     loss = ctypes.c_double(0.0)
-    check(load().shoot_gradient(ctypes.byref(prm), pq, pp, pt, ctypes.byref(loss), og, oq, m.stream))
+    with m.guard():
+        check(load().shoot_gradient(ctypes.byref(prm), pq, pp, pt, ctypes.byref(loss), og, oq, m.stream))
     return loss.value, gp, gq
 
 
@@ -248,7 +263,8 @@ def register(q0, target, T, sigma, lam, p0=None, m=10, max_iter=100, grad_tol=1e
         raise ValueError("p0: expected shape (%d, %d)" % (m_.n, m_.dim))
     prm = _params(m_.n, T, sigma, lam, 0, m, max_iter, grad_tol, integrator, h_at, m_.dim)
     info = GsRegisterInfo()
-    check(load().register_landmarks(ctypes.byref(prm), pq, pt, pp, ctypes.byref(info), m_.stream))
+    with m_.guard():
+        check(load().register_landmarks(ctypes.byref(prm), pq, pt, pp, ctypes.byref(info), m_.stream))
     return pout, info.as_dict()
 
 

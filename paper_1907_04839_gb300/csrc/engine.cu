@@ -128,14 +128,33 @@ gs_status ensure_clean(Workspace& w, int n, cudaStream_t st, int dim) {
   return GS_OK;
 }
 
-bool is_device_ptr(const void* p) {
+PtrKind classify_pointer(int type, int ptr_device, int current_device) {
+  if (type == cudaMemoryTypeManaged) return kPtrDevice;  // migrates to whichever GPU touches it
+  if (type != cudaMemoryTypeDevice) return kPtrHost;
+  return ptr_device == current_device ? kPtrDevice : kPtrOtherDevice;
+}
+
+PtrKind pointer_kind(const void* p) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return kPtrHost;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  int cur = 0;
+  if (cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    return kPtrOtherDevice;
+  }
+  return classify_pointer(static_cast<int>(at.type), at.device, cur);
 }
+
+bool is_device_ptr(const void* p) { return pointer_kind(p) == kPtrDevice; }
+
+namespace {
+gs_status other_device() {
+  return fail(GS_EINVAL, "an array lives on another GPU than the current device: make its device current");
+}
+}  // namespace
 
 // Device view of a caller input array: the pointer itself, or a staged copy.
 gs_status stage_in(const float* src, float* staging, size_t n3, cudaStream_t st, const float** dev, bool* host) {
@@ -143,7 +162,9 @@ gs_status stage_in(const float* src, float* staging, size_t n3, cudaStream_t st,
     *dev = nullptr;
     return GS_OK;
   }
-  if (is_device_ptr(src)) {
+  const PtrKind kind = pointer_kind(src);
+  if (kind == kPtrOtherDevice) return other_device();
+  if (kind == kPtrDevice) {
     *dev = src;
     return GS_OK;
   }
@@ -155,7 +176,9 @@ gs_status stage_in(const float* src, float* staging, size_t n3, cudaStream_t st,
 
 gs_status copy_out(float* dst, const float* src, size_t n3, cudaStream_t st, bool* host) {
   if (!dst) return GS_OK;
-  const bool dev = is_device_ptr(dst);
+  const PtrKind kind = pointer_kind(dst);
+  if (kind == kPtrOtherDevice) return other_device();
+  const bool dev = kind == kPtrDevice;
   if (!dev) *host = true;
   GS_CUDA(cudaMemcpyAsync(dst, src, n3 * sizeof(float), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   return GS_OK;
@@ -307,7 +330,8 @@ gs_status enqueue_steps(Workspace& w, int kind, int n, int T, double sigma, doub
   const StepConfig fc = choose_step_config(0, npad, w.num_sms, variants);
   const StepConfig bc = choose_step_config(1, npad, w.num_sms, variants);
   if (fc.threads == 0 || bc.threads == 0) return fail(GS_EINVAL, "no step kernel configuration");
-  const int ftrig = late_trigger_for(0, fc) ? 1 : 0, btrig = late_trigger_for(1, bc) ? 1 : 0;
+  const int ftrig = late_trigger_for(0, fc, dim, integ == GS_RK4) ? 1 : 0;
+  const int btrig = late_trigger_for(1, bc, dim, integ == GS_RK4) ? 1 : 0;
   const int S = stages_of(integ);
   const size_t n3 = static_cast<size_t>(dim) * n;  // FP64 state per checkpoint array
   if (ev) GS_CUDA(cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal));
@@ -914,6 +938,10 @@ void gs_release_workspace(void) {
     cudaSetDevice(cur);
   }
   gs::g_ws.clear();
+}
+
+int32_t gs_pointer_rule(int32_t type, int32_t ptr_device, int32_t current_device) {
+  return static_cast<int32_t>(gs::classify_pointer(type, ptr_device, current_device));
 }
 
 int32_t gs_version(void) { return 105; }

@@ -134,6 +134,8 @@ gs_status get_workspace(Workspace** out);
 // FP64 state checkpoints.
 gs_status reserve(Workspace& w, int npad, int T, int splits, int nck = 0);
 gs_status ensure_clean(Workspace& w, int n, cudaStream_t st, int dim = 3);
+// True for memory the current device can use in place: its own device
+// memory or managed memory.
 bool is_device_ptr(const void* p);
 gs_status stage_in(const float* src, float* staging, size_t n3, cudaStream_t st, const float** dev, bool* host);
 gs_status copy_out(float* dst, const float* src, size_t n3, cudaStream_t st, bool* host);

@@ -90,6 +90,17 @@ PairConfig choose_forward_config_capped(int npad, int num_sms, int max_splits);
 // Record the calling thread's error message (returned by gs_last_error).
 void set_last_error(const char* msg);
 
+// Where a caller's array lives, as the current device sees it.  Host memory
+// (pageable or pinned) is staged through a device buffer; device memory of
+// the current GPU and managed memory are used in place; device memory of
+// another GPU is rejected, because a kernel of this device reading it
+// faults unless peer access happens to be enabled.
+enum PtrKind { kPtrHost = 0, kPtrDevice = 1, kPtrOtherDevice = 2 };
+// The rule itself, from cudaPointerAttributes::type and ::device and the
+// current device's ordinal (no CUDA call).
+PtrKind classify_pointer(int type, int ptr_device, int current_device);
+PtrKind pointer_kind(const void* p);
+
 cudaError_t launch_pair_forward(const PairConfig& cfg, const PairFwdArgs& a, cudaStream_t st, bool pdl);
 cudaError_t launch_pair_backward(const PairConfig& cfg, const PairBwdArgs& a, cudaStream_t st, bool pdl);
 
@@ -213,13 +224,20 @@ void set_late_trigger(int mode);
 // Whether choose_step_config reads the measured step-configuration table.
 void set_step_table(bool on);
 // Whether a single-problem step launch of configuration c (kind 0 forward,
-// 1 reverse) triggers the next launch after its pair sums.
-bool late_trigger_for(int kind, const StepConfig& c);
+// 1 reverse; dim 3 or 2; rk: RK4 stages) triggers the next launch after its
+// pair sums.
+bool late_trigger_for(int kind, const StepConfig& c, int dim, bool rk);
 // The policy for a launch of `ctas` CTAs on `num_sms` SMs: load balancing
 // when the grid is at least 1.5 waves of 8 CTAs per SM, else spread.
 int policy_for_grid(long long ctas, int num_sms);
 // cudaOccupancyMaxActiveClusters of a single-problem step kernel variant.
 cudaError_t max_active_clusters(int kind, int threads, int R, int groups, int cluster, int* out);
+// The kernel instantiation a launch of configuration cfg runs (null: none
+// compiled).  variants: RK4 stages or the terminal launch; rk: RK4 stages.
+using FwdKernel = void (*)(StepFwdArgs);
+using BwdKernel = void (*)(StepBwdArgs);
+FwdKernel forward_kernel_for(const StepConfig& cfg, int dim, bool variants);
+BwdKernel backward_kernel_for(const StepConfig& cfg, int dim, bool rk);
 cudaError_t launch_step_forward(const StepConfig& cfg, const StepFwdArgs& a, cudaStream_t st, bool pdl);
 cudaError_t launch_step_backward(const StepConfig& cfg, const StepBwdArgs& a, cudaStream_t st, bool pdl);
 // One launch over `items` (problem, tile) items; cfg gives the kernel variant

@@ -80,14 +80,9 @@ gs_status scratch_for_current_device(unsigned char** out, int* num_sms) {
   return GS_OK;
 }
 
-bool on_device(const void* p) {
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
+// Device memory of the current GPU, or managed memory (another GPU's
+// memory and host memory are refused).
+bool on_device(const void* p) { return pointer_kind(p) == kPtrDevice; }
 
 gs_status cuda_fail(cudaError_t e) {
   set_last_error(cudaGetErrorString(e));
@@ -110,7 +105,7 @@ extern "C" gs_status step_forward_noalloc(int64_t N, double sigma, const float* 
     return GS_EINVAL;
   }
   if (!q || !p || !Hq || !Hp || !on_device(q) || !on_device(p) || !on_device(Hq) || !on_device(Hp)) {
-    set_last_error("step_forward_noalloc: q, p, Hq and Hp must be device arrays");
+    set_last_error("step_forward_noalloc: q, p, Hq and Hp must be device arrays of the current GPU");
     return GS_EINVAL;
   }
   unsigned char* base = nullptr;

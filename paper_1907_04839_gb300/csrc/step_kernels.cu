@@ -679,21 +679,26 @@ void set_cluster_policy(int policy) { g_cluster_policy = policy; }
 namespace {
 int g_late_trigger = -1;
 std::mutex g_res_mu;
-std::map<std::pair<int, int>, int> g_resident;  // (device, configuration) -> resident CTAs of the plain kernel
+// ((device, kernel), cluster size) -> CTAs of that kernel resident at once
+std::map<std::pair<std::pair<int, const void*>, int>, int> g_resident;
 }  // namespace
 
 void set_late_trigger(int mode) { g_late_trigger = mode; }
 
-bool late_trigger_for(int kind, const StepConfig& c) {
+bool late_trigger_for(int kind, const StepConfig& c, int dim, bool rk) {
   if (g_late_trigger >= 0) return g_late_trigger == 1;
   // The library's rule, from GB300 measurements of gradient graphs
   // (N = 2048..16384): reverse steps whose CTAs are all resident at once
   // trigger (-1.7% reverse-sweep time at N = 4096); forward steps never
-  // (+13% forward-sweep time at N = 4096 with the trigger).
+  // (+13% forward-sweep time at N = 4096 with the trigger).  Residency is
+  // that of the instantiation the launch runs (the uneven-cluster, RK4 and
+  // planar kernels differ in registers and shared memory).
   if (kind != 1) return false;
+  const BwdKernel kern = backward_kernel_for(c, dim, rk);
+  if (!kern) return false;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
-  const auto key = std::make_pair(dev * 1000000 + kind * 100000 + c.threads * 100 + c.R, c.cluster * 16 + c.groups);
+  const auto key = std::make_pair(std::make_pair(dev, reinterpret_cast<const void*>(kern)), c.cluster);
   int resident = -1;
   {
     std::lock_guard<std::mutex> lk(g_res_mu);
@@ -702,7 +707,10 @@ bool late_trigger_for(int kind, const StepConfig& c) {
   }
   if (resident < 0) {
     int clusters = 0;
-    if (max_active_clusters(kind, c.threads, c.R, c.groups, c.cluster, &clusters) != cudaSuccess) clusters = 0;
+    if (occupancy_clusters(kern, c.threads, c.cluster, &clusters) != cudaSuccess) {
+      cudaGetLastError();
+      clusters = 0;
+    }
     resident = clusters * c.cluster;
     std::lock_guard<std::mutex> lk(g_res_mu);
     g_resident[key] = resident;
@@ -851,58 +859,62 @@ cudaError_t launch_bstep_backward(const StepConfig& c, int items, const StepBwdA
   return cudaErrorInvalidValue;
 }
 
-// Launches of the variants (RK4 stages, the terminal launch) go to the
-// V = true instantiation of the built-in configuration's kernel variant.
-cudaError_t launch_step_forward(const StepConfig& c, const StepFwdArgs& a, cudaStream_t st, bool pdl) {
-  if (a.dim == 2) {  // planar landmarks: the built-in configuration only
-    if (c.threads != kVarFwdThreads || c.R != 1 || c.groups != 1) return cudaErrorNotSupported;
-    if (a.rk || a.terminal) return launch_cluster(k_step_forward<kVarFwdThreads, 1, 1, true, 2>, c, a, st, pdl);
-    return launch_cluster(k_step_forward<kVarFwdThreads, 1, 1, false, 2>, c, a, st, pdl);
+// The instantiation that runs a launch of configuration c.  The variants
+// (RK4 stages, the terminal launch) go to the V = true instantiation of the
+// built-in configuration's kernel variant; planar landmarks (dim 2) to the
+// D = 2 instantiations of that variant.  Null: no instantiation exists.
+FwdKernel forward_kernel_for(const StepConfig& c, int dim, bool variants) {
+  if (dim == 2) {  // planar landmarks: the built-in configuration only
+    if (c.threads != kVarFwdThreads || c.R != 1 || c.groups != 1) return nullptr;
+    return variants ? k_step_forward<kVarFwdThreads, 1, 1, true, 2> : k_step_forward<kVarFwdThreads, 1, 1, false, 2>;
   }
-  if (a.rk || a.terminal) {
-    if (c.threads == kVarFwdThreads && c.R == 1 && c.groups == 1)
-      return launch_cluster(k_step_forward<kVarFwdThreads, 1, 1, true>, c, a, st, pdl);
-    return cudaErrorNotSupported;
+  if (variants) {
+    if (c.threads == kVarFwdThreads && c.R == 1 && c.groups == 1) return k_step_forward<kVarFwdThreads, 1, 1, true>;
+    return nullptr;
   }
 #define X(T_, R_, W_) \
-  if (c.threads == T_ && c.R == R_ && c.groups == W_) \
-    return launch_cluster(k_step_forward<T_, R_, W_, false>, c, a, st, pdl);
+  if (c.threads == T_ && c.R == R_ && c.groups == W_) return k_step_forward<T_, R_, W_, false>;
   GS_STEP_FWD_CASES(X)
 #undef X
-  return cudaErrorInvalidValue;
+  return nullptr;
+}
+
+BwdKernel backward_kernel_for(const StepConfig& c, int dim, bool rk) {
+  if ((c.threads / c.groups * c.R) % c.cluster != 0) {  // the instantiations for clusters that do not divide the tile
+    if (c.R != 1 || c.groups != 1 || (c.threads != 32 && c.threads != kVarBwdThreads)) return nullptr;
+    if (dim == 2) {
+      if (c.threads != kVarBwdThreads) return nullptr;
+      return rk ? k_step_backward<kVarBwdThreads, 1, 1, true, 2, true> : k_step_backward<kVarBwdThreads, 1, 1, false, 2, true>;
+    }
+    if (rk) return c.threads == kVarBwdThreads ? k_step_backward<kVarBwdThreads, 1, 1, true, 3, true> : nullptr;
+    if (c.threads == 32) return k_step_backward<32, 1, 1, false, 3, true>;
+    return k_step_backward<kVarBwdThreads, 1, 1, false, 3, true>;
+  }
+  if (dim == 2) {
+    if (c.threads != kVarBwdThreads || c.R != 1 || c.groups != 1) return nullptr;
+    return rk ? k_step_backward<kVarBwdThreads, 1, 1, true, 2> : k_step_backward<kVarBwdThreads, 1, 1, false, 2>;
+  }
+  if (rk) {
+    if (c.threads == kVarBwdThreads && c.R == 1 && c.groups == 1) return k_step_backward<kVarBwdThreads, 1, 1, true>;
+    return nullptr;
+  }
+#define X(T_, R_, W_) \
+  if (c.threads == T_ && c.R == R_ && c.groups == W_) return k_step_backward<T_, R_, W_, false>;
+  GS_STEP_BWD_CASES(X)
+#undef X
+  return nullptr;
+}
+
+cudaError_t launch_step_forward(const StepConfig& c, const StepFwdArgs& a, cudaStream_t st, bool pdl) {
+  const FwdKernel k = forward_kernel_for(c, a.dim, a.rk || a.terminal);
+  if (!k) return cudaErrorNotSupported;
+  return launch_cluster(k, c, a, st, pdl);
 }
 
 cudaError_t launch_step_backward(const StepConfig& c, const StepBwdArgs& a, cudaStream_t st, bool pdl) {
-  if ((c.threads / c.groups * c.R) % c.cluster != 0) {  // the instantiations for clusters that do not divide the tile
-    if (c.R != 1 || c.groups != 1 || (c.threads != 32 && c.threads != kVarBwdThreads)) return cudaErrorNotSupported;
-    if (a.dim == 2) {
-      if (c.threads != kVarBwdThreads) return cudaErrorNotSupported;
-      if (a.rk) return launch_cluster(k_step_backward<kVarBwdThreads, 1, 1, true, 2, true>, c, a, st, pdl);
-      return launch_cluster(k_step_backward<kVarBwdThreads, 1, 1, false, 2, true>, c, a, st, pdl);
-    }
-    if (a.rk) {
-      if (c.threads != kVarBwdThreads) return cudaErrorNotSupported;
-      return launch_cluster(k_step_backward<kVarBwdThreads, 1, 1, true, 3, true>, c, a, st, pdl);
-    }
-    if (c.threads == 32) return launch_cluster(k_step_backward<32, 1, 1, false, 3, true>, c, a, st, pdl);
-    return launch_cluster(k_step_backward<kVarBwdThreads, 1, 1, false, 3, true>, c, a, st, pdl);
-  }
-  if (a.dim == 2) {
-    if (c.threads != kVarBwdThreads || c.R != 1 || c.groups != 1) return cudaErrorNotSupported;
-    if (a.rk) return launch_cluster(k_step_backward<kVarBwdThreads, 1, 1, true, 2>, c, a, st, pdl);
-    return launch_cluster(k_step_backward<kVarBwdThreads, 1, 1, false, 2>, c, a, st, pdl);
-  }
-  if (a.rk) {
-    if (c.threads == kVarBwdThreads && c.R == 1 && c.groups == 1)
-      return launch_cluster(k_step_backward<kVarBwdThreads, 1, 1, true>, c, a, st, pdl);
-    return cudaErrorNotSupported;
-  }
-#define X(T_, R_, W_) \
-  if (c.threads == T_ && c.R == R_ && c.groups == W_) \
-    return launch_cluster(k_step_backward<T_, R_, W_, false>, c, a, st, pdl);
-  GS_STEP_BWD_CASES(X)
-#undef X
-  return cudaErrorInvalidValue;
+  const BwdKernel k = backward_kernel_for(c, a.dim, a.rk != 0);
+  if (!k) return cudaErrorNotSupported;
+  return launch_cluster(k, c, a, st, pdl);
 }
 
 }  // namespace gs

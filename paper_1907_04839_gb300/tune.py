@@ -209,7 +209,10 @@ def emit_table(lib, dev, sms, stream, path, sigma, instances=1):
                 _lib.check(lib.gs_set_step_config(other, fixed[other][0], 1, 1, fixed[other][1]))
                 for nt in shapes:
                     for c in TABLE_CLUSTERS:
-                        if c > TABLE_BWD[0] or c > npad // 8:
+                        # the rule step_config_for applies: at most one CTA of
+                        # the cluster per target of the tile (M = nt with one
+                        # target per thread) and at least 8 sources per CTA
+                        if c > nt or c > npad // 8:
                             continue
                         apply = lambda: _lib.check(lib.gs_set_step_config(kind, nt, 1, 1, c))
                         apply()

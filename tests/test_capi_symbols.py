@@ -243,3 +243,20 @@ def test_step_config_rejects_bad_arguments():
     assert lib.gs_step_config(0, 0, 152, 0, ctypes.byref(t), ctypes.byref(c)) == -1
     assert lib.gs_step_config(0, (1 << 26) + 1, 152, 0, ctypes.byref(t), ctypes.byref(c)) == -1
     assert lib.gs_step_config(0, 100, 152, 0, None, ctypes.byref(c)) == -1
+
+
+@pytest.mark.parametrize("mtype,ptr_dev,cur,want", [
+    (0, -2, 0, 0),   # unregistered host memory: staged
+    (1, 0, 0, 0),    # pinned host memory: staged
+    (2, 0, 0, 1),    # device memory of the current GPU: used in place
+    (2, 3, 3, 1),
+    (2, 1, 0, 2),    # device memory of another GPU: rejected
+    (2, 0, 5, 2),
+    (3, 1, 0, 1),    # managed memory: used in place on any GPU
+])
+def test_pointer_rule_rejects_another_gpus_memory(mtype, ptr_dev, cur, want):
+    # The rule every entry point applies to a caller's array, checked
+    # without a GPU: memory of another device than the current one must be
+    # refused, not handed to this device's kernels.
+    import paper_1907_04839_gb300 as gsh
+    assert gsh.load().gs_pointer_rule(mtype, ptr_dev, cur) == want

@@ -486,9 +486,23 @@ const char* gs_last_error(void);
 /* Free the device workspace and cached CUDA graphs of every device. */
 void gs_release_workspace(void);
 
-/* Library ABI version: 100 * major + minor (101: gs_params gained
- * integrator and kinetic_at; 102: dim; 103: gs_server_config.schedule;
- * 104: gs_set_step_table; 105: gs_step_config). */
+/*
+ * gs_measure_peaks — diagnostics (no counterpart in the paper): measured
+ * throughput of the arithmetic units that bound the pair kernels, on the
+ * current device.  Each unit runs 8 independent dependency chains per
+ * thread, 4 CTAs of 256 threads per SM, for about target_ms (1 to 2000) per
+ * launch; the best of three launches timed with CUDA events on `stream`
+ * counts.  rates (4 doubles, host):
+ *   [0] scalar FP32 FFMA, TFLOP/s (2 flops per FMA);
+ *   [1] paired FP32 FFMA2 (f32x2), TFLOP/s (2 flops per lane);
+ *   [2] MUFU ex2.approx.ftz.f32 results per second;
+ *   [3] FP64 DFMA, TFLOP/s.
+ * ms_out (4 doubles, host, may be NULL): the kernel times behind them.
+ * Synchronises `stream`.  GS_EINVAL for a NULL rates or target_ms outside
+ * [1, 2000].
+ */
+gs_status gs_measure_peaks(double* rates, double* ms_out, double target_ms, void* stream);
+
 /*
  * gs_pointer_rule — diagnostics (no counterpart in the paper): the rule by
  * which every entry point treats a caller's array, given the
@@ -501,6 +515,30 @@ void gs_release_workspace(void);
  */
 int32_t gs_pointer_rule(int32_t type, int32_t ptr_device, int32_t current_device);
 
+/*
+ * gs_set_sweep_mode — tuning (no counterpart in the paper): whether a plain
+ * sweep (Euler steps of 3-D landmarks, no checkpoints) runs as one
+ * persistent launch that walks all T time steps, its clusters meeting at a
+ * grid-wide barrier between steps, instead of one launch per step.  mode -1
+ * (the initial state) or 1: persistent wherever every cluster of the
+ * sweep's configuration is resident on the device at once; 0: one launch
+ * per step.  Each time step is computed by the same configuration either
+ * way, and the results are bitwise the same.  Clears the cached graphs.
+ * GS_EINVAL for another mode.
+ *
+ * gs_sweep_persistent — diagnostics: *persistent = 1 if the forward
+ * (kind 0) or reverse (kind 1) sweep of a plain gradient at N landmarks
+ * runs as one persistent launch on the current device under the current
+ * settings, else 0.  GS_EINVAL for a bad kind, N outside [1, 2^26] or a
+ * NULL output.
+ */
+gs_status gs_set_sweep_mode(int32_t mode);
+gs_status gs_sweep_persistent(int32_t kind, int64_t N, int32_t* persistent);
+
+/* Library ABI version: 100 * major + minor (101: gs_params gained
+ * integrator and kinetic_at; 102: dim; 103: gs_server_config.schedule;
+ * 104: gs_set_step_table; 105: gs_step_config; 106: gs_pointer_rule,
+ * gs_measure_peaks, gs_set_sweep_mode, gs_sweep_persistent). */
 int32_t gs_version(void);
 
 #ifdef __cplusplus

@@ -1,0 +1,162 @@
+// Measured throughput of the arithmetic units the pair kernels run on.
+//
+// The roofline of the pair-sum kernels is the FP32 pipe (they issue paired
+// f32x2 FMA/ADD/MUL instructions), with the MUFU unit (one ex2 per pair)
+// second; the FP64 unit serves the state updates.  Nominal unit counts times
+// the clock give a derived peak, and this file measures the same rates on
+// the device the library runs on, so that a fraction of peak rests on a
+// measurement:
+//   * FFMA:  scalar FP32 fused multiply-add, 2 flops each;
+//   * FFMA2: the paired form (one instruction, two lanes), 2 flops per lane;
+//   * EX2:   MUFU ex2.approx.ftz.f32, results per second;
+//   * DFMA:  FP64 fused multiply-add, 2 flops each.
+// Each kernel runs CH independent dependency chains per thread on every SM
+// (4 CTAs of 256 threads per SM: 8 warps per scheduler), long enough (about
+// 50 ms) that launch overhead does not count, and is timed with CUDA events
+// on the caller's stream.  The best of three timed launches is reported.
+#include <cmath>
+
+#include "engine.h"
+#include "gs_device.cuh"
+
+namespace gs {
+namespace {
+
+constexpr int kPeakThreads = 256;
+constexpr int kPeakCtasPerSm = 4;
+constexpr int kChains = 8;
+constexpr int kInner = 16;  // chain steps per loop iteration
+
+// x <- x*a + b converges to b/(1-a) and never leaves the normal range, so
+// every operation is a full-rate one.  The final test is never true for
+// these constants, but the compiler cannot know it, so no chain is dead.
+__global__ void __launch_bounds__(kPeakThreads) k_peak_ffma(int iters, float a, float b, float* sink) {
+  float x[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) x[c] = 1e-3f * threadIdx.x + c;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < kInner; ++u)
+#pragma unroll
+      for (int c = 0; c < kChains; ++c) x[c] = __fmaf_rn(x[c], a, b);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += x[c];
+  if (s == -1.0f) sink[0] = s;
+}
+
+__global__ void __launch_bounds__(kPeakThreads) k_peak_ffma2(int iters, float a, float b, float* sink) {
+  float2 x[kChains];
+  const float2 a2 = make_float2(a, a), b2 = make_float2(b, b);
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) x[c] = make_float2(1e-3f * threadIdx.x + c, 2e-3f * threadIdx.x - c);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < kInner; ++u)
+#pragma unroll
+      for (int c = 0; c < kChains; ++c) x[c] = __ffma2_rn(x[c], a2, b2);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += x[c].x + x[c].y;
+  if (s == -1.0f) sink[0] = s;
+}
+
+// y <- 2^-y stays in [0.5, 1] for y in [0, 1].
+__global__ void __launch_bounds__(kPeakThreads) k_peak_ex2(int iters, float* sink) {
+  float y[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) y[c] = 0.1f * c + 1e-4f * threadIdx.x;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < kInner; ++u)
+#pragma unroll
+      for (int c = 0; c < kChains; ++c) y[c] = ex2_approx(-y[c]);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += y[c];
+  if (s == -1.0f) sink[0] = s;
+}
+
+__global__ void __launch_bounds__(kPeakThreads) k_peak_dfma(int iters, double a, double b, float* sink) {
+  double x[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) x[c] = 1e-3 * threadIdx.x + c;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < kInner; ++u)
+#pragma unroll
+      for (int c = 0; c < kChains; ++c) x[c] = __fma_rn(x[c], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += x[c];
+  if (s == -1.0) sink[0] = static_cast<float>(s);
+}
+
+// One launch of unit `which` with `iters` loop iterations; returns its
+// device time in ms.
+gs_status time_unit(int which, int iters, int blocks, float* sink, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1,
+                    float* ms) {
+  GS_CUDA(cudaEventRecord(e0, st));
+  switch (which) {
+    case 0: k_peak_ffma<<<blocks, kPeakThreads, 0, st>>>(iters, 0.9999f, 1e-4f, sink); break;
+    case 1: k_peak_ffma2<<<blocks, kPeakThreads, 0, st>>>(iters, 0.9999f, 1e-4f, sink); break;
+    case 2: k_peak_ex2<<<blocks, kPeakThreads, 0, st>>>(iters, sink); break;
+    default: k_peak_dfma<<<blocks, kPeakThreads, 0, st>>>(iters, 0.9999, 1e-4, sink); break;
+  }
+  GS_CUDA(cudaGetLastError());
+  GS_CUDA(cudaEventRecord(e1, st));
+  GS_CUDA(cudaEventSynchronize(e1));
+  GS_CUDA(cudaEventElapsedTime(ms, e0, e1));
+  return GS_OK;
+}
+
+}  // namespace
+}  // namespace gs
+
+extern "C" gs_status gs_measure_peaks(double* rates, double* ms_out, double target_ms, void* stream) {
+  using namespace gs;
+  set_last_error("");
+  if (!rates) return fail(GS_EINVAL, "rates is NULL");
+  if (!(target_ms >= 1.0 && target_ms <= 2000.0)) return fail(GS_EINVAL, "target_ms must be in [1, 2000]");
+  std::lock_guard<std::mutex> lk(engine_mutex());
+  Workspace* w = nullptr;
+  gs_status s = get_workspace(&w);
+  if (s != GS_OK) return s;
+  if ((s = reserve(*w, kPad, 1, 1)) != GS_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int blocks = w->num_sms * kPeakCtasPerSm;
+  // The sink is a workspace word no kernel reads; the kernels never write it.
+  float* sink = reinterpret_cast<float*>(w->status + 5);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  GS_CUDA(cudaEventCreate(&e0));
+  GS_CUDA(cudaEventCreate(&e1));
+  for (int which = 0; which < 4 && s == GS_OK; ++which) {
+    // Calibrate the iteration count to about target_ms, then keep the best
+    // of three launches.
+    int iters = which == 3 ? 64 : 2048;
+    float ms = 0.f;
+    for (int probe = 0; probe < 4 && s == GS_OK; ++probe) {
+      s = time_unit(which, iters, blocks, sink, st, e0, e1, &ms);
+      if (s != GS_OK || ms >= 0.5 * target_ms) break;
+      const double scale = ms > 0.01 ? target_ms / ms : 64.0;
+      iters = static_cast<int>(std::fmin(1e9, std::ceil(iters * std::fmin(scale, 64.0))));
+    }
+    float best = 1e30f;
+    for (int r = 0; r < 3 && s == GS_OK; ++r) {
+      s = time_unit(which, iters, blocks, sink, st, e0, e1, &ms);
+      best = std::fmin(best, ms);
+    }
+    if (s != GS_OK) break;
+    const double ops = static_cast<double>(blocks) * kPeakThreads * iters * kInner * kChains * (which == 1 ? 2 : 1);
+    const double per_s = ops / (best * 1e-3);
+    rates[which] = which == 2 ? per_s : 2.0 * per_s * 1e-12;  // TFLOP/s, or ex2 results per second
+    if (ms_out) ms_out[which] = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return s;
+}

@@ -486,6 +486,19 @@ const char* gs_last_error(void);
 /* Free the device workspace and cached CUDA graphs of every device. */
 void gs_release_workspace(void);
 
+
+/*
+ * gs_pointer_rule — diagnostics (no counterpart in the paper): the rule by
+ * which every entry point treats a caller's array, given the
+ * cudaPointerAttributes fields `type` (cudaMemoryType: 0 unregistered host,
+ * 1 host, 2 device, 3 managed) and `device`, and the current device's
+ * ordinal.  Returns 0 = host memory (staged through the workspace), 1 = used
+ * in place (device memory of the current device, or managed memory),
+ * 2 = rejected with GS_EINVAL (device memory of another GPU).  Makes no CUDA
+ * call.
+ */
+int32_t gs_pointer_rule(int32_t type, int32_t ptr_device, int32_t current_device);
+
 /*
  * gs_measure_peaks — diagnostics (no counterpart in the paper): measured
  * throughput of the arithmetic units that bound the pair kernels, on the
@@ -503,42 +516,10 @@ void gs_release_workspace(void);
  */
 gs_status gs_measure_peaks(double* rates, double* ms_out, double target_ms, void* stream);
 
-/*
- * gs_pointer_rule — diagnostics (no counterpart in the paper): the rule by
- * which every entry point treats a caller's array, given the
- * cudaPointerAttributes fields `type` (cudaMemoryType: 0 unregistered host,
- * 1 host, 2 device, 3 managed) and `device`, and the current device's
- * ordinal.  Returns 0 = host memory (staged through the workspace), 1 = used
- * in place (device memory of the current device, or managed memory),
- * 2 = rejected with GS_EINVAL (device memory of another GPU).  Makes no CUDA
- * call.
- */
-int32_t gs_pointer_rule(int32_t type, int32_t ptr_device, int32_t current_device);
-
-/*
- * gs_set_sweep_mode — tuning (no counterpart in the paper): whether a plain
- * sweep (Euler steps of 3-D landmarks, no checkpoints) runs as one
- * persistent launch that walks all T time steps, its clusters meeting at a
- * grid-wide barrier between steps, instead of one launch per step.  mode -1
- * (the initial state) or 1: persistent wherever every cluster of the
- * sweep's configuration is resident on the device at once; 0: one launch
- * per step.  Each time step is computed by the same configuration either
- * way, and the results are bitwise the same.  Clears the cached graphs.
- * GS_EINVAL for another mode.
- *
- * gs_sweep_persistent — diagnostics: *persistent = 1 if the forward
- * (kind 0) or reverse (kind 1) sweep of a plain gradient at N landmarks
- * runs as one persistent launch on the current device under the current
- * settings, else 0.  GS_EINVAL for a bad kind, N outside [1, 2^26] or a
- * NULL output.
- */
-gs_status gs_set_sweep_mode(int32_t mode);
-gs_status gs_sweep_persistent(int32_t kind, int64_t N, int32_t* persistent);
-
 /* Library ABI version: 100 * major + minor (101: gs_params gained
  * integrator and kinetic_at; 102: dim; 103: gs_server_config.schedule;
  * 104: gs_set_step_table; 105: gs_step_config; 106: gs_pointer_rule,
- * gs_measure_peaks, gs_set_sweep_mode, gs_sweep_persistent). */
+ * gs_measure_peaks). */
 int32_t gs_version(void);
 
 #ifdef __cplusplus

@@ -19,7 +19,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgshoot.so")
 HEADER = os.path.join(ROOT, "include", "gshoot.h")
 
-SOURCES = ["pair_kernels.cu", "step_kernels.cu", "sweep_kernels.cu", "combine.cu", "engine.cu", "lbfgs.cu", "batch.cu", "noalloc.cu",
+SOURCES = ["pair_kernels.cu", "step_kernels.cu", "combine.cu", "engine.cu", "lbfgs.cu", "batch.cu", "noalloc.cu",
            "velocity.cu", "diag.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]

@@ -28,7 +28,7 @@ EXPORTS = [
     "gs_time_pair_kernels", "gs_time_pair_config", "gs_set_step_config", "step_forward_noalloc",
     "gs_set_phase_timing", "gs_phase_times", "gs_set_cluster_policy", "gs_max_active_clusters",
     "gs_set_late_trigger", "gs_check_wait_timeout", "gs_set_step_table", "gs_step_config",
-    "gs_pointer_rule", "gs_measure_peaks", "gs_set_sweep_mode", "gs_sweep_persistent",
+    "gs_pointer_rule", "gs_measure_peaks",
     "gs_last_error",
     "gs_release_workspace",
     "gs_version",
@@ -153,13 +153,14 @@ def _declare(lib):
                  "gs_time_pair_kernels",
                  "step_forward_noalloc", "gs_time_pair_config", "gs_set_step_config", "gs_set_phase_timing",
                  "gs_phase_times", "gs_set_cluster_policy", "gs_max_active_clusters", "gs_set_late_trigger",
-                 "gs_set_step_table", "gs_step_config", "gs_check_wait_timeout", "gs_measure_peaks",
-                 "gs_set_sweep_mode", "gs_sweep_persistent"):
+                 "gs_set_step_table", "gs_step_config", "gs_check_wait_timeout", "gs_measure_peaks"):
         getattr(lib, name).restype = ctypes.c_int
     lib.gs_last_error.restype = ctypes.c_char_p
     lib.gs_last_error.argtypes = []
     lib.gs_release_workspace.restype = None
     lib.gs_version.restype = i32
+    lib.gs_measure_peaks.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                     ctypes.c_double, ctypes.c_void_p]
     lib.gs_pointer_rule.restype = i32
     lib.gs_pointer_rule.argtypes = [i32, i32, i32]
 

@@ -304,46 +304,6 @@ StepBwdArgs backward_step_args(Workspace& w, const StepConfig& c, int n, int T, 
   return b;
 }
 
-// Arguments of a persistent sweep (kind 1: the forward sweep also forms the
-// loss, and the reverse sweep writes the gradient).
-SweepArgs sweep_args(Workspace& w, const StepConfig& c, int kind, int n, int T, double sigma, double lambda,
-                     unsigned* bar) {
-  const KernelScales sc = make_scales(sigma);
-  SweepArgs a;
-  std::memset(&a, 0, sizeof(a));
-  a.traj = w.traj;
-  a.adj = w.adj;
-  a.slot = static_cast<long long>(w.slot());
-  a.T = T;
-  a.n = n;
-  a.npad = round_up(n, kPad);
-  a.split_len = c.split_len;
-  a.kappa_f = static_cast<float>(sc.kappa);
-  a.kq_f = static_cast<float>(sc.kq);
-  a.kq = sc.kq;
-  a.kappa = sc.kappa;
-  a.dt = 1.0 / T;
-  a.lambda = lambda;
-  a.q64 = w.q64;
-  a.p64 = w.p64;
-  a.hp0 = w.hp0;
-  a.hq0 = w.hq0;
-  a.t64 = w.t64;
-  a.a64 = w.a64;
-  a.b64 = w.b64;
-  a.with_loss = kind == 1;
-  a.grad_p0 = w.out_a;
-  a.grad_q0 = w.out_b;
-  a.grad_p0_64 = w.gp64;
-  a.red_h = w.red_h;
-  a.red_m = w.red_m;
-  a.ticket = w.ticket;
-  a.scalars = w.scalars;
-  a.bar = bar;
-  a.status = w.status;
-  return a;
-}
-
 // Enqueue the T forward steps (and, for kind 1, the loss and T reverse
 // steps): one fused cluster kernel per time step, or per stage of an RK4
 // step (S = 4 launches per step; record slot S*k + s holds the state of
@@ -370,38 +330,11 @@ gs_status enqueue_steps(Workspace& w, int kind, int n, int T, double sigma, doub
   const StepConfig fc = choose_step_config(0, npad, w.num_sms, variants);
   const StepConfig bc = choose_step_config(1, npad, w.num_sms, variants);
   if (fc.threads == 0 || bc.threads == 0) return fail(GS_EINVAL, "no step kernel configuration");
-  // A plain Euler sweep of 3-D landmarks without checkpoints runs as one
-  // persistent launch per sweep where its clusters all fit on the device at
-  // once (sweep_kernels.cu).  Each kind decides on its own.
-  const bool plain = !variants && dim == 3 && ckpt == 0;
-  const bool fsweep = plain && sweep_fits(0, fc);
-  const bool bsweep = plain && kind == 1 && sweep_fits(1, bc);
-  if (fsweep || bsweep) GS_CUDA(cudaMemsetAsync(w.ticket + 2, 0, 2 * sizeof(unsigned), st));  // barrier counters
-  if (ev) GS_CUDA(cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal));
-  if (fsweep) {
-    GS_CUDA(launch_sweep_forward(fc, sweep_args(w, fc, kind, n, T, sigma, lambda, w.ticket + 2), st, false));
-    if (ev) GS_CUDA(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
-    if (kind == 0) {
-      if (ev) GS_CUDA(cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal));
-      return GS_OK;
-    }
-    if (bsweep) {
-      GS_CUDA(launch_sweep_backward(bc, sweep_args(w, bc, kind, n, T, sigma, lambda, w.ticket + 3), st, true));
-    } else {
-      const int btrig = late_trigger_for(1, bc, dim, false) ? 1 : 0;
-      for (int s = 0; s < T; ++s) {
-        StepBwdArgs b = backward_step_args(w, bc, n, T, s, sigma, -1, integ, h_end, dim);
-        b.late_trigger = s + 1 < T ? btrig : 0;
-        GS_CUDA(launch_step_backward(bc, b, st, true));
-      }
-    }
-    if (ev) GS_CUDA(cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal));
-    return GS_OK;
-  }
   const int ftrig = late_trigger_for(0, fc, dim, integ == GS_RK4) ? 1 : 0;
   const int btrig = late_trigger_for(1, bc, dim, integ == GS_RK4) ? 1 : 0;
   const int S = stages_of(integ);
   const size_t n3 = static_cast<size_t>(dim) * n;  // FP64 state per checkpoint array
+  if (ev) GS_CUDA(cudaEventRecordWithFlags(ev[0], st, cudaEventRecordExternal));
   for (int k = 0; k < T; ++k) {
     if (ckpt && k % ckpt == 0) {
       double* ck = w.ck64 + 2 * static_cast<size_t>(k / ckpt) * n3;
@@ -427,11 +360,6 @@ gs_status enqueue_steps(Workspace& w, int kind, int n, int T, double sigma, doub
   }
   if (ev) GS_CUDA(cudaEventRecordWithFlags(ev[1], st, cudaEventRecordExternal));
   if (kind == 0) {
-    if (ev) GS_CUDA(cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal));
-    return GS_OK;
-  }
-  if (bsweep) {
-    GS_CUDA(launch_sweep_backward(bc, sweep_args(w, bc, kind, n, T, sigma, lambda, w.ticket + 3), st, true));
     if (ev) GS_CUDA(cudaEventRecordWithFlags(ev[2], st, cudaEventRecordExternal));
     return GS_OK;
   }
@@ -1010,29 +938,6 @@ void gs_release_workspace(void) {
     cudaSetDevice(cur);
   }
   gs::g_ws.clear();
-}
-
-gs_status gs_set_sweep_mode(int32_t mode) {
-  gs::g_err.clear();
-  if (mode < -1 || mode > 1) return gs::fail(GS_EINVAL, "mode must be -1, 0 or 1");
-  std::lock_guard<std::mutex> lk(gs::g_mu);
-  gs::set_sweep_mode(mode);
-  for (auto& kv : gs::g_ws) kv.second->drop_graphs();
-  return GS_OK;
-}
-
-gs_status gs_sweep_persistent(int32_t kind, int64_t N, int32_t* persistent) {
-  gs::g_err.clear();
-  if (kind != 0 && kind != 1) return gs::fail(GS_EINVAL, "kind must be 0 (forward) or 1 (reverse)");
-  if (N < 1 || N > (1LL << 26)) return gs::fail(GS_EINVAL, "N must be in [1, 2^26]");
-  if (!persistent) return gs::fail(GS_EINVAL, "output pointer must not be NULL");
-  int dev = 0, sms = 0;
-  GS_CUDA(cudaGetDevice(&dev));
-  GS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  std::lock_guard<std::mutex> lk(gs::g_mu);
-  const gs::StepConfig c = gs::choose_step_config(kind, gs::round_up(N, gs::kPad), sms, false);
-  *persistent = c.threads != 0 && gs::sweep_fits(kind, c) ? 1 : 0;
-  return GS_OK;
 }
 
 int32_t gs_pointer_rule(int32_t type, int32_t ptr_device, int32_t current_device) {

@@ -187,52 +187,6 @@ struct StepBwdArgs {
   int late_trigger;    // trigger the next launch after the pair sums (pdl_trigger)
 };
 
-// ---------------------------------------------------------------- persistent sweeps
-// One launch runs every time step of a forward (or reverse) Euler sweep of a
-// 3-D problem.  Its clusters keep the roles of the per-step kernels (cluster
-// = target tile, CTA rank = source split, slice of the tile reduced per
-// CTA) through all T steps, keep the FP64 state of their slice in
-// registers, and meet at a grid-wide barrier between steps.  That needs
-// every cluster resident at once, which the host checks before it picks
-// this form (sweep_fits).
-struct SweepArgs {
-  float4* traj;        // QP record slots 0..T (slot k at traj + k * slot)
-  float4* adj;         // two AB record buffers (adj, adj + slot)
-  long long slot;      // float4 per record slot
-  int T, n, npad, split_len;
-  float kappa_f, kq_f;
-  double kq, kappa, dt, lambda;
-  double* q64;         // forward: state at step 0 in, state at step T out
-  double* p64;
-  double* hp0;         // forward: Hp, Hq at step 0 out; reverse: in
-  double* hq0;
-  const double* t64;   // target (with_loss)
-  double* a64;         // forward: adjoint initialisation out (with_loss);
-  double* b64;         // reverse: in, and the adjoint at step 0 out
-  int with_loss;       // forward: form the loss and the adjoint initialisation
-  float* grad_p0;      // reverse: gradient outputs (may be null)
-  float* grad_q0;
-  double* grad_p0_64;
-  double* red_h;       // per-CTA partial sums (grid-sized)
-  double* red_m;
-  unsigned* ticket;
-  double* scalars;     // [0] = H0, [1] = loss
-  unsigned* bar;       // grid-barrier counter, zero when the launch starts
-  unsigned* status;
-};
-// Whether a sweep (kind 0 forward, 1 reverse) in configuration c runs as one
-// persistent launch on the current device: a compiled shape (one target per
-// thread, one warp group, 64/128-thread CTAs forward and 32/64 reverse,
-// clusters of 4 to 16) whose clusters are all resident at once, and the
-// mode (set_sweep_mode) allows it.
-bool sweep_fits(int kind, const StepConfig& c);
-// -1: the library's rule (persistent wherever sweep_fits), 0: never (one
-// launch per step), 1: same as -1 (kept for symmetry with the other modes).
-void set_sweep_mode(int mode);
-int sweep_mode();
-cudaError_t launch_sweep_forward(const StepConfig& c, const SweepArgs& a, cudaStream_t st, bool pdl);
-cudaError_t launch_sweep_backward(const StepConfig& c, const SweepArgs& a, cudaStream_t st, bool pdl);
-
 // Packed batches of independent problems.  Problem b occupies landmarks
 // [off, off+npad) of every packed array; items are (problem, target tile).
 struct BatchProb {
@@ -264,7 +218,6 @@ bool set_step_override(int kind, int threads, int R, int groups, int cluster);
 // driver default, 1 spread, 2 load balancing), or -1: each configuration's
 // own policy.
 void set_cluster_policy(int policy);
-int forced_cluster_policy();  // -1: none forced
 // When step kernels trigger the next launch after their pair sums: -1 the
 // library's rule (reverse-step grids resident in one wave), 0 never, 1 always.
 void set_late_trigger(int mode);

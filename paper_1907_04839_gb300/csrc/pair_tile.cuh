@@ -58,14 +58,15 @@ __device__ __forceinline__ void pipe_init(Pipe& p, int warps) {
   fence_mbar_init();
 }
 
-// Issue the bulk copies of chunk c (NA record arrays) into stage s.  Source
-// offsets and lengths are even, so records are copied whole.
+// Issue the bulk copies of chunk c (NA record arrays) into stage c % kStages.
+// Source offsets and lengths are even, so records are copied whole.
 template <int NA, int D>
 __device__ __forceinline__ void issue_chunk(StageBuf<NA, D>& st, Pipe& pp, const float4* const* src, int j0, int j1,
-                                            int c, int s) {
+                                            int c) {
   const int off = j0 + c * kChunk;
   const int len = min(kChunk, j1 - off);
   const unsigned bytes = static_cast<unsigned>(len) * (16 * D / 2);
+  const int s = c % kStages;
   uint64_t* bar = &pp.full[s];
   mbar_arrive_expect_tx(bar, NA * bytes);
 #pragma unroll
@@ -80,28 +81,20 @@ __device__ __forceinline__ void issue_chunk(StageBuf<NA, D>& st, Pipe& pp, const
 // every warp has released it.  Returns false in every thread if a wait
 // expired; the expiry is recorded in *status, and every copy still in flight
 // has been waited for (bounded) before return.  Ends with a CTA barrier.
-//
-// base: chunks this CTA streamed through the same ring before (a kernel
-// that calls this once per time step passes the running count).  Chunk c
-// of this call is chunk base + c of the ring's life: it takes stage
-// (base + c) % kStages and phase ((base + c) / kStages) & 1 of that stage's
-// mbarriers, so the barriers need no re-initialisation between calls.
 template <int NA, int Groups = 1, int D = 3, class Tile>
 __device__ bool stream_sources(StageBuf<NA, D>& st, Pipe& pp, const float4* const* src, int j0, int j1, Tile& tile,
-                               unsigned* status, int group = 0, int base = 0) {
+                               unsigned* status, int group = 0) {
   const int tid = threadIdx.x;
   const int nch = j1 > j0 ? (j1 - j0 + kChunk - 1) / kChunk : 0;
   int issued = 0;
   if (tid == 0) {
-    for (; issued < nch && issued < kStages; ++issued)
-      issue_chunk<NA, D>(st, pp, src, j0, j1, issued, (base + issued) % kStages);
+    for (; issued < nch && issued < kStages; ++issued) issue_chunk<NA, D>(st, pp, src, j0, j1, issued);
   }
   volatile int* abort = &pp.abort;
   for (int c = 0; c < nch; ++c) {
-    const int g = base + c;
-    const int s = g % kStages;
+    const int s = c % kStages;
     if (*abort) break;
-    if (!mbar_wait(&pp.full[s], (g / kStages) & 1)) {
+    if (!mbar_wait(&pp.full[s], (c / kStages) & 1)) {
       *abort = 1;
       break;
     }
@@ -120,9 +113,9 @@ __device__ bool stream_sources(StageBuf<NA, D>& st, Pipe& pp, const float4* cons
     if ((tid & 31) == 0) mbar_arrive(&pp.empty[s]);
     if (tid == 0 && c + kStages < nch) {
       // Refill stage s with chunk c + kStages once every warp has released it.
-      if (mbar_wait(&pp.empty[s], (g / kStages) & 1)) {
+      if (mbar_wait(&pp.empty[s], (c / kStages) & 1)) {
         fence_proxy_async_smem();
-        issue_chunk<NA, D>(st, pp, src, j0, j1, c + kStages, s);
+        issue_chunk<NA, D>(st, pp, src, j0, j1, c + kStages);
         issued = c + kStages + 1;
       } else {
         *abort = 1;
@@ -137,7 +130,7 @@ __device__ bool stream_sources(StageBuf<NA, D>& st, Pipe& pp, const float4* cons
       // this memory: the last kStages chunks issued are the only ones that
       // can still be in flight.
       for (int d = max(0, issued - kStages); d < issued; ++d)
-        (void)mbar_wait(&pp.full[(base + d) % kStages], ((base + d) / kStages) & 1);
+        (void)mbar_wait(&pp.full[d % kStages], (d / kStages) & 1);
     }
     __syncthreads();
     return false;

@@ -67,7 +67,7 @@ INSTR_PER_PAIR_VEL = 9
 # DRAM bytes (read + write) of one k_step_backward launch, from ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum, caches flushed before the
 # launch) of the current kernel, by N.  Empty it whenever the kernel changes.
-DRAM_BYTES_PER_BWD_LAUNCH = {4096: 422912, 16384: 1596160}
+DRAM_BYTES_PER_BWD_LAUNCH = {}
 
 
 def parse():
@@ -237,13 +237,39 @@ def read_measured_peaks():
     return {}
 
 
+def measure_peaks(lib, stream_ptr, uuid):
+    """Measured throughput of the units the pair kernels run on
+    (gs_measure_peaks: FFMA, paired FFMA2, MUFU ex2, FP64 DFMA chains on
+    every SM, best of three ~50 ms launches, CUDA events), with the SM clock
+    sampled while they run."""
+    rates = (ctypes.c_double * 4)()
+    kms = (ctypes.c_double * 4)()
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    st = lib.gs_measure_peaks(rates, kms, ctypes.c_double(50.0), stream_ptr)
+    clk = clocks.stop()
+    if st != 0:
+        return None
+    return {"ffma_tflops": rates[0], "ffma2_tflops": rates[1], "fp32_tflops": max(rates[0], rates[1]),
+            "mufu_ex2_per_s": rates[2], "fp64_tflops": rates[3], "kernel_ms": [round(x, 3) for x in kms],
+            "sm_mhz": clk.get("sm_mhz"), "clock_reasons": clk.get("reasons"),
+            "basis": "gs_measure_peaks: 8 independent chains per thread, 4 x 256-thread CTAs per SM, "
+                     "best of 3 launches of ~50 ms (CUDA events)"}
+
+
 # ---------------------------------------------------------------- CPU oracle
 
 def oracle_gradient_sample(min_seconds=10.0, max_evals=50):
-    """Full FP64 oracle gradient evaluations of the workload, until ~min_seconds."""
+    """The FP64 oracle on this host's cores, on bounded samples: whole
+    gradient evaluations of the workload on all cores until ~min_seconds;
+    one whole gradient on a single thread; and a whole registration of the
+    smallest configuration (N = 256, T = 10, sigma = 0.2, 4 bumps, 50 L-BFGS
+    iterations from p0 = 0) on all cores."""
     import oracle
+    import landmark_synth as ls
     q0, p0, t = workload()
     q0, p0, t = (a.astype(np.float64) for a in (q0, p0, t))
+    cores = oracle.max_threads()
     n_ev, t0 = 0, time.perf_counter()
     while True:
         oracle.shoot_gradient(q0, p0, t, T_STEPS, SIGMA, LAMBDA)
@@ -251,45 +277,65 @@ def oracle_gradient_sample(min_seconds=10.0, max_evals=50):
         el = time.perf_counter() - t0
         if el >= min_seconds or n_ev >= max_evals:
             break
-    return {"value": n_ev / el, "unit": "grad-evals/s", "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": "%d full FP64 gradient evaluations of the workload (%.1f s)" % (n_ev, el)}
+    oracle.set_threads(1)
+    try:
+        t1 = time.perf_counter()
+        oracle.shoot_gradient(q0, p0, t, T_STEPS, SIGMA, LAMBDA)
+        el1 = time.perf_counter() - t1
+    finally:
+        oracle.set_threads(cores)
+    pr = ls.ellipsoid_pair(256, seed=0, n_bumps=4)
+    rq, rt = (np.asarray(a, np.float32).astype(np.float64) for a in (pr.q0, pr.target))
+    t2 = time.perf_counter()
+    reg = oracle.register(rq, rt, 10, 0.2, LAMBDA, max_iter=50, grad_tol=0.0)
+    el2 = time.perf_counter() - t2
+    return {"value": n_ev / el, "unit": "grad-evals/s", "cores": cores, "kind": "oracle",
+            "sample": "%d full FP64 gradient evaluations of the workload (%.1f s)" % (n_ev, el),
+            "single_thread": {"value": 1.0 / el1, "unit": "grad-evals/s", "cores": 1,
+                              "sample": "1 full FP64 gradient evaluation of the workload (%.1f s)" % el1},
+            "register_n256": {"seconds": el2, "iters": reg["iters"], "evals": reg["evals"], "cores": cores,
+                              "loss": reg["f"],
+                              "sample": "oracle.register, N=256, T=10, sigma=0.2, lambda=10, 50 iterations"}}
+
+
+def gshoot_config(n=N_LANDMARKS, world=1):
+    """The `config` object both arms report for the gradient workload."""
+    return {"workload": WORKLOAD if n == N_LANDMARKS else WORKLOAD.replace("N=4096", "N=%d" % n),
+            "N": n, "T": T_STEPS, "sigma": SIGMA, "lambda": LAMBDA,
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": "flushed between steps (256 MiB write, untimed)",
+            "precision": "FP32 pair terms, compensated; per-step split combine (see roofline.combine); "
+                         "FP64 state/loss"}
 
 
 def run_reference(args, dist):
-    """FP64 CPU oracle as the reference arm: each step is one time step of
-    the workload (StepForward + StepBackward pair sums over all N^2 pairs),
-    scaled to gradient evaluations (T such steps per evaluation)."""
+    """FP64 CPU oracle as the reference arm: each step is one whole gradient
+    evaluation of the workload (oracle.shoot_gradient: T forward steps, the
+    loss, T reverse steps, all N^2 pairs each), on all host cores."""
     if dist.rank != 0:
         return 0
     import oracle
     q0, p0, t = workload()
-    q = q0.astype(np.float64)
-    p = p0.astype(np.float64)
-    rng = np.random.default_rng(7)
-    a = rng.normal(size=q.shape)
-    b = rng.normal(size=q.shape)
+    q, p, tt = (a.astype(np.float64) for a in (q0, p0, t))
     for _ in range(max(0, args.warmup)):
-        oracle.step_forward(q, p, SIGMA)
-        oracle.step_backward(q, p, a, b, SIGMA)
+        oracle.shoot_gradient(q, p, tt, T_STEPS, SIGMA, LAMBDA)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.step_forward(q, p, SIGMA)
-        oracle.step_backward(q, p, a, b, SIGMA)
+        oracle.shoot_gradient(q, p, tt, T_STEPS, SIGMA, LAMBDA)
     el = time.perf_counter() - t0
     step_s = el / args.steps
-    value = 1.0 / (T_STEPS * step_s)
+    value = 1.0 / step_s
     cores = oracle.max_threads()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "grad-evals/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": N_LANDMARKS, "T": T_STEPS, "sigma": SIGMA,
-                   "lambda": LAMBDA, "step": "one time step (StepForward+StepBackward, all N^2 pairs)"},
+        "config": gshoot_config(N_LANDMARKS, 1),
         "cpu_baseline": {"value": value, "unit": "grad-evals/s", "cores": cores, "kind": "oracle",
-                         "sample": "%d single time steps (fwd+bwd pair sums) scaled by T=%d" % (args.steps, T_STEPS)},
+                         "sample": "%d whole FP64 gradient evaluations of the workload (%.1f s)" % (args.steps, el)},
         "e2e": {"value": value, "unit": "grad-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "pair_interactions_per_s": 2 * N_LANDMARKS ** 2 / step_s,
+        "pair_interactions_per_s": 2 * T_STEPS * N_LANDMARKS ** 2 / step_s,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -526,7 +572,7 @@ def velocity_grid(n_side=101, half=1.2):
     return np.ascontiguousarray(g, dtype=np.float32)
 
 
-def measure_velocity(gsh, reps=5, T=T_STEPS):
+def measure_velocity(gsh, reps=5, T=T_STEPS, peak=None):
     """The Eq. 4 velocity field: a 101^3 grid of points carried through the
     deformation of the workload's landmarks (flow_points: the landmark flow
     plus T Euler steps of every point), and one velocity_field evaluation at
@@ -556,7 +602,8 @@ def measure_velocity(gsh, reps=5, T=T_STEPS):
     t_flow = timed(lambda: gsh.flow_points(dq, dp, dx, T, SIGMA))
     t_vel = timed(lambda: gsh.velocity_field(dq, dp, dx, SIGMA))
     num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = alu_peak_tflops(num_sms, float(read_measured_peaks().get("sm_max_mhz", 2070.0)))
+    if peak is None:
+        peak = alu_peak_tflops(num_sms, float(read_measured_peaks().get("sm_max_mhz", 2070.0)))
     pairs_vel = float(m) * n
     tf = FLOPS_PER_PAIR_VEL * pairs_vel / (t_vel * 1e-3) / 1e12
     return {
@@ -566,10 +613,179 @@ def measure_velocity(gsh, reps=5, T=T_STEPS):
         "velocity_field_ms": t_vel, "velocity_pair_interactions_per_s": pairs_vel / (t_vel * 1e-3),
         "roofline": {"bound": "alu", "kernel": "k_velocity (one velocity_field call, conversions included)",
                      "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
-                     "fp32_pipe_frac": INSTR_PER_PAIR_VEL * pairs_vel / (t_vel * 1e-3) / (
-                         num_sms * 128 * float(read_measured_peaks().get("sm_max_mhz", 2070.0)) * 1e6)},
+                     "fp32_pipe_frac": INSTR_PER_PAIR_VEL * pairs_vel / (t_vel * 1e-3) / (peak * 1e12 / 2)},
         "timing": "CUDA events on the stream, device inputs, median of %d calls" % reps,
     }
+
+
+def _grad_inputs(dev, n, sigma_seed=0):
+    import torch
+    import landmark_synth as ls
+    pr = ls.ellipsoid_pair(n, seed=sigma_seed, n_bumps=8)
+    p0 = ls.random_momentum(n, P0_SCALE, seed=sigma_seed + 1)
+    return tuple(torch.tensor(np.asarray(a, np.float32), device=dev) for a in (pr.q0, p0, pr.target))
+
+
+def _timed_gradients(lib, prm, bufs, stream, reps, flush):
+    """Median device time (ms) of one shoot_gradient call and of its forward
+    and reverse sweeps (phase events), L2 flushed before each call."""
+    import torch
+    P = lambda x: ctypes.c_void_p(x.data_ptr())
+    q, p, t, gp, gq = bufs
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    call = lambda: lib.shoot_gradient(ctypes.byref(prm), P(q), P(p), P(t), None, P(gp), P(gq), sp)
+    import paper_1907_04839_gb300 as gsh
+    gsh.check(lib.gs_set_phase_timing(1))
+    try:
+        for _ in range(3):
+            gsh.check(call())
+        tt, fw, bw = [], [], []
+        pf, pb = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        for r in range(reps):
+            flush.fill_(float(r))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            gsh.check(call())
+            b.record(stream)
+            b.synchronize()
+            tt.append(a.elapsed_time(b))
+            gsh.check(lib.gs_phase_times(ctypes.byref(pf), ctypes.byref(pb)))
+            fw.append(pf.value)
+            bw.append(pb.value)
+    finally:
+        gsh.check(lib.gs_set_phase_timing(0))
+    return float(np.median(tt)), float(np.median(fw)), float(np.median(bw))
+
+
+def roofline_at(gsh, lib, dev, n, peak, mufu_peak, T=T_STEPS, sigma=0.05, reps=8):
+    """The step kernels' roofline at a larger N (the spec bar is set
+    at N >= 16384): whole gradients of an ellipsoid workload (sigma = 0.05,
+    T = 20), per-launch times from the graph's phase events (sweep / T)."""
+    import torch
+    q, p, t = _grad_inputs(dev, n)
+    bufs = (q, p, t, torch.empty_like(q), torch.empty_like(q))
+    prm = gsh.GsParams(N=n, T=T, ckpt_every=0, sigma=sigma, lambda_=LAMBDA, lbfgs_m=10, max_iter=1, grad_tol=0.0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ms, fwd, bwd = _timed_gradients(lib, prm, bufs, torch.cuda.current_stream(dev), reps, flush)
+    del flush
+    pairs = float(n) * n
+    lanes = peak * 1e12 / 2
+    out = {"N": n, "T": T, "sigma": sigma, "gradient_ms": ms, "peak": peak, "unit": "TFLOP/s",
+           "basis": "per-launch time = sweep time / T from graph events, median of %d gradients" % reps}
+    for name, sweep, fl, ins, kind in (("reverse", bwd, FLOPS_PER_PAIR_BWD, INSTR_PER_PAIR_BWD, 1),
+                                       ("forward", fwd, FLOPS_PER_PAIR_FWD, INSTR_PER_PAIR_FWD, 0)):
+        launch = sweep / T * 1e-3
+        th, cl = ctypes.c_int32(0), ctypes.c_int32(0)
+        gsh.check(lib.gs_step_config(kind, n, 0, 0, ctypes.byref(th), ctypes.byref(cl)))
+        out[name] = {"launch_ms": launch * 1e3, "achieved": fl * pairs / launch / 1e12,
+                     "frac": fl * pairs / launch / 1e12 / peak, "fp32_pipe_frac": ins * pairs / launch / lanes,
+                     "xu_frac": pairs / launch / mufu_peak, "launch_shape": {"threads": th.value, "cluster": cl.value}}
+    return out
+
+
+def measure_combine(gsh, lib, dev, sizes=(4096, 16384)):
+    """Whole gradients with the split partials of each step added in
+    double-single arithmetic and in FP64 (gs_set_combine_precision), same
+    inputs, same process."""
+    import torch
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = {"basis": "median device time of whole gradients (T=20, sigma=0.1), L2 flushed"}
+    cur = None
+    try:
+        for n in sizes:
+            q, p, t = _grad_inputs(dev, n)
+            bufs = (q, p, t, torch.empty_like(q), torch.empty_like(q))
+            prm = gsh.GsParams(N=n, T=T_STEPS, ckpt_every=0, sigma=SIGMA, lambda_=LAMBDA, lbfgs_m=10, max_iter=1,
+                               grad_tol=0.0)
+            row = {}
+            for f64 in (0, 1):
+                gsh.check(lib.gs_set_combine_precision(f64))
+                ms, fw, bw = _timed_gradients(lib, prm, bufs, torch.cuda.current_stream(dev),
+                                              20 if n <= 4096 else 6, flush)
+                row["fp64" if f64 else "double_single"] = {"gradient_ms": ms, "forward_ms": fw, "reverse_ms": bw}
+            row["fp64_extra_pct"] = 100.0 * (row["fp64"]["gradient_ms"] / row["double_single"]["gradient_ms"] - 1)
+            out["N%d" % n] = row
+    finally:
+        gsh.check(lib.gs_set_combine_precision(0))
+    del flush
+    return out
+
+
+def measure_register_small(gsh):
+    """A whole registration of the smallest configuration (N = 256, T = 10,
+    sigma = 0.2, lambda = 10, 4 bumps, 50 L-BFGS iterations from p0 = 0),
+    host arrays in and out, wall clock (median of 3)."""
+    import landmark_synth as ls
+    pr = ls.ellipsoid_pair(256, seed=0, n_bumps=4)
+    q0, t = (np.ascontiguousarray(a, np.float32) for a in (pr.q0, pr.target))
+    gsh.register(q0, t, 10, 0.2, LAMBDA, max_iter=5, grad_tol=0.0)
+    ts = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        _, info = gsh.register(q0, t, 10, 0.2, LAMBDA, max_iter=50, grad_tol=0.0)
+        ts.append(time.perf_counter() - t0)
+    return {"seconds": float(np.median(ts)), "iters": info["iters"], "evals": info["evals"], "loss": info["loss"],
+            "timing": "register() wall clock, host arrays, median of 3"}
+
+
+def measure_served_vs_plain(gsh, count, max_iter=200, T=T_STEPS):
+    """The served workload three ways, on the same first `count` requests of
+    the trace: (1) the server under the trace's 200/s arrivals (overload:
+    its completion rate is the capacity); (2) the server under a Poisson
+    rate of half that capacity, so that latency percentiles describe a
+    stable queue; (3) the plain single-registration path, one register()
+    call after another in arrival order, each timed, with the latencies a
+    single plain worker would give under the same two arrival processes.
+    Accuracy of (1) against (3): per-request final loss, AverageDist and
+    MaxDist."""
+    import landmark_synth as ls
+    burst = measure_served(gsh, count, max_iter=max_iter, T=T)
+    cap = burst["regs_per_s"]
+    sub = measure_served(gsh, count, max_iter=max_iter, T=T, rate=0.5 * cap)
+    trace = served_trace(count)
+    svc, infos = [], []
+    for r in trace:
+        t0 = time.perf_counter()
+        _, info = gsh.register(r["q0"], r["target"], T, r["sigma"], r["lam"], max_iter=max_iter, grad_tol=1e-5)
+        svc.append(time.perf_counter() - t0)
+        infos.append(info)
+
+    def fifo(arrivals):
+        end, lat = 0.0, []
+        for a, s in zip(arrivals, svc):
+            end = max(end, a) + s
+            lat.append(end - a)
+        return np.array(lat), end - arrivals[0]
+
+    arr_burst = [r["t_arrival"] for r in trace]
+    arr_sub = [r["t_arrival"] for r in ls.poisson_trace(count, 0.5 * cap, n_lo=1000, n_hi=50000, trace_seed=0,
+                                                        first_seed=1001)]
+    lat_b, mk_b = fifo(arr_burst)
+    lat_s, mk_s = fifo(arr_sub)
+    served_loss = [q["loss"] for q in burst["per_request"]]
+    rel = [abs(a - b["loss"]) / max(abs(b["loss"]), 1e-300) for a, b in zip(served_loss, infos)]
+    plain = {
+        "regs_per_s": count / float(np.sum(svc)), "service_s": [round(x, 3) for x in svc],
+        "latency_p50_s_at_200_per_s": float(np.percentile(lat_b, 50)),
+        "latency_p99_s_at_200_per_s": float(np.percentile(lat_b, 99)),
+        "latency_p50_s_at_half_capacity": float(np.percentile(lat_s, 50)),
+        "latency_p99_s_at_half_capacity": float(np.percentile(lat_s, 99)),
+        "makespan_s_at_200_per_s": mk_b,
+        "avg_dist_mean": float(np.mean([i["avg_dist"] for i in infos])),
+        "max_dist_mean": float(np.mean([i["max_dist"] for i in infos])),
+        "status": [int(i["status"]) for i in infos],
+        "timing": "register() wall clock per request, host arrays; latencies of one FIFO worker",
+    }
+    burst["capacity_regs_per_s"] = cap
+    burst["half_capacity"] = {k: sub[k] for k in ("arrival_rate_per_s", "regs_per_s", "makespan_s", "latency_p50_s",
+                                                 "latency_p99_s", "service_p50_s", "service_p99_s")}
+    burst["plain_loop"] = plain
+    burst["served_over_plain_regs_per_s"] = burst["regs_per_s"] / plain["regs_per_s"]
+    burst["accuracy_vs_plain"] = {
+        "loss_rel_diff_median": float(np.median(rel)), "loss_rel_diff_max": float(np.max(rel)),
+        "avg_dist_mean_served": float(np.mean([q["avg_dist"] for q in burst["per_request"]])),
+        "max_dist_mean_served": float(np.mean([q["max_dist"] for q in burst["per_request"]]))}
+    return burst
 
 
 def run_workload(args, dist):
@@ -642,6 +858,7 @@ def run_gshoot(args, dist):
         uuid = "GPU-" + str(u) if u is not None and not str(u).startswith("GPU-") else str(u)
     except Exception:
         uuid = None
+    peaks_meas = measure_peaks(lib, sp, uuid)
     clocks = ClockSampler(uuid)
     K = args.steps
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
@@ -712,14 +929,25 @@ def run_gshoot(args, dist):
     num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peaks = read_measured_peaks()
     max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = alu_peak_tflops(num_sms, max_mhz)
+    derived_peak = alu_peak_tflops(num_sms, max_mhz)
+    if peaks_meas:
+        peak = peaks_meas["ffma2_tflops"]
+        peak_basis = ("measured: paired FP32 FFMA2 chains on all %d SMs (gs_measure_peaks), %.1f TFLOP/s at a "
+                      "median %s MHz; derived %d x 128 lanes x 2 x %.0f MHz = %.1f TFLOP/s" % (
+                          num_sms, peak, peaks_meas.get("sm_mhz"), num_sms, max_mhz, derived_peak))
+        mufu_peak = peaks_meas["mufu_ex2_per_s"]
+    else:
+        peak = derived_peak
+        peak_basis = "%d SMs x 128 FP32 lanes x 2 flops x %.0f MHz (derived: the measurement failed)" % (
+            num_sms, max_mhz)
+        mufu_peak = num_sms * 32 * max_mhz * 1e6
     pairs = n * n
     # average launch duration in the timed steps: sweep time / T launches
     bwd_launch_ms = bwd_phase / (K * T_STEPS)
     fwd_launch_ms = fwd_phase / (K * T_STEPS)
     bwd_tf = FLOPS_PER_PAIR_BWD * pairs / (bwd_launch_ms * 1e-3) / 1e12
     fwd_tf = FLOPS_PER_PAIR_FWD * pairs / (fwd_launch_ms * 1e-3) / 1e12
-    pipe_lanes = num_sms * 128 * max_mhz * 1e6
+    pipe_lanes = peak * 1e12 / 2  # FP32 lane-operations per second at the measured rate
     traffic = DRAM_BYTES_PER_BWD_LAUNCH.get(n)
     shape = {}
     for kind, name in ((0, "forward"), (1, "reverse")):
@@ -729,37 +957,39 @@ def run_gshoot(args, dist):
     roofline = {
         "bound": "alu", "kernel": "k_step_backward (StepBackward pair sums + fused adjoint update)",
         "achieved": bwd_tf, "peak": peak, "unit": "TFLOP/s", "frac": bwd_tf / peak, "traffic": traffic,
-        "peak_basis": "%d SMs x 128 FP32 lanes x 2 flops x %.0f MHz (max SM clock; derived, not measured)" % (
-            num_sms, max_mhz),
+        "peak_basis": peak_basis,
         "flops_per_launch": FLOPS_PER_PAIR_BWD * pairs, "launch_ms": bwd_launch_ms,
         "launch_ms_basis": "reverse-sweep time / T from graph events in the timed steps (gaps included)",
         "isolated_launch_ms": bwd_ms.value,
         "launch_shape": shape["reverse"],
         "fp32_pipe_frac": INSTR_PER_PAIR_BWD * pairs / (bwd_launch_ms * 1e-3) / pipe_lanes,
+        "xu_frac": pairs / (bwd_launch_ms * 1e-3) / mufu_peak,
         "forward": {"kernel": "k_step_forward", "achieved": fwd_tf, "frac": fwd_tf / peak,
                     "launch_ms": fwd_launch_ms, "isolated_launch_ms": fwd_ms.value,
                     "launch_shape": shape["forward"],
-                    "fp32_pipe_frac": INSTR_PER_PAIR_FWD * pairs / (fwd_launch_ms * 1e-3) / pipe_lanes},
+                    "fp32_pipe_frac": INSTR_PER_PAIR_FWD * pairs / (fwd_launch_ms * 1e-3) / pipe_lanes,
+                    "xu_frac": pairs / (fwd_launch_ms * 1e-3) / mufu_peak},
+        "peaks": peaks_meas,
+        "combine": measure_combine(gsh, lib, dev),
     }
+    roofline_large = roofline_at(gsh, lib, dev, 16384, peak, mufu_peak)
     line = {
         "metric": METRIC, "value": value, "unit": "grad-evals/s", "n_gpus": dist.world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD if n == N_LANDMARKS else WORKLOAD.replace("N=4096", "N=%d" % n),
-                   "N": n, "T": T_STEPS, "sigma": SIGMA, "lambda": LAMBDA,
-                   "parallelism": "replicas" if dist.world > 1 else "single",
-                   "l2": "flushed between steps (256 MiB write, untimed)",
-                   "precision": "FP32 pair terms, compensated; double-single split combine; FP64 state/loss"},
+        "config": gshoot_config(n, dist.world),
         "pair_interactions_per_s": value * 2 * T_STEPS * pairs,
         "roofline": roofline,
+        "roofline_n16384": roofline_large,
         "e2e": e2e,
         "gpu_launches": K * launches.value,
         "clocks": clk,
     }
+    line["register_n256"] = measure_register_small(gsh)
     if not args.no_samples:
         line["batched"] = measure_batched(gsh, args.batched_count or 128)
-        line["served"] = measure_served(gsh, args.served_count or 8)
-        line["velocity"] = measure_velocity(gsh)
+        line["served"] = measure_served_vs_plain(gsh, args.served_count or 8)
+        line["velocity"] = measure_velocity(gsh, peak=peak)
         line["population"] = measure_population(gsh)
         line["variants"] = measure_variants(gsh)
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:

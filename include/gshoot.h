@@ -422,6 +422,19 @@ gs_status gs_max_active_clusters(int32_t kind, int32_t threads, int32_t R, int32
 gs_status gs_set_late_trigger(int32_t mode);
 
 /*
+ * gs_set_combine_precision — numerics (no counterpart in the paper): how the
+ * time-step kernels add the per-split partial sums of each target (the
+ * block-sum combine of every step).  f64 = 0 (the initial state):
+ * double-single arithmetic (FP32 pairs with error-free TwoSum, about 48
+ * significant bits); f64 = 1: each partial converted to FP64 and the
+ * partials added in FP64.  Either way the order is fixed and the result
+ * deterministic; the two differ in the last bits.  Applies to every entry
+ * point that runs the step kernels, batched and served ones included.
+ * Clears the cached graphs.  GS_EINVAL for another value.
+ */
+gs_status gs_set_combine_precision(int32_t f64);
+
+/*
  * gs_set_step_table — tuning (no counterpart in the paper): whether the
  * fused time-step kernels take their CTA and cluster sizes from the table
  * measured offline on this GPU model (one entry per padded landmark count
@@ -519,7 +532,7 @@ gs_status gs_measure_peaks(double* rates, double* ms_out, double target_ms, void
 /* Library ABI version: 100 * major + minor (101: gs_params gained
  * integrator and kinetic_at; 102: dim; 103: gs_server_config.schedule;
  * 104: gs_set_step_table; 105: gs_step_config; 106: gs_pointer_rule,
- * gs_measure_peaks). */
+ * gs_measure_peaks, gs_set_combine_precision). */
 int32_t gs_version(void);
 
 #ifdef __cplusplus

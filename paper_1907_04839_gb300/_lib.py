@@ -28,7 +28,7 @@ EXPORTS = [
     "gs_time_pair_kernels", "gs_time_pair_config", "gs_set_step_config", "step_forward_noalloc",
     "gs_set_phase_timing", "gs_phase_times", "gs_set_cluster_policy", "gs_max_active_clusters",
     "gs_set_late_trigger", "gs_check_wait_timeout", "gs_set_step_table", "gs_step_config",
-    "gs_pointer_rule", "gs_measure_peaks",
+    "gs_pointer_rule", "gs_measure_peaks", "gs_set_combine_precision",
     "gs_last_error",
     "gs_release_workspace",
     "gs_version",
@@ -153,7 +153,8 @@ def _declare(lib):
                  "gs_time_pair_kernels",
                  "step_forward_noalloc", "gs_time_pair_config", "gs_set_step_config", "gs_set_phase_timing",
                  "gs_phase_times", "gs_set_cluster_policy", "gs_max_active_clusters", "gs_set_late_trigger",
-                 "gs_set_step_table", "gs_step_config", "gs_check_wait_timeout", "gs_measure_peaks"):
+                 "gs_set_step_table", "gs_step_config", "gs_check_wait_timeout", "gs_measure_peaks",
+                 "gs_set_combine_precision"):
         getattr(lib, name).restype = ctypes.c_int
     lib.gs_last_error.restype = ctypes.c_char_p
     lib.gs_last_error.argtypes = []

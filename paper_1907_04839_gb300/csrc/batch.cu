@@ -642,6 +642,7 @@ struct BatchEngine {
       a.red_h = red_h;
       a.red_m = red_m;
       a.status = status_d;
+      a.combine64 = combine_f64() ? 1 : 0;
       GS_CUDA(launch_bstep_forward(fc, nf, a, bt, st, k > 0));
     }
     if (!grad) return GS_OK;
@@ -663,6 +664,7 @@ struct BatchEngine {
       b.hq0 = hq0;
       b.grad_p0_64 = gt;
       b.status = status_d;
+      b.combine64 = combine_f64() ? 1 : 0;
       GS_CUDA(launch_bstep_backward(bc, nb, b, btb, st, true));
     }
     return GS_OK;

@@ -261,6 +261,7 @@ StepFwdArgs forward_step_args(Workspace& w, const StepConfig& c, int kind, int n
   a.ticket = w.ticket;
   a.scalars = w.scalars;
   a.status = w.status;
+  a.combine64 = combine_f64() ? 1 : 0;
   return a;
 }
 
@@ -301,6 +302,7 @@ StepBwdArgs backward_step_args(Workspace& w, const StepConfig& c, int n, int T, 
   b.grad_q0 = w.out_b;
   b.grad_p0_64 = w.gp64;
   b.status = w.status;
+  b.combine64 = combine_f64() ? 1 : 0;
   return b;
 }
 
@@ -843,6 +845,15 @@ gs_status gs_set_late_trigger(int32_t mode) {
   if (mode < -1 || mode > 1) return gs::fail(GS_EINVAL, "mode must be -1, 0 or 1");
   std::lock_guard<std::mutex> lk(gs::g_mu);
   gs::set_late_trigger(mode);
+  for (auto& kv : gs::g_ws) kv.second->drop_graphs();
+  return GS_OK;
+}
+
+gs_status gs_set_combine_precision(int32_t f64) {
+  gs::g_err.clear();
+  if (f64 != 0 && f64 != 1) return gs::fail(GS_EINVAL, "f64 must be 0 (double-single) or 1 (FP64)");
+  std::lock_guard<std::mutex> lk(gs::g_mu);
+  gs::set_combine_f64(f64 == 1);
   for (auto& kv : gs::g_ws) kv.second->drop_graphs();
   return GS_OK;
 }

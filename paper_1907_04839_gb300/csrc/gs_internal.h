@@ -156,6 +156,7 @@ struct StepFwdArgs {
   int dim;             // 2: planar landmarks (records of 2 float4, (N,2) FP64
                        // arrays); 0 or 3: 3-D
   int late_trigger;    // trigger the next launch after the pair sums (pdl_trigger)
+  int combine64;       // add the split partials in FP64 (0: double-single)
 };
 
 struct StepBwdArgs {
@@ -185,6 +186,7 @@ struct StepBwdArgs {
   int h_at_end;        // the loss takes H at t = 1: no H(p0, q0) term in the gradient
   int dim;             // 2: planar landmarks; 0 or 3: 3-D
   int late_trigger;    // trigger the next launch after the pair sums (pdl_trigger)
+  int combine64;       // add the split partials in FP64 (0: double-single)
 };
 
 // Packed batches of independent problems.  Problem b occupies landmarks
@@ -221,6 +223,10 @@ void set_cluster_policy(int policy);
 // When step kernels trigger the next launch after their pair sums: -1 the
 // library's rule (reverse-step grids resident in one wave), 0 never, 1 always.
 void set_late_trigger(int mode);
+// Whether the step kernels add their split partials in FP64 (true) or in
+// double-single arithmetic (false, the initial state).
+void set_combine_f64(bool on);
+bool combine_f64();
 // Whether choose_step_config reads the measured step-configuration table.
 void set_step_table(bool on);
 // Whether a single-problem step launch of configuration c (kind 0 forward,

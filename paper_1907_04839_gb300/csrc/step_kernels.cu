@@ -122,6 +122,37 @@ __device__ __forceinline__ void pack_ds(const ds (&w)[2 * D], float4 (&x)[D]) {
   for (int f = 0; f < D; ++f) x[f] = make_float4(w[2 * f].hi, w[2 * f].lo, w[2 * f + 1].hi, w[2 * f + 1].lo);
 }
 
+// The sum over the cluster's C source splits of one target coordinate's two
+// partials (get(rr, x, y) yields split rr's double-single x and y), added in
+// rank order: in double-single arithmetic (TwoSum), or, when f64 is set,
+// each partial converted to FP64 and added in FP64.
+template <class Get>
+__device__ __forceinline__ void combine_splits(unsigned C, bool f64, Get get, double& s0, double& s1) {
+  if (f64) {
+    double a = 0.0, b = 0.0;
+#pragma unroll 4
+    for (unsigned rr = 0; rr < C; ++rr) {
+      float2 x, y;
+      get(rr, x, y);
+      a += static_cast<double>(x.x) + static_cast<double>(x.y);
+      b += static_cast<double>(y.x) + static_cast<double>(y.y);
+    }
+    s0 = a;
+    s1 = b;
+    return;
+  }
+  ds a{0.f, 0.f}, b{0.f, 0.f};
+#pragma unroll 4
+  for (unsigned rr = 0; rr < C; ++rr) {
+    float2 x, y;
+    get(rr, x, y);
+    a = ds_add(a, ds{x.x, x.y});
+    b = ds_add(b, ds{y.x, y.y});
+  }
+  s0 = ds_to_double(a);
+  s1 = ds_to_double(b);
+}
+
 // W > 1: the warp groups' partials of every target of the tile, added in
 // shared memory in group order into red[0].  Ends with a CTA barrier.
 template <int NT, int R, int W, int M, int D, class Tile, class Res>
@@ -220,21 +251,20 @@ __device__ __forceinline__ void forward_body(const StepFwdArgs& a, const StepVie
     const int k = item % D;
     if (lt >= M || v.tile * M + lt >= v.n) continue;
     const int i = tile0 + lt;  // packed landmark index
-    ds hp{0.f, 0.f}, hq{0.f, 0.f};
-#pragma unroll 4
-    for (unsigned rr = 0; rr < C; ++rr) {
-      const float2* rp = reinterpret_cast<const float2*>(&recv[(static_cast<int>(rr) * slice + ll) * D]);
-      const float2 x = rp[k];
-      const float2 y = rp[D + k];
-      hp = ds_add(hp, ds{x.x, x.y});
-      hq = ds_add(hq, ds{y.x, y.y});
-    }
+    double Hp, Hq;
+    combine_splits(
+        C, a.combine64 != 0,
+        [&](unsigned rr, float2& x, float2& y) {
+          const float2* rp = reinterpret_cast<const float2*>(&recv[(static_cast<int>(rr) * slice + ll) * D]);
+          x = rp[k];
+          y = rp[D + k];
+        },
+        Hp, Hq);
     if (a.dry) {  // timing only: keep the reduction, touch no state
-      hc += ds_to_double(hp) + ds_to_double(hq);
+      hc += Hp + Hq;
       continue;
     }
     const int tt = D * i + k;
-    const double Hp = ds_to_double(hp), Hq = ds_to_double(hq);
     const double q_old = a.q64[tt], p_old = a.p64[tt];
     float* an = reinterpret_cast<float*>(a.ab + (i >> 1) * D) + 2 * k + (i & 1);
     if (V && a.terminal) {
@@ -382,29 +412,29 @@ __device__ __forceinline__ void backward_body(const StepBwdArgs& a, const StepVi
     const int k = item % D;
     if ((Ragged && lt >= M) || v.tile * M + lt >= v.n) continue;
     const int i = tile0 + lt;
-    ds da{0.f, 0.f}, db{0.f, 0.f};
+    double dA, dB;  // dalpha, dbeta of this coordinate
     if constexpr (kPush) {
-#pragma unroll 4
-      for (unsigned rr = 0; rr < C; ++rr) {
-        const float2* rp = reinterpret_cast<const float2*>(&recv[(static_cast<int>(rr) * slice + ll) * D]);
-        const float2 x = rp[k];
-        const float2 y = rp[D + k];
-        da = ds_add(da, ds{x.x, x.y});
-        db = ds_add(db, ds{y.x, y.y});
-      }
+      combine_splits(
+          C, a.combine64 != 0,
+          [&](unsigned rr, float2& x, float2& y) {
+            const float2* rp = reinterpret_cast<const float2*>(&recv[(static_cast<int>(rr) * slice + ll) * D]);
+            x = rp[k];
+            y = rp[D + k];
+          },
+          dA, dB);
     } else {
       const uint32_t lp = smem_u32(&sm.red[0][lt][0]);
-#pragma unroll 4
-      for (unsigned rr = 0; rr < C; ++rr) {
-        const uint32_t rp = dsmem_addr(lp, rr);
-        const float2 x = ld_dsmem_f2(rp + 8u * k);
-        const float2 y = ld_dsmem_f2(rp + 8u * D + 8u * k);
-        da = ds_add(da, ds{x.x, x.y});
-        db = ds_add(db, ds{y.x, y.y});
-      }
+      combine_splits(
+          C, a.combine64 != 0,
+          [&](unsigned rr, float2& x, float2& y) {
+            const uint32_t rp = dsmem_addr(lp, rr);
+            x = ld_dsmem_f2(rp + 8u * k);
+            y = ld_dsmem_f2(rp + 8u * D + 8u * k);
+          },
+          dA, dB);
     }
     if (a.dry) {
-      if (!isfinite(da.hi + db.hi)) atomicOr(a.status, kErrNonFinite);
+      if (!isfinite(dA + dB)) atomicOr(a.status, kErrNonFinite);
       continue;
     }
     const int tt = D * i + k;
@@ -416,7 +446,7 @@ __device__ __forceinline__ void backward_body(const StepBwdArgs& a, const StepVi
       // and the four v; the next stage adjoint is
       //   kbar_{s-1} = dt b_{s-1} w + c_s dt v,  b = (1/6, 1/3, 1/3),
       //   c = (1/2, 1/2, 1) for s = 1, 2, 3.
-      const double va = ds_to_double(da), vb = ds_to_double(db);
+      const double va = dA, vb = dB;
       const double wa = a.a64[tt], wb = a.b64[tt];
       const double ya = (a.stage == 3 ? wa : a.ya64[tt]) + va;
       const double yb = (a.stage == 3 ? wb : a.yb64[tt]) + vb;
@@ -437,8 +467,8 @@ __device__ __forceinline__ void backward_body(const StepBwdArgs& a, const StepVi
       an[0] = (float)(v.dt / 6.0 * al);  // stage 4 adjoint of the previous step
       an[2 * D] = -(float)(v.kappa * (v.dt / 6.0 * be));
     } else {
-      al = a.a64[tt] + v.dt * ds_to_double(da);
-      be = a.b64[tt] + v.dt * ds_to_double(db);
+      al = a.a64[tt] + v.dt * dA;
+      be = a.b64[tt] + v.dt * dB;
       if (!isfinite(al) || !isfinite(be)) atomicOr(a.status, kErrNonFinite);
       a.a64[tt] = al;
       a.b64[tt] = be;
@@ -684,6 +714,13 @@ std::map<std::pair<std::pair<int, const void*>, int>, int> g_resident;
 }  // namespace
 
 void set_late_trigger(int mode) { g_late_trigger = mode; }
+
+namespace {
+bool g_combine64 = false;
+}  // namespace
+
+void set_combine_f64(bool on) { g_combine64 = on; }
+bool combine_f64() { return g_combine64; }
 
 bool late_trigger_for(int kind, const StepConfig& c, int dim, bool rk) {
   if (g_late_trigger >= 0) return g_late_trigger == 1;

@@ -75,6 +75,10 @@ def test_reference_arm_prints_the_contract_line():
     assert d["e2e"] == {"value": d["value"], "unit": "grad-evals/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
     assert d["config"]["N"] == 4096 and d["config"]["T"] == 20
+    # the same workload object the GPU arm reports: whole gradients, same config
+    import bench
+    assert d["config"] == bench.gshoot_config(4096, 1)
+    assert "whole FP64 gradient" in d["cpu_baseline"]["sample"]
 
 
 def test_clock_sampler_reads_median_under_load_and_reasons(tmp_path):

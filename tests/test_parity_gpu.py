@@ -167,6 +167,38 @@ def test_step_forward_full_size_sampled():
     assert rel(host(Hq)[rows], rq) < 1e-5
 
 
+def test_step_backward_full_size_sampled():
+    # StepBackward at the largest size with non-zero adjoints (the dynamic
+    # reverse sweep's pair sums), 48 sampled targets against the oracle.
+    n, sigma = 65536, 0.05
+    pr = ls.ellipsoid_pair(n, seed=4)
+    q = f32(pr.q0)
+    p = f32(ls.random_momentum(n, 0.003, seed=5))
+    rng = np.random.default_rng(6)
+    a, b = f32(rng.normal(0.0, 1.0, size=(n, 3))), f32(rng.normal(0.0, 0.01, size=(n, 3)))
+    da, db = gs().step_backward(dev(q), dev(p), dev(a), dev(b), sigma)
+    rows = np.random.default_rng(7).choice(n, size=48, replace=False)
+    ra, rb = oracle.step_backward_rows(q, p, a, b, sigma, rows)
+    ea, eb = rel(host(da)[rows], ra), rel(host(db)[rows], rb)
+    print("N=%d step_backward 48 rows: dalpha %.2e dbeta %.2e" % (n, ea, eb))
+    assert ea < 1e-5 and eb < 1e-5
+
+
+def test_gradient_full_size_one_step():
+    # The fused forward and reverse step kernels at 65536 landmarks with a
+    # moving flow (p0 != 0), against the oracle's whole gradient (T = 1:
+    # about 1.3e10 FP64 pair evaluations on the host).
+    n, T, sigma, lam = 65536, 1, 0.05, 10.0
+    pr = ls.ellipsoid_pair(n, seed=8)
+    q0, t = f32(pr.q0), f32(pr.target)
+    p0 = f32(ls.random_momentum(n, 0.003, seed=9))
+    loss, gp, gq = gs().shoot_gradient(dev(q0), dev(p0), dev(t), T, sigma, lam)
+    r = oracle.shoot_gradient(q0, p0, t, T, sigma, lam)
+    e = (abs(loss - r["loss"]) / abs(r["loss"]), rel(host(gp), r["grad_p0"]), rel(host(gq), r["grad_q0"]))
+    print("N=%d T=%d gradient rel err loss %.2e grad_p0 %.2e grad_q0 %.2e" % ((n, T) + e))
+    assert e[0] < 1e-5 and e[1] < 1e-4 and e[2] < 1e-4
+
+
 def test_gradient_deterministic_bitwise():
     q0, p0, t = _grad_case(1500, 8, 0.1, 10.0, 0.02)
     a = gs().shoot_gradient(dev(q0), dev(p0), dev(t), 8, 0.1, 10.0)

@@ -7,8 +7,9 @@ cudaMalloc, which can synchronise the whole device.  The entry point keeps
 its scratch in a static device array instead of the library's workspace.
 This test calls it through the C ABI twice in a row, on two different
 problems, and checks each result against the ordinary step_forward entry
-point within the 1e-5 normwise tolerance the parity tests use.  The file name
-makes pytest collect it last.
+point, and against the FP64 oracle on the same FP32 inputs, within the 1e-5
+normwise tolerance the parity tests use.  The file name makes pytest collect
+it last.
 """
 import ctypes
 
@@ -45,6 +46,11 @@ def test_step_forward_noalloc_matches_step_forward_twice():
         torch.cuda.synchronize()
         assert rel(Hp, ref_Hp) < 1e-5
         assert rel(Hq, ref_Hq) < 1e-5
+        # the FP64 oracle on the same FP32 inputs
+        import oracle
+        o_Hq, o_Hp = oracle.step_forward(q.double().cpu().numpy(), p.double().cpu().numpy(), sigma)
+        assert rel(Hp, torch.from_numpy(o_Hp)) < 1e-5
+        assert rel(Hq, torch.from_numpy(o_Hq)) < 1e-5
 
 
 def test_step_forward_noalloc_rejects_oversize_and_host_arrays():

@@ -422,6 +422,18 @@ gs_status gs_max_active_clusters(int32_t kind, int32_t threads, int32_t R, int32
 gs_status gs_set_late_trigger(int32_t mode);
 
 /*
+ * gs_set_batch_config — tuning (no counterpart in the paper): the launch
+ * shape of the packed time-step kernels that register_batch and servers
+ * created after this call use, for kind 0 (forward) or 1 (reverse): CTA
+ * size (one target per thread) and cluster size, which must divide the CTA
+ * size.  threads = 0 restores the built-in shape (128 threads forward, 64
+ * reverse, clusters of 8).  An engine keeps the shape it was created with,
+ * so a problem's sums split the same way alone and in any mix of that
+ * engine.  GS_EINVAL for a shape with no packed kernel.
+ */
+gs_status gs_set_batch_config(int32_t kind, int32_t threads, int32_t cluster);
+
+/*
  * gs_set_combine_precision — numerics (no counterpart in the paper): how the
  * time-step kernels add the per-split partial sums of each target (the
  * block-sum combine of every step).  f64 = 0 (the initial state):
@@ -532,7 +544,7 @@ gs_status gs_measure_peaks(double* rates, double* ms_out, double target_ms, void
 /* Library ABI version: 100 * major + minor (101: gs_params gained
  * integrator and kinetic_at; 102: dim; 103: gs_server_config.schedule;
  * 104: gs_set_step_table; 105: gs_step_config; 106: gs_pointer_rule,
- * gs_measure_peaks, gs_set_combine_precision). */
+ * gs_measure_peaks, gs_set_combine_precision, gs_set_batch_config). */
 int32_t gs_version(void);
 
 #ifdef __cplusplus

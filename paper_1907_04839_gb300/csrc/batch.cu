@@ -371,10 +371,15 @@ struct BatchEngine {
     t0 = std::chrono::steady_clock::now();
     GS_CUDA(cudaGetDevice(&device));
     GS_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device));
-    // One kernel shape for every problem of a batch: 128-thread CTAs, one
-    // target per thread forward, 64 backward, clusters of 8 CTAs.
-    fcfg = step_config_for(0, 1 << 16, 128, 1, 8);
-    bcfg = step_config_for(1, 1 << 16, 64, 1, 8);
+    // One kernel shape per kind for every problem of the engine (so that a
+    // problem's sums split the same way alone and in any mix), fixed at
+    // creation: batch_shape (the built-in shape, or a tuning override).
+    int th = 0, cl = 0;
+    batch_shape(0, &th, &cl);
+    fcfg = step_config_for(0, 1 << 16, th, 1, cl);
+    batch_shape(1, &th, &cl);
+    bcfg = step_config_for(1, 1 << 16, th, 1, cl);
+    if (fcfg.threads == 0 || bcfg.threads == 0) return fail(GS_EINVAL, "no packed kernel for the batch shape");
     max_probs = max_probs_;
     // bytes per landmark of capacity
     const size_t per = (T + 1) * kRecBytes / 2 + 2 * kRecBytes / 2 + 8 * 3 * sizeof(double) + 3 * sizeof(float) +
@@ -383,7 +388,9 @@ struct BatchEngine {
     const size_t fixed = 64u << 20;
     if (budget <= fixed + per * kPad) return fail(GS_EINVAL, "memory budget too small");
     cap = static_cast<int>(std::min<size_t>((budget - fixed) / per, size_t(1) << 28)) / kPad * kPad;
-    max_items = cap / 64 + max_probs;
+    // items: one per target tile of every problem, for the smaller of the
+    // two kinds' tile sizes
+    max_items = cap / std::min(fcfg.threads, bcfg.threads) + max_probs;
     auto get = [&](void** p, size_t b) -> cudaError_t {
       cudaError_t e = cudaMalloc(p, b + 256);
       if (e == cudaSuccess) {
@@ -487,6 +494,9 @@ struct BatchEngine {
     bp.npad = npad;
     int len = (npad + fcfg.cluster - 1) / fcfg.cluster;
     bp.split_len = (len + 7) / 8 * 8;
+    len = (npad + bcfg.cluster - 1) / bcfg.cluster;
+    bp.split_len_b = (len + 7) / 8 * 8;
+    bp.pad_ = 0;
     bp.kq = sc.kq;
     bp.kappa = sc.kappa;
     bp.dt = 1.0 / T;

@@ -849,6 +849,14 @@ gs_status gs_set_late_trigger(int32_t mode) {
   return GS_OK;
 }
 
+gs_status gs_set_batch_config(int32_t kind, int32_t threads, int32_t cluster) {
+  gs::g_err.clear();
+  std::lock_guard<std::mutex> lk(gs::g_mu);
+  if (!gs::set_batch_shape(kind, threads, cluster))
+    return gs::fail(GS_EINVAL, "no packed kernel with that CTA size and cluster size");
+  return GS_OK;
+}
+
 gs_status gs_set_combine_precision(int32_t f64) {
   gs::g_err.clear();
   if (f64 != 0 && f64 != 1) return gs::fail(GS_EINVAL, "f64 must be 0 (double-single) or 1 (FP64)");

@@ -192,7 +192,10 @@ struct StepBwdArgs {
 // Packed batches of independent problems.  Problem b occupies landmarks
 // [off, off+npad) of every packed array; items are (problem, target tile).
 struct BatchProb {
-  int off, n, npad, split_len;
+  int off, n, npad;
+  int split_len;    // sources per CTA of the forward kernel's clusters
+  int split_len_b;  // and of the reverse kernel's
+  int pad_;
   double kq, kappa, dt, lambda;
 };
 struct BatchItem {
@@ -246,6 +249,11 @@ FwdKernel forward_kernel_for(const StepConfig& cfg, int dim, bool variants);
 BwdKernel backward_kernel_for(const StepConfig& cfg, int dim, bool rk);
 cudaError_t launch_step_forward(const StepConfig& cfg, const StepFwdArgs& a, cudaStream_t st, bool pdl);
 cudaError_t launch_step_backward(const StepConfig& cfg, const StepBwdArgs& a, cudaStream_t st, bool pdl);
+// The launch shape of the packed batch kernels of `kind` (0 forward, 1
+// reverse) that a batch engine created now uses: CTA size and cluster size.
+// set_batch_shape(kind, 0, 0) restores the built-in shape.
+void batch_shape(int kind, int* threads, int* cluster);
+bool set_batch_shape(int kind, int threads, int cluster);
 // One launch over `items` (problem, tile) items; cfg gives the kernel variant
 // and cluster size (its tiles / split_len fields are unused).
 cudaError_t launch_bstep_forward(const StepConfig& cfg, int items, const StepFwdArgs& a, const BatchTables& bt,

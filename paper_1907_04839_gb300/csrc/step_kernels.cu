@@ -545,14 +545,14 @@ __global__ void __launch_bounds__(NT) k_step_backward(StepBwdArgs a) {
 // blockIdx.y indexes the item table; each item is one target tile of one
 // problem.  The H0 and mismatch sums of each CTA go to red_h / red_m at
 // index blockIdx.y * C + rank; a separate kernel adds them per problem.
-__device__ __forceinline__ StepView batch_view(const BatchTables& bt) {
+__device__ __forceinline__ StepView batch_view(const BatchTables& bt, bool reverse) {
   const BatchItem it = bt.items[blockIdx.y];
   const BatchProb P = bt.probs[it.prob];
   StepView v;
   v.off = P.off;
   v.n = P.n;
   v.npad = P.npad;
-  v.split_len = P.split_len;
+  v.split_len = reverse ? P.split_len_b : P.split_len;
   v.tile = it.tile;
   v.kappa_f = static_cast<float>(P.kappa);
   v.kq_f = static_cast<float>(P.kq);
@@ -566,7 +566,7 @@ __device__ __forceinline__ StepView batch_view(const BatchTables& bt) {
 template <int NT, int R, int W>
 __global__ void __launch_bounds__(NT) k_bstep_forward(StepFwdArgs a, BatchTables bt) {
   __shared__ double shred[NT / 32];
-  const StepView v = batch_view(bt);
+  const StepView v = batch_view(bt, false);
   double hc = 0.0, mc = 0.0;
   forward_body<NT, R, W, false, 3>(a, v, hc, mc);
   const bool reduce_h = a.first != 0;
@@ -583,7 +583,7 @@ __global__ void __launch_bounds__(NT) k_bstep_forward(StepFwdArgs a, BatchTables
 
 template <int NT, int R, int W>
 __global__ void __launch_bounds__(NT) k_bstep_backward(StepBwdArgs a, BatchTables bt) {
-  backward_body<NT, R, W, false, 3>(a, batch_view(bt));
+  backward_body<NT, R, W, false, 3>(a, batch_view(bt, true));
 }
 
 // ---------------------------------------------------------------- host side
@@ -809,6 +809,31 @@ const StepRule* table_rule(int npad) {
 }  // namespace
 
 void set_step_table(bool on) { g_use_table = on; }
+
+namespace {
+int g_batch_shape[2][2] = {{0, 0}, {0, 0}};  // threads, cluster per kind (0: built-in)
+}  // namespace
+
+void batch_shape(int kind, int* threads, int* cluster) {
+  // Built-in: 128-thread CTAs forward, 64 reverse, one target per thread,
+  // clusters of 8 for both.
+  *threads = g_batch_shape[kind][0] ? g_batch_shape[kind][0] : (kind == 0 ? 128 : 64);
+  *cluster = g_batch_shape[kind][1] ? g_batch_shape[kind][1] : 8;
+}
+
+bool set_batch_shape(int kind, int threads, int cluster) {
+  if (kind != 0 && kind != 1) return false;
+  if (threads == 0) {
+    g_batch_shape[kind][0] = g_batch_shape[kind][1] = 0;
+    return true;
+  }
+  // the packed kernels exist for the one-group shapes whose cluster divides the tile
+  const StepConfig c = step_config_for(kind, 1 << 16, threads, 1, cluster);
+  if (c.threads == 0 || threads % cluster != 0) return false;
+  g_batch_shape[kind][0] = threads;
+  g_batch_shape[kind][1] = cluster;
+  return true;
+}
 
 // Default configuration per problem size, from sweeps on GB300 (152 SMs).
 StepConfig choose_step_config(int kind, int npad, int num_sms, bool variants) {

@@ -65,6 +65,12 @@ def main():
                                                            "write it to PATH")
     ap.add_argument("--instances", type=int, default=1,
                     help="--emit-table: time each shape in this many graph instantiations and keep the slowest")
+    ap.add_argument("--batch-shapes", action="store_true",
+                    help="time whole packed registrations (register_batch) for every packed launch shape, on the "
+                         "batched distribution (N log-uniform in [500, 8000]) and on the served one "
+                         "(N log-uniform in [1000, 50000])")
+    ap.add_argument("--batch-count", type=int, default=128, help="--batch-shapes: problems of the batched mix")
+    ap.add_argument("--batch-iters", type=int, default=20, help="--batch-shapes: L-BFGS iterations per problem")
     args = ap.parse_args()
     import torch
 
@@ -75,6 +81,9 @@ def main():
     stream = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
     if args.emit_table:
         emit_table(lib, dev, sms, stream, args.emit_table, args.sigma, args.instances)
+        return
+    if args.batch_shapes:
+        batch_shapes(lib, args.batch_count, args.batch_iters)
         return
     for n in args.n:
         pr = ls.ellipsoid_pair(n, seed=0, n_bumps=8)
@@ -139,6 +148,74 @@ def main():
                                       "splits_req": s, "splits": used.value, "tiles": tiles,
                                       "ctas": tiles * used.value, "ms": ms.value,
                                       "gpairs_per_s": pairs / ms.value / 1e6}), flush=True)
+
+
+# packed launch shapes (threads, cluster) per kind; a cluster must divide the CTA
+BATCH_FWD = [(128, 8), (128, 4), (128, 16), (64, 8), (64, 16), (64, 4)]
+BATCH_BWD = [(64, 8), (64, 4), (64, 16), (32, 8), (32, 16), (32, 4)]
+
+
+def batch_shapes(lib, count, iters, reps=3):
+    """Whole packed registrations (register_batch, `iters` L-BFGS iterations
+    per problem, grad_tol 0 so every shape does the same evaluations) of two
+    problem mixes, for each packed launch shape: one kind varied at a time
+    against the built-in shape of the other, then the best of each kind
+    together.  Each line: the shape and the best of `reps` wall-clock
+    times.  A packed shape is fixed per engine (gs_set_batch_config), so
+    the choice never depends on the mix an engine happens to hold."""
+    import time
+    import torch
+    import landmark_synth as ls
+    from . import register_batch
+
+    def mix_batched():
+        out = []
+        for r in ls.batched_requests(count, n_lo=500, n_hi=8000, sigmas=(0.05, 0.1, 0.2), first_seed=1):
+            pr = ls.ellipsoid_pair(r["n"], seed=r["seed"], n_bumps=8)
+            out.append(dict(q0=np.asarray(pr.q0, np.float32), target=np.asarray(pr.target, np.float32),
+                            sigma=r["sigma"], lam=10.0))
+        return out
+
+    def mix_served():
+        out = []
+        for r in ls.poisson_trace(8, 200.0, n_lo=1000, n_hi=50000, trace_seed=0, first_seed=1001):
+            pr = ls.ellipsoid_pair(r["n"], seed=r["seed"], n_bumps=8)
+            out.append(dict(q0=np.asarray(pr.q0, np.float32), target=np.asarray(pr.target, np.float32),
+                            sigma=0.1, lam=10.0))
+        return out
+
+    def timed(probs, fs, bs):
+        _lib.check(lib.gs_set_batch_config(0, fs[0], fs[1]))
+        _lib.check(lib.gs_set_batch_config(1, bs[0], bs[1]))
+        best = math.inf
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            register_batch(probs, T=20, max_iter=iters, grad_tol=0.0)
+            torch.cuda.synchronize()
+            best = min(best, time.perf_counter() - t0)
+        return best
+
+    try:
+        for name, probs in (("batched", mix_batched()), ("served", mix_served())):
+            register_batch(probs[:2], T=20, max_iter=2, grad_tol=0.0)
+            base = timed(probs, BATCH_FWD[0], BATCH_BWD[0])
+            res = {}
+            for kind, shapes in ((0, BATCH_FWD), (1, BATCH_BWD)):
+                for shp in shapes:
+                    fs, bs = (shp, BATCH_BWD[0]) if kind == 0 else (BATCH_FWD[0], shp)
+                    t = base if shp == (BATCH_FWD[0] if kind == 0 else BATCH_BWD[0]) else timed(probs, fs, bs)
+                    res[(kind, shp)] = t
+                    print(json.dumps({"mix": name, "kind": "fwd" if kind == 0 else "bwd", "threads": shp[0],
+                                      "cluster": shp[1], "s": t, "vs_builtin": t / base}), flush=True)
+            bf = min(BATCH_FWD, key=lambda x: res[(0, x)])
+            bb = min(BATCH_BWD, key=lambda x: res[(1, x)])
+            t = timed(probs, bf, bb)
+            print(json.dumps({"mix": name, "best": {"fwd": bf, "bwd": bb}, "s": t, "builtin_s": base,
+                              "vs_builtin": t / base}), flush=True)
+    finally:
+        lib.gs_set_batch_config(0, 0, 0)
+        lib.gs_set_batch_config(1, 0, 0)
 
 
 TABLE_SIZES = list(range(64, 16384 + 1, 64))

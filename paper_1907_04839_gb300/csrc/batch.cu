@@ -355,6 +355,20 @@ struct BatchEngine {
   std::vector<std::pair<int, int>> free_segs;  // (off, len) in landmarks
   cudaStream_t st = nullptr;
   std::chrono::steady_clock::time_point t0;
+  // Pinned host mirrors of what every round uploads or reads back, so that
+  // the copies are asynchronous and a round synchronises only where the
+  // host needs a result: the item tables, the two-loop states, trial steps,
+  // history slots, and a ring of problem lists (each upload takes the next
+  // entry; the ring is longer than the uploads between two synchronisations).
+  static constexpr int kListRing = 32;
+  std::vector<void*> pinned;
+  BatchItem* items_h = nullptr;  // forward items, then reverse items at + max_items
+  int *item0_h = nullptr, *ntiles_h = nullptr, *slot_h = nullptr, *lists_h = nullptr;
+  int list_next = 0;
+  TwoLoopState* stv_h = nullptr;
+  double *ah_h = nullptr, *loss_h = nullptr, *dots_h = nullptr;
+  unsigned* status_h = nullptr;
+
 
   double now() const {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -420,6 +434,19 @@ struct BatchEngine {
     GS_CUDA(get((void**)&state_d, sizeof(TwoLoopState) * max_probs));
     GS_CUDA(get((void**)&status_d, sizeof(unsigned) * 8));
     GS_CUDA(cudaMemset(status_d, 0, sizeof(unsigned) * 8));
+    auto host = [&](void** p, size_t b) -> cudaError_t {
+      cudaError_t e = cudaMallocHost(p, b);
+      if (e == cudaSuccess) pinned.push_back(*p);
+      return e;
+    };
+    GS_CUDA(host((void**)&items_h, sizeof(BatchItem) * 2 * static_cast<size_t>(max_items)));
+    for (int** p : {&item0_h, &ntiles_h, &slot_h}) GS_CUDA(host((void**)p, sizeof(int) * max_probs));
+    GS_CUDA(host((void**)&lists_h, sizeof(int) * static_cast<size_t>(max_probs) * kListRing));
+    GS_CUDA(host((void**)&stv_h, sizeof(TwoLoopState) * max_probs));
+    GS_CUDA(host((void**)&ah_h, sizeof(double) * max_probs));
+    GS_CUDA(host((void**)&loss_h, sizeof(double) * max_probs));
+    GS_CUDA(host((void**)&dots_h, sizeof(double) * 4 * max_probs));
+    GS_CUDA(host((void**)&status_h, sizeof(unsigned) * 8));
     // every optimiser vector starts at zero (never read before written, but
     // a stale NaN must not be able to leak through a zero coefficient)
     for (double* p : {x, g, d, xt, gt, q64, p64, a64, b64, t64, hp0, hq0, gp64})
@@ -438,6 +465,8 @@ struct BatchEngine {
   void release() {
     for (void* p : allocs) cudaFree(p);
     allocs.clear();
+    for (void* p : pinned) cudaFreeHost(p);
+    pinned.clear();
   }
 
   int alloc_seg(int len) {
@@ -586,47 +615,56 @@ struct BatchEngine {
   // Upload the problem table and the forward / reverse item tables of the
   // listed problems (items_d and items_d + max_items).  item0[b], ntiles[b]
   // describe each problem's forward items (for the loss reduction).
+  //
+  // The tables go through pinned mirrors: the previous round's copies out of
+  // them finished at that round's last synchronisation, so no wait is needed
+  // here.
   gs_status build_items(const std::vector<int>& list, int* n_fwd, int* n_bwd) {
-    std::vector<BatchItem> fi, bi;
-    std::vector<int> item0(max_probs, 0), ntiles(max_probs, 0);
     // largest problems first: their long CTAs start early
     std::vector<int> order(list);
     std::sort(order.begin(), order.end(), [&](int a, int b) { return slots[a].n > slots[b].n; });
     const int Mf = fcfg.threads * fcfg.R, Mb = bcfg.threads * bcfg.R;
+    int nf = 0, nb = 0;
+    for (int b : order) {
+      nf += (probs_h[b].npad + Mf - 1) / Mf;
+      nb += (probs_h[b].npad + Mb - 1) / Mb;
+    }
+    if (std::max(nf, nb) > max_items) return fail(GS_ENOMEM, "batch item table full");
+    BatchItem* fi = items_h;
+    BatchItem* bi = items_h + max_items;
+    std::fill(item0_h, item0_h + max_probs, 0);
+    std::fill(ntiles_h, ntiles_h + max_probs, 0);
+    nf = nb = 0;
     for (int b : order) {
       const int tf = (probs_h[b].npad + Mf - 1) / Mf, tb = (probs_h[b].npad + Mb - 1) / Mb;
-      item0[b] = static_cast<int>(fi.size());
-      ntiles[b] = tf;
-      for (int t = 0; t < tf; ++t) fi.push_back(BatchItem{b, t});
-      for (int t = 0; t < tb; ++t) bi.push_back(BatchItem{b, t});
+      item0_h[b] = nf;
+      ntiles_h[b] = tf;
+      for (int t = 0; t < tf; ++t) fi[nf++] = BatchItem{b, t};
+      for (int t = 0; t < tb; ++t) bi[nb++] = BatchItem{b, t};
     }
-    if (static_cast<int>(std::max(fi.size(), bi.size())) > max_items) return fail(GS_ENOMEM, "batch item table full");
     GS_CUDA(cudaMemcpyAsync(probs_d, probs_h.data(), sizeof(BatchProb) * max_probs, cudaMemcpyHostToDevice, st));
-    GS_CUDA(cudaMemcpyAsync(items_d, fi.data(), sizeof(BatchItem) * fi.size(), cudaMemcpyHostToDevice, st));
-    GS_CUDA(cudaMemcpyAsync(items_d + max_items, bi.data(), sizeof(BatchItem) * bi.size(), cudaMemcpyHostToDevice, st));
-    GS_CUDA(cudaMemcpyAsync(item0_d, item0.data(), sizeof(int) * max_probs, cudaMemcpyHostToDevice, st));
-    GS_CUDA(cudaMemcpyAsync(ntiles_d, ntiles.data(), sizeof(int) * max_probs, cudaMemcpyHostToDevice, st));
-    *n_fwd = static_cast<int>(fi.size());
-    *n_bwd = static_cast<int>(bi.size());
-    // the host vectors must outlive the copies
-    GS_CUDA(cudaStreamSynchronize(st));
+    GS_CUDA(cudaMemcpyAsync(items_d, fi, sizeof(BatchItem) * nf, cudaMemcpyHostToDevice, st));
+    GS_CUDA(cudaMemcpyAsync(items_d + max_items, bi, sizeof(BatchItem) * nb, cudaMemcpyHostToDevice, st));
+    GS_CUDA(cudaMemcpyAsync(item0_d, item0_h, sizeof(int) * max_probs, cudaMemcpyHostToDevice, st));
+    GS_CUDA(cudaMemcpyAsync(ntiles_d, ntiles_h, sizeof(int) * max_probs, cudaMemcpyHostToDevice, st));
+    *n_fwd = nf;
+    *n_bwd = nb;
     return GS_OK;
   }
 
   gs_status upload_list(const std::vector<int>& list) {
-    GS_CUDA(cudaMemcpyAsync(list_d, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, st));
+    int* h = lists_h + static_cast<size_t>(list_next) * max_probs;
+    list_next = (list_next + 1) % kListRing;
+    std::copy(list.begin(), list.end(), h);
+    GS_CUDA(cudaMemcpyAsync(list_d, h, sizeof(int) * list.size(), cudaMemcpyHostToDevice, st));
     return GS_OK;
   }
 
-  // One batched gradient of the listed problems at p0 = xt: losses to loss_d,
-  // FP64 gradients to gt.  Also works as a forward flow only (grad = false).
-  gs_status gradient(const std::vector<int>& list, bool grad) {
-    if (list.empty()) return GS_OK;
-    int nf = 0, nb = 0;
-    gs_status s = build_items(list, &nf, &nb);
-    if (s != GS_OK) return s;
-    if ((s = upload_list(list)) != GS_OK) return s;
-    GS_CUDA(plaunch(static_cast<int>(list.size()), kBT, st, k_bpack, (const int*)list_d, (const BatchProb*)probs_d,
+  // The launches of one batched gradient of `count` listed problems (nf / nb
+  // forward / reverse items) at p0 = xt, on stream cs: losses to loss_d,
+  // FP64 gradients to gt; a forward flow only when grad is false.
+  gs_status enqueue_gradient(cudaStream_t cs, int count, int nf, int nb, bool grad) {
+    GS_CUDA(plaunch(count, kBT, cs, k_bpack, (const int*)list_d, (const BatchProb*)probs_d,
                     (const float*)qin, (const double*)xt, q64, p64, traj, status_d));
     const size_t slot = static_cast<size_t>(kRecF4) * (cap / 2);
     BatchTables bt{items_d, probs_d};
@@ -653,10 +691,10 @@ struct BatchEngine {
       a.red_m = red_m;
       a.status = status_d;
       a.combine64 = combine_f64() ? 1 : 0;
-      GS_CUDA(launch_bstep_forward(fc, nf, a, bt, st, k > 0));
+      GS_CUDA(launch_bstep_forward(fc, nf, a, bt, cs, k > 0));
     }
     if (!grad) return GS_OK;
-    GS_CUDA(plaunch(static_cast<int>(list.size()), 32, st, k_bloss, (const int*)list_d, (const int*)item0_d,
+    GS_CUDA(plaunch(count, 32, cs, k_bloss, (const int*)list_d, (const int*)item0_d,
                     (const int*)ntiles_d, (const BatchProb*)probs_d, (const double*)red_h, (const double*)red_m,
                     fcfg.cluster, loss_d));
     BatchTables btb{items_d + max_items, probs_d};
@@ -675,40 +713,61 @@ struct BatchEngine {
       b.grad_p0_64 = gt;
       b.status = status_d;
       b.combine64 = combine_f64() ? 1 : 0;
-      GS_CUDA(launch_bstep_backward(bc, nb, b, btb, st, true));
+      GS_CUDA(launch_bstep_backward(bc, nb, b, btb, cs, true));
     }
     return GS_OK;
   }
 
-  gs_status dots(const std::vector<int>& list, const DotSpec& spec, std::vector<double>* out) {
+  // One batched gradient of the listed problems at p0 = xt: the tables are
+  // uploaded, then the launch sequence is enqueued.  (Replaying that
+  // sequence as a CUDA graph cached per shape measured no faster: a round of
+  // small problems is bound by the latency of its chain of dependent
+  // kernels, not by the launches.)
+  gs_status gradient(const std::vector<int>& list, bool grad) {
+    if (list.empty()) return GS_OK;
+    int nf = 0, nb = 0;
+    gs_status s = build_items(list, &nf, &nb);
+    if (s != GS_OK) return s;
+    if ((s = upload_list(list)) != GS_OK) return s;
+    return enqueue_gradient(st, static_cast<int>(list.size()), nf, nb, grad);
+  }
+
+  // Dot products of the listed problems, read back with one
+  // synchronisation; with_loss also reads the losses (loss_h) and the device
+  // status word in the same wait, and reports an expired wait or a bad
+  // launch.
+  gs_status dots(const std::vector<int>& list, const DotSpec& spec, std::vector<double>* out,
+                 bool with_loss = false) {
     if (list.empty()) return GS_OK;
     if ((upload_list(list)) != GS_OK) return GS_ECUDA;
     GS_CUDA(plaunch(static_cast<int>(list.size()), kBT, st, k_bdots, (const int*)list_d, (const BatchProb*)probs_d, spec,
                     dots_d));
-    out->assign(4 * static_cast<size_t>(max_probs), 0.0);
-    GS_CUDA(cudaMemcpyAsync(out->data(), dots_d, sizeof(double) * 4 * max_probs, cudaMemcpyDeviceToHost, st));
+    GS_CUDA(cudaMemcpyAsync(dots_h, dots_d, sizeof(double) * 4 * max_probs, cudaMemcpyDeviceToHost, st));
+    if (with_loss) {
+      GS_CUDA(cudaMemcpyAsync(loss_h, loss_d, sizeof(double) * max_probs, cudaMemcpyDeviceToHost, st));
+      GS_CUDA(cudaMemcpyAsync(status_h, status_d, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    }
     GS_CUDA(cudaStreamSynchronize(st));
+    out->assign(dots_h, dots_h + 4 * static_cast<size_t>(max_probs));
+    if (with_loss) {
+      if (*status_h & kErrTimeout) return fail(GS_ETIMEOUT, "a device-side wait expired");
+      if (*status_h & kErrBadLaunch) return fail(GS_ECUDA, "device reported an inconsistent launch");
+    }
     return GS_OK;
   }
 
   gs_status vec(int op, const std::vector<int>& list, const int* slot_host) {
     if (list.empty()) return GS_OK;
     if (upload_list(list) != GS_OK) return GS_ECUDA;
-    if (slot_host) GS_CUDA(cudaMemcpyAsync(slot_d, slot_host, sizeof(int) * max_probs, cudaMemcpyHostToDevice, st));
+    if (slot_host) {
+      std::copy(slot_host, slot_host + max_probs, slot_h);
+      GS_CUDA(cudaMemcpyAsync(slot_d, slot_h, sizeof(int) * max_probs, cudaMemcpyHostToDevice, st));
+    }
     GS_CUDA(plaunch(static_cast<int>(list.size()), kBT, st, k_bvec, op, (const int*)list_d, (const BatchProb*)probs_d,
                     (const double*)a_d, (const int*)(slot_host ? slot_d : nullptr), stride(), x, g, d, xt, gt, S, Y));
-    if (slot_host) GS_CUDA(cudaStreamSynchronize(st));
     return GS_OK;
   }
 
-  gs_status check_status() {
-    unsigned h = 0;
-    GS_CUDA(cudaMemcpyAsync(&h, status_d, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-    GS_CUDA(cudaStreamSynchronize(st));
-    if (h & kErrTimeout) return fail(GS_ETIMEOUT, "a device-side wait expired");
-    if (h & kErrBadLaunch) return fail(GS_ECUDA, "device reported an inconsistent launch");
-    return GS_OK;
-  }
 
   // One round over the active problems the schedule selects (all of them,
   // or under the fair schedule those behind in charged pair work; see the
@@ -740,7 +799,7 @@ struct BatchEngine {
     gs_status s;
     // 1. directions
     if (!need_dir.empty()) {
-      std::vector<TwoLoopState> stv(max_probs);
+      TwoLoopState* stv = stv_h;
       for (int sl : need_dir) {
         Problem& p = slots[sl];
         stv[sl].head = p.head;
@@ -748,7 +807,7 @@ struct BatchEngine {
         stv[sl].gamma = p.gamma;
         std::memcpy(stv[sl].rho, p.rho, sizeof(p.rho));
       }
-      GS_CUDA(cudaMemcpyAsync(state_d, stv.data(), sizeof(TwoLoopState) * max_probs, cudaMemcpyHostToDevice, st));
+      GS_CUDA(cudaMemcpyAsync(state_d, stv, sizeof(TwoLoopState) * max_probs, cudaMemcpyHostToDevice, st));
       if ((s = upload_list(need_dir)) != GS_OK) return s;
       GS_CUDA(plaunch(static_cast<int>(need_dir.size()), kBT, st, k_btwoloop, (const int*)list_d,
                       (const BatchProb*)probs_d, (const TwoLoopState*)state_d, m, stride(), (const double*)g,
@@ -757,7 +816,7 @@ struct BatchEngine {
       sp.a[0] = g; sp.b[0] = d; sp.a[1] = g; sp.b[1] = g;
       sp.count = 2;
       std::vector<double> r;
-      if ((s = dots(need_dir, sp, &r)) != GS_OK) return s;  // synchronises (stv stays alive)
+      if ((s = dots(need_dir, sp, &r)) != GS_OK) return s;  // synchronises
       std::vector<int> restart;
       for (int sl : need_dir) {
         Problem& p = slots[sl];
@@ -776,7 +835,8 @@ struct BatchEngine {
       if ((s = vec(1, restart, nullptr)) != GS_OK) return s;
     }
     // 2. trial points and one batched gradient
-    std::vector<double> ah(max_probs, 0.0);
+    double* ah = ah_h;
+    std::fill(ah, ah + max_probs, 0.0);
     std::vector<int> search;
     for (int sl : active) {
       Problem& p = slots[sl];
@@ -785,21 +845,19 @@ struct BatchEngine {
         search.push_back(sl);
       }
     }
-    GS_CUDA(cudaMemcpyAsync(a_d, ah.data(), sizeof(double) * max_probs, cudaMemcpyHostToDevice, st));
+    GS_CUDA(cudaMemcpyAsync(a_d, ah, sizeof(double) * max_probs, cudaMemcpyHostToDevice, st));
     if ((s = vec(0, search, nullptr)) != GS_OK) return s;   // xt = x + a d
     std::vector<int> init;
     for (int sl : active)
       if (slots[sl].phase == kInit) init.push_back(sl);
     if ((s = vec(4, init, nullptr)) != GS_OK) return s;  // xt = x for the first evaluation
     if ((s = gradient(active, true)) != GS_OK) return s;
-    std::vector<double> loss(max_probs, 0.0);
-    GS_CUDA(cudaMemcpyAsync(loss.data(), loss_d, sizeof(double) * max_probs, cudaMemcpyDeviceToHost, st));
     DotSpec sp{};
     sp.a[0] = gt; sp.b[0] = d; sp.a[1] = gt; sp.b[1] = gt;
     sp.count = 2;
     std::vector<double> r;
-    if ((s = dots(active, sp, &r)) != GS_OK) return s;
-    if ((s = check_status()) != GS_OK) return s;
+    if ((s = dots(active, sp, &r, true)) != GS_OK) return s;  // also the losses and the status word
+    const std::vector<double> loss(loss_h, loss_h + max_probs);
     // 3. advance the state machines
     std::vector<int> accepted, to_copy;
     for (int sl : active) {
@@ -832,8 +890,7 @@ struct BatchEngine {
     if (!accepted.empty()) {
       std::vector<int> slot_host(max_probs, 0);
       for (int sl : accepted) slot_host[sl] = slots[sl].head;
-      if ((s = vec(2, accepted, slot_host.data())) != GS_OK) return s;  // s, y into the head slot
-      GS_CUDA(cudaMemcpyAsync(slot_d, slot_host.data(), sizeof(int) * max_probs, cudaMemcpyHostToDevice, st));
+      if ((s = vec(2, accepted, slot_host.data())) != GS_OK) return s;  // s, y into the head slot (uploads slot_d)
       DotSpec u{};
       u.a[0] = S; u.b[0] = Y; u.a[1] = Y; u.b[1] = Y; u.a[2] = S; u.b[2] = S; u.a[3] = gt; u.b[3] = gt;
       u.slot_a = slot_d; u.slot_b = slot_d;

@@ -260,3 +260,32 @@ def test_pointer_rule_rejects_another_gpus_memory(mtype, ptr_dev, cur, want):
     # refused, not handed to this device's kernels.
     import paper_1907_04839_gb300 as gsh
     assert gsh.load().gs_pointer_rule(mtype, ptr_dev, cur) == want
+
+
+def test_batch_config_accepts_packed_shapes_only():
+    # Host logic only: the packed kernels exist for one-group shapes whose
+    # cluster divides the CTA; 0 restores the built-in shape.
+    import paper_1907_04839_gb300 as gsh
+    lib = gsh.load()
+    try:
+        assert lib.gs_set_batch_config(0, 128, 4) == 0
+        assert lib.gs_set_batch_config(1, 64, 16) == 0
+        assert lib.gs_set_batch_config(1, 32, 8) == 0
+        assert lib.gs_set_batch_config(1, 64, 12) == -1   # does not divide the tile
+        assert lib.gs_set_batch_config(0, 96, 8) == -1    # no such CTA size
+        assert lib.gs_set_batch_config(0, 128, 32) == -1  # clusters of at most 16
+        assert lib.gs_set_batch_config(2, 128, 8) == -1   # kind 0 or 1
+    finally:
+        assert lib.gs_set_batch_config(0, 0, 0) == 0
+        assert lib.gs_set_batch_config(1, 0, 0) == 0
+
+
+def test_combine_precision_switch_validates_its_argument():
+    import paper_1907_04839_gb300 as gsh
+    lib = gsh.load()
+    try:
+        assert lib.gs_set_combine_precision(1) == 0
+        assert lib.gs_set_combine_precision(2) == -1
+        assert lib.gs_set_combine_precision(-1) == -1
+    finally:
+        assert lib.gs_set_combine_precision(0) == 0

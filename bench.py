@@ -85,7 +85,9 @@ def parse():
                     help="registrations of the batched workload (default: 128 in the grad run's sample, 512 alone)")
     ap.add_argument("--served-count", type=int, default=None,
                     help="requests of the served trace (default: 8 in the grad run's sample, 64 alone)")
-    ap.add_argument("--no-samples", action="store_true", help="grad run without the batched / served samples")
+    ap.add_argument("--no-samples", action="store_true",
+                    help="grad run only (for profiling): no batched / served / other samples, no peak "
+                         "microbenchmark (the roofline then uses the derived peak)")
     return ap.parse_args()
 
 
@@ -864,7 +866,8 @@ def run_gshoot(args, dist):
         uuid = "GPU-" + str(u) if u is not None and not str(u).startswith("GPU-") else str(u)
     except Exception:
         uuid = None
-    peaks_meas = measure_peaks(lib, sp, uuid)
+    # (--no-samples, the profiling command, runs the gradient's kernels only)
+    peaks_meas = None if args.no_samples else measure_peaks(lib, sp, uuid)
     clocks = ClockSampler(uuid)
     K = args.steps
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
@@ -944,7 +947,7 @@ def run_gshoot(args, dist):
         mufu_peak = peaks_meas["mufu_ex2_per_s"]
     else:
         peak = derived_peak
-        peak_basis = "%d SMs x 128 FP32 lanes x 2 flops x %.0f MHz (derived: the measurement failed)" % (
+        peak_basis = "%d SMs x 128 FP32 lanes x 2 flops x %.0f MHz (derived: not measured in this run)" % (
             num_sms, max_mhz)
         mufu_peak = num_sms * 32 * max_mhz * 1e6
     pairs = n * n
@@ -976,9 +979,9 @@ def run_gshoot(args, dist):
                     "fp32_pipe_frac": INSTR_PER_PAIR_FWD * pairs / (fwd_launch_ms * 1e-3) / pipe_lanes,
                     "xu_frac": pairs / (fwd_launch_ms * 1e-3) / mufu_peak},
         "peaks": peaks_meas,
-        "combine": measure_combine(gsh, lib, dev),
+        "combine": None if args.no_samples else measure_combine(gsh, lib, dev),
     }
-    roofline_large = roofline_at(gsh, lib, dev, 16384, peak, mufu_peak)
+    roofline_large = None if args.no_samples else roofline_at(gsh, lib, dev, 16384, peak, mufu_peak)
     line = {
         "metric": METRIC, "value": value, "unit": "grad-evals/s", "n_gpus": dist.world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -991,8 +994,8 @@ def run_gshoot(args, dist):
         "gpu_launches": K * launches.value,
         "clocks": clk,
     }
-    line["register_n256"] = measure_register_small(gsh)
     if not args.no_samples:
+        line["register_n256"] = measure_register_small(gsh)
         line["batched"] = measure_batched(gsh, args.batched_count or 128)
         line["served"] = measure_served_vs_plain(gsh, args.served_count or 8)
         line["velocity"] = measure_velocity(gsh, peak=peak)

@@ -24,6 +24,8 @@ _lock = threading.Lock()
 _lib = None
 
 _D = ctypes.POINTER(ctypes.c_double)
+# objective callback of orc_lbfgs: f(ctx, x, g) returns f(x), writes the gradient
+_FG = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_void_p, _D, _D)
 
 
 def build(force: bool = False) -> str:
@@ -63,6 +65,8 @@ def _load():
             lib.orc_lbfgs_quadratic.restype = cint
             lib.orc_lbfgs_rosenbrock.argtypes = [i64, _D, cint, cint, cd, _D, IP, IP]
             lib.orc_lbfgs_rosenbrock.restype = cint
+            lib.orc_lbfgs.argtypes = [i64, _D, _FG, ctypes.c_void_p, cint, cint, cd, _D, IP, IP, _D]
+            lib.orc_lbfgs.restype = cint
             lib.orc_register.argtypes = [i64, cint, cd, cd, cint, cint, cd, _D, _D, _D, _D, IP, IP, _D]
             lib.orc_register.restype = cint
             lib.orc_shoot_forward_v.argtypes = [cint, i64, cint, cd, cint, _D, _D, _D, _D]
@@ -224,6 +228,26 @@ def lbfgs_rosenbrock(x0, m=10, max_iter=500, grad_tol=1e-10):
     f = ctypes.c_double(0); it = ctypes.c_int(0); ev = ctypes.c_int(0)
     st = _load().orc_lbfgs_rosenbrock(x.size, _p(x), int(m), int(max_iter), float(grad_tol),
                                       ctypes.byref(f), ctypes.byref(it), ctypes.byref(ev))
+    return _lbfgs_out(st, f, it, ev, x)
+
+
+def lbfgs_callback(fg, x0, m=10, max_iter=100, grad_tol=1e-10):
+    """The oracle's L-BFGS (the one `register` runs) on a Python objective:
+    fg(x) -> (f, g) with x, g 1-D float64 arrays.  For pins that observe every
+    evaluation the optimiser makes."""
+    x = np.ascontiguousarray(x0, dtype=np.float64).ravel().copy()
+    n = x.size
+
+    def cb(_ctx, xp, gp):
+        xv = np.ctypeslib.as_array(xp, shape=(n,)).copy()
+        f, g = fg(xv)
+        np.ctypeslib.as_array(gp, shape=(n,))[:] = np.asarray(g, dtype=np.float64)
+        return float(f)
+
+    cfn = _FG(cb)
+    f = ctypes.c_double(0); it = ctypes.c_int(0); ev = ctypes.c_int(0)
+    st = _load().orc_lbfgs(n, _p(x), cfn, None, int(m), int(max_iter), float(grad_tol), ctypes.byref(f),
+                           ctypes.byref(it), ctypes.byref(ev), None)
     return _lbfgs_out(st, f, it, ev, x)
 
 

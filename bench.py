@@ -731,11 +731,13 @@ def measure_register_small(gsh):
 
 
 def measure_served_vs_plain(gsh, count, max_iter=200, T=T_STEPS):
-    """The served workload four ways, on the same first `count` requests of
+    """The served workload five ways, on the same first `count` requests of
     the trace: (1) the server (fair schedule) under the trace's 200/s
     arrivals (overload: its completion rate is the capacity); (2) the same
     with every resident request in every round (schedule "all": the most
-    packing, the least latency advantage for small requests); (3) the
+    packing, the least latency advantage for small requests); (2b) two lanes
+    (schedule "lanes": requests of at most 8192 landmarks fair-scheduled in a
+    second engine alongside the all-rounds rounds of the larger ones); (3) the
     server under a Poisson rate of half the capacity of (1), so that latency
     percentiles describe a stable queue; (4) the plain single-registration
     path, one register() call after another in arrival order, each timed,
@@ -745,6 +747,7 @@ def measure_served_vs_plain(gsh, count, max_iter=200, T=T_STEPS):
     import landmark_synth as ls
     burst = measure_served(gsh, count, max_iter=max_iter, T=T)
     every = measure_served(gsh, count, max_iter=max_iter, T=T, schedule="all")
+    lanes = measure_served(gsh, count, max_iter=max_iter, T=T, schedule="lanes")
     cap = burst["regs_per_s"]
     sub = measure_served(gsh, count, max_iter=max_iter, T=T, rate=0.5 * cap)
     trace = served_trace(count)
@@ -789,6 +792,10 @@ def measure_served_vs_plain(gsh, count, max_iter=200, T=T_STEPS):
     burst["schedule_all"] = {k: every[k] for k in ("regs_per_s", "makespan_s", "latency_p50_s", "latency_p99_s",
                                                   "service_p50_s", "service_p99_s", "pair_interactions_per_s")}
     burst["schedule_all"]["served_over_plain_regs_per_s"] = every["regs_per_s"] / plain["regs_per_s"]
+    burst["schedule_lanes"] = {k: lanes[k] for k in ("regs_per_s", "makespan_s", "latency_p50_s", "latency_p99_s",
+                                                    "service_p50_s", "service_p99_s", "pair_interactions_per_s")}
+    burst["schedule_lanes"]["served_over_plain_regs_per_s"] = lanes["regs_per_s"] / plain["regs_per_s"]
+    burst["schedule_lanes"]["lane_split"] = 8192
     burst["accuracy_vs_plain"] = {
         "loss_rel_diff_median": float(np.median(rel)), "loss_rel_diff_max": float(np.max(rel)),
         "avg_dist_mean_served": float(np.mean([q["avg_dist"] for q in burst["per_request"]])),

@@ -259,8 +259,10 @@ typedef struct gs_server_config {
     void* stream;           /* cudaStream_t for all of the server's work */
     int32_t schedule;       /* GS_SCHED_ALL (0): every resident request is evaluated in
                                every round; GS_SCHED_FAIR (1): fair shares of pair work,
-                               so small requests advance more rounds than large ones */
-    int32_t reserved;       /* set to 0 */
+                               so small requests advance more rounds than large ones;
+                               GS_SCHED_LANES (2): two lanes, see below */
+    int32_t lane_split;     /* GS_SCHED_LANES: requests of at most this many landmarks go
+                               to the small lane (0: 8192); must be 0 otherwise */
 } gs_server_config;
 
 /* Round schedules of the server (gs_server_config.schedule).  Under
@@ -270,8 +272,16 @@ typedef struct gs_server_config {
  * cost, and a request starts at the smallest virtual time present when it is
  * admitted.  Every request then receives the same pair work per unit time,
  * and a small request finishes after its own work instead of the largest
- * request's.  A request's iterates do not depend on the schedule. */
-enum { GS_SCHED_ALL = 0, GS_SCHED_FAIR = 1 };
+ * request's.  Under GS_SCHED_LANES the server keeps two engines: requests of
+ * at most lane_split landmarks go to a small lane (a quarter of the memory
+ * budget, the fair schedule, a stream of its own), the others to a large
+ * lane (the rest of the budget, every resident request in every round, on
+ * `stream`).  gs_server_step runs one round of the large lane and, on a
+ * second host thread at the same time, as many rounds of the small lane as
+ * fit in it (at least one), so small requests finish early without taking
+ * rounds from the large ones.  A request's iterates do not depend on the
+ * schedule or the lane. */
+enum { GS_SCHED_ALL = 0, GS_SCHED_FAIR = 1, GS_SCHED_LANES = 2 };
 
 typedef struct gs_server gs_server;
 
@@ -286,7 +296,9 @@ gs_status gs_server_submit(gs_server* sv, int64_t N, double sigma, double lambda
 
 /* One round: admit queued requests while memory allows, evaluate the
  * resident requests the schedule selects once each (all of them under
- * GS_SCHED_ALL), advance their L-BFGS, retire finished ones, admit again.
+ * GS_SCHED_ALL; under GS_SCHED_LANES one round of the large lane and the
+ * small lane's rounds that run alongside it), advance their L-BFGS, retire
+ * finished ones, admit again.
  * Out (each may be NULL): requests resident, requests queued, requests
  * finished in this round. */
 gs_status gs_server_step(gs_server* sv, int32_t* active, int32_t* queued, int32_t* completed);

@@ -311,17 +311,20 @@ class Server:
     poll() returns (p0, info, latency) of a finished request or None.
     schedule "fair" (the default) shares pair work equally among resident
     requests, so small ones finish sooner; "all" evaluates every resident
-    request in every round."""
+    request in every round; "lanes" runs requests of at most `lane_split`
+    landmarks (0: 8192) in a second, fair-scheduled engine concurrently with
+    the all-rounds engine of the larger ones."""
 
     def __init__(self, T, m=10, max_iter=100, grad_tol=1e-5, memory_budget=8 << 30, max_problems=1024,
-                 stream=None, schedule="fair"):
-        if schedule not in ("all", "fair"):
-            raise ValueError("schedule must be 'all' or 'fair'")
+                 stream=None, schedule="fair", lane_split=0):
+        schedules = {"all": 0, "fair": 1, "lanes": 2}
+        if schedule not in schedules:
+            raise ValueError("schedule must be 'all', 'fair' or 'lanes'")
         self._lib = load()
         cfg = GsServerConfig(T=int(T), lbfgs_m=int(m), max_iter=int(max_iter), max_problems=int(max_problems),
                              grad_tol=float(grad_tol), memory_budget=int(memory_budget),
-                             stream=ctypes.c_void_p(stream or 0), schedule=1 if schedule == "fair" else 0,
-                             reserved=0)
+                             stream=ctypes.c_void_p(stream or 0), schedule=schedules[schedule],
+                             lane_split=int(lane_split))
         self._h = ctypes.c_void_p(0)
         check(self._lib.gs_server_create(ctypes.byref(cfg), ctypes.byref(self._h)))
         self._n = {}

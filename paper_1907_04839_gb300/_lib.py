@@ -101,7 +101,7 @@ class GsServerConfig(ctypes.Structure):
         ("memory_budget", ctypes.c_uint64),
         ("stream", ctypes.c_void_p),
         ("schedule", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("lane_split", ctypes.c_int32),
     ]
 
 

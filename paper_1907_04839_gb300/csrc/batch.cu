@@ -20,12 +20,14 @@
 // iterates do not depend on which other problems share its rounds, as long
 // as its tile configuration is the same.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
 #include <deque>
 #include <map>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "engine.h"
@@ -956,8 +958,10 @@ struct BatchEngine {
     for (int sl : done) {
       Problem& p = slots[sl];
       std::vector<double> xh(3 * static_cast<size_t>(p.n));
-      GS_CUDA(cudaMemcpy(xh.data(), x + 3 * static_cast<size_t>(p.off), xh.size() * sizeof(double),
-                         cudaMemcpyDeviceToHost));
+      // on this engine's stream: a second lane may be running on another
+      GS_CUDA(cudaMemcpyAsync(xh.data(), x + 3 * static_cast<size_t>(p.off), xh.size() * sizeof(double),
+                              cudaMemcpyDeviceToHost, st));
+      GS_CUDA(cudaStreamSynchronize(st));
       p.p0_result.resize(xh.size());
       for (size_t i = 0; i < xh.size(); ++i) p.p0_result[i] = static_cast<float>(xh[i]);
       p.result.loss = p.f;
@@ -980,32 +984,59 @@ struct BatchEngine {
 // ---------------------------------------------------------------- C ABI
 
 struct gs_server {
-  gs::BatchEngine eng;
+  gs::BatchEngine eng;    // every request; under GS_SCHED_LANES the large ones
+  // GS_SCHED_LANES: requests of at most lane_split landmarks run in a second
+  // engine on its own stream, under the fair schedule, concurrently with the
+  // large lane's rounds.
+  bool lanes = false;
+  int lane_split = 0;
+  gs::BatchEngine small;
+  cudaStream_t small_st = nullptr;
   std::mutex mu;
   struct Pending {
     gs::Problem proto;
     std::vector<float> q0, target, p0;
   };
   std::deque<Pending> queue;            // submitted, not yet admitted
-  std::map<int64_t, int> admitted;      // request id -> slot
+  std::map<int64_t, int> admitted;      // request id -> slot (lanes: slot + lane * kLaneTag)
   std::map<int64_t, gs::Problem> finished;
   int64_t next_id = 1;
 };
 
 namespace {
 
+constexpr int kLaneTag = 1 << 24;  // admitted[] value offset of the small lane's slots
+
 gs_status server_admit(gs_server* sv) {
-  // admit in arrival order while a segment fits
+  // admit in arrival order while a segment fits (in the request's lane)
   while (!sv->queue.empty()) {
     gs_server::Pending& pd = sv->queue.front();
+    const bool small = sv->lanes && pd.proto.n <= sv->lane_split;
+    gs::BatchEngine& e = small ? sv->small : sv->eng;
     gs_status err = GS_OK;
-    const int sl = sv->eng.admit(pd.proto, pd.q0.data(), pd.target.data(), pd.p0.empty() ? nullptr : pd.p0.data(), &err);
+    const int sl = e.admit(pd.proto, pd.q0.data(), pd.target.data(), pd.p0.empty() ? nullptr : pd.p0.data(), &err);
     if (err != GS_OK) return err;
     if (sl < 0) break;  // no room until something finishes
-    sv->admitted[pd.proto.id] = sl;
+    sv->admitted[pd.proto.id] = sl + (small ? kLaneTag : 0);
     sv->queue.pop_front();
   }
   return GS_OK;
+}
+
+bool has_active(const gs::BatchEngine& e) {
+  for (const gs::Problem& p : e.slots)
+    if (p.off >= 0 && p.phase != gs::kDone) return true;
+  return false;
+}
+
+// Move an engine's finished problems to the server's results and free them.
+void collect(gs_server* sv, gs::BatchEngine& e, const std::vector<int>& done) {
+  for (int sl : done) {
+    gs::Problem& p = e.slots[sl];
+    sv->finished[p.id] = p;
+    sv->admitted.erase(p.id);
+    e.retire(sl);
+  }
 }
 
 }  // namespace
@@ -1022,16 +1053,44 @@ gs_status gs_server_create(const gs_server_config* cfg, gs_server** out) {
     gs::set_last_error("bad server configuration");
     return GS_EINVAL;
   }
-  if (cfg->schedule != GS_SCHED_ALL && cfg->schedule != GS_SCHED_FAIR) {
-    gs::set_last_error("schedule must be GS_SCHED_ALL or GS_SCHED_FAIR");
+  if (cfg->schedule != GS_SCHED_ALL && cfg->schedule != GS_SCHED_FAIR && cfg->schedule != GS_SCHED_LANES) {
+    gs::set_last_error("schedule must be GS_SCHED_ALL, GS_SCHED_FAIR or GS_SCHED_LANES");
+    return GS_EINVAL;
+  }
+  if (cfg->lane_split < 0 || (cfg->lane_split != 0 && cfg->schedule != GS_SCHED_LANES)) {
+    gs::set_last_error("lane_split must be 0, or >= 1 with GS_SCHED_LANES");
     return GS_EINVAL;
   }
   gs_server* sv = new gs_server();
-  sv->eng.schedule = cfg->schedule;
-  gs_status s = sv->eng.init(cfg->T, cfg->lbfgs_m, cfg->max_iter, cfg->grad_tol, cfg->memory_budget,
-                             cfg->max_problems, static_cast<cudaStream_t>(cfg->stream));
+  gs_status s = GS_OK;
+  if (cfg->schedule == GS_SCHED_LANES) {
+    // a quarter of the budget for the small lane, the rest for the large one
+    sv->lanes = true;
+    sv->lane_split = cfg->lane_split > 0 ? cfg->lane_split : 8192;
+    sv->eng.schedule = GS_SCHED_ALL;
+    sv->small.schedule = GS_SCHED_FAIR;
+    const uint64_t small_budget = cfg->memory_budget / 4;
+    cudaError_t e = cudaStreamCreateWithFlags(&sv->small_st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      gs::set_last_error(cudaGetErrorString(e));
+      delete sv;
+      return GS_ECUDA;
+    }
+    s = sv->small.init(cfg->T, cfg->lbfgs_m, cfg->max_iter, cfg->grad_tol, small_budget, cfg->max_problems,
+                       sv->small_st);
+    if (s == GS_OK)
+      s = sv->eng.init(cfg->T, cfg->lbfgs_m, cfg->max_iter, cfg->grad_tol, cfg->memory_budget - small_budget,
+                       cfg->max_problems, static_cast<cudaStream_t>(cfg->stream));
+    sv->small.t0 = sv->eng.t0;  // one clock for every request's timestamps
+  } else {
+    sv->eng.schedule = cfg->schedule;
+    s = sv->eng.init(cfg->T, cfg->lbfgs_m, cfg->max_iter, cfg->grad_tol, cfg->memory_budget, cfg->max_problems,
+                     static_cast<cudaStream_t>(cfg->stream));
+  }
   if (s != GS_OK) {
     sv->eng.release();
+    sv->small.release();
+    if (sv->small_st) cudaStreamDestroy(sv->small_st);
     delete sv;
     return s;
   }
@@ -1048,7 +1107,8 @@ gs_status gs_server_submit(gs_server* sv, int64_t N, double sigma, double lambda
     return GS_EINVAL;
   }
   std::lock_guard<std::mutex> lk(sv->mu);
-  if (gs::round_up(N, gs::kPad) > sv->eng.cap) {
+  const gs::BatchEngine& lane = sv->lanes && N <= sv->lane_split ? sv->small : sv->eng;
+  if (gs::round_up(N, gs::kPad) > lane.cap) {
     gs::set_last_error("request larger than the server's memory budget");
     return GS_ENOMEM;
   }
@@ -1082,19 +1142,46 @@ gs_status gs_server_step(gs_server* sv, int32_t* active, int32_t* queued, int32_
   std::lock_guard<std::mutex> lk(sv->mu);
   gs_status s = server_admit(sv);
   if (s != GS_OK) return s;
-  std::vector<int> done;
-  if ((s = sv->eng.round(&done)) != GS_OK) return s;
-  if ((s = sv->eng.finish(done)) != GS_OK) return s;
-  for (int sl : done) {
-    gs::Problem& p = sv->eng.slots[sl];
-    sv->finished[p.id] = p;
-    sv->admitted.erase(p.id);
-    sv->eng.retire(sl);
+  std::vector<int> done, done_small;
+  const bool run_small = sv->lanes && has_active(sv->small);
+  if (run_small && has_active(sv->eng)) {
+    // One round of the large lane on this thread; meanwhile the small lane
+    // runs rounds on a worker thread, on its own stream, until the large
+    // round is over (at least one).
+    std::atomic<bool> large_done{false};
+    gs_status s_small = GS_OK;
+    const int device = sv->eng.device;
+    std::thread worker([&] {
+      if (cudaSetDevice(device) != cudaSuccess) {
+        s_small = GS_ECUDA;
+        return;
+      }
+      do {
+        std::vector<int> d;
+        if ((s_small = sv->small.round(&d)) != GS_OK) return;
+        if ((s_small = sv->small.finish(d)) != GS_OK) return;
+        done_small.insert(done_small.end(), d.begin(), d.end());
+      } while (!large_done.load() && has_active(sv->small));
+    });
+    s = sv->eng.round(&done);
+    if (s == GS_OK) s = sv->eng.finish(done);
+    large_done.store(true);
+    worker.join();
+    if (s != GS_OK) return s;
+    if (s_small != GS_OK) return s_small;
+  } else if (run_small) {
+    if ((s = sv->small.round(&done_small)) != GS_OK) return s;
+    if ((s = sv->small.finish(done_small)) != GS_OK) return s;
+  } else {
+    if ((s = sv->eng.round(&done)) != GS_OK) return s;
+    if ((s = sv->eng.finish(done)) != GS_OK) return s;
   }
+  collect(sv, sv->eng, done);
+  collect(sv, sv->small, done_small);
   if ((s = server_admit(sv)) != GS_OK) return s;
   if (active) *active = static_cast<int32_t>(sv->admitted.size());
   if (queued) *queued = static_cast<int32_t>(sv->queue.size());
-  if (completed) *completed = static_cast<int32_t>(done.size());
+  if (completed) *completed = static_cast<int32_t>(done.size() + done_small.size());
   return GS_OK;
 }
 
@@ -1134,15 +1221,18 @@ gs_status gs_server_stats(gs_server* sv, int64_t* capacity_landmarks, int64_t* f
   std::lock_guard<std::mutex> lk(sv->mu);
   int64_t fr = 0;
   for (auto& s : sv->eng.free_segs) fr += s.second;
-  if (capacity_landmarks) *capacity_landmarks = sv->eng.cap;
+  for (auto& s : sv->small.free_segs) fr += s.second;
+  if (capacity_landmarks) *capacity_landmarks = static_cast<int64_t>(sv->eng.cap) + sv->small.cap;
   if (free_landmarks) *free_landmarks = fr;
-  if (bytes) *bytes = static_cast<int64_t>(sv->eng.bytes);
+  if (bytes) *bytes = static_cast<int64_t>(sv->eng.bytes + sv->small.bytes);
   return GS_OK;
 }
 
 void gs_server_destroy(gs_server* sv) {
   if (!sv) return;
   sv->eng.release();
+  sv->small.release();
+  if (sv->small_st) cudaStreamDestroy(sv->small_st);
   delete sv;
 }
 

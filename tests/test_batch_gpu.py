@@ -161,3 +161,36 @@ def test_server_fair_schedule_finishes_small_requests_first_with_the_same_result
     assert all(allr[k] == results[("all", k)][1]["evals"] for k in range(len(reqs)))
     # fair: the small requests finish before the large one
     assert max(fair[k] for k in (1, 2, 3)) < fair[0]
+
+
+def test_server_lanes_run_small_requests_alongside_large_ones_with_the_same_results():
+    # Two large requests and four small ones under GS_SCHED_LANES (lane_split
+    # 1000): the small ones run in the second engine, on their own stream and
+    # host thread, during the large lane's rounds, so they finish in fewer
+    # server steps than the large ones; every result is bitwise the one of a
+    # packed batch (the iterates depend on neither the schedule nor the lane).
+    big = problems(2, seed0=95, n_lo=6000, n_hi=8000)
+    small = problems(4, seed0=96, n_lo=300, n_hi=600)
+    reqs = big + small
+    ref = gs().register_batch(reqs, T=4, max_iter=10, grad_tol=0.0)
+    sv = gs().Server(T=4, max_iter=10, grad_tol=0.0, memory_budget=512 << 20, max_problems=8, schedule="lanes",
+                     lane_split=1000)
+    ids = [sv.submit(p["q0"], p["target"], p["sigma"], p["lam"]) for p in reqs]
+    steps, fin, out = 0, {}, {}
+    while len(fin) < len(ids) and steps < 500:
+        sv.step()
+        steps += 1
+        for k, rid in enumerate(ids):
+            if k not in fin:
+                o = sv.poll(rid)
+                if o is not None:
+                    fin[k], out[k] = steps, o
+    stats = sv.stats()
+    sv.close()
+    print("lanes: finished at step", fin)
+    assert len(fin) == len(ids)
+    for k in range(len(reqs)):
+        assert np.array_equal(out[k][0], ref[k][0]) and out[k][1]["loss"] == ref[k][1]["loss"], k
+        assert out[k][2][0] >= out[k][2][1] > 0
+    assert max(fin[k] for k in range(2, 6)) < min(fin[0], fin[1])
+    assert stats["capacity_landmarks"] > 0

@@ -94,10 +94,15 @@ def test_invalid_dimension_and_server_schedule_are_rejected():
         assert lib.shoot_forward(ctypes.byref(prm), P(q), P(q), P(q), P(q), None, None) == -1
         assert b"dim" in lib.gs_last_error()
     cfg = gsh.GsServerConfig(T=4, lbfgs_m=10, max_iter=1, max_problems=1, grad_tol=0.0, memory_budget=1 << 20,
-                             stream=None, schedule=7, reserved=0)
+                             stream=None, schedule=7, lane_split=0)
     h = ctypes.c_void_p(0)
     assert lib.gs_server_create(ctypes.byref(cfg), ctypes.byref(h)) == -1
     assert b"schedule" in lib.gs_last_error()
+    # a lane threshold only with the two-lane schedule, and never negative
+    for sched, split in ((1, 4096), (2, -1)):
+        cfg.schedule, cfg.lane_split = sched, split
+        assert lib.gs_server_create(ctypes.byref(cfg), ctypes.byref(h)) == -1
+        assert b"lane_split" in lib.gs_last_error()
     with pytest.raises(ValueError):
         gsh.Server(T=4, schedule="sometimes")
 

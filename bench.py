@@ -818,8 +818,7 @@ def run_workload(args, dist):
         metric = "registrations/s (one template to 34 subjects, N=1847, T=40, packed)"
         value, ms = res["packed_regs_per_s"], res["packed_s"] * 1e3
     else:
-        res = measure_served(gsh, args.served_count or 64)
-        res["schedule_all"] = measure_served(gsh, args.served_count or 64, schedule="all")
+        res = measure_served_vs_plain(gsh, args.served_count or 64)
         metric = "served registrations/s (Poisson 200/s, N~LogU[1000,50000], T=20)"
         value, ms = res["regs_per_s"], res["makespan_s"] * 1e3
     line = {"metric": metric, "value": value * dist.world, "unit": "regs/s", "n_gpus": dist.world, "steps": 1,

@@ -660,9 +660,11 @@ def _timed_gradients(lib, prm, bufs, stream, reps, flush):
 
 
 def roofline_at(gsh, lib, dev, n, peak, mufu_peak, T=T_STEPS, sigma=0.05, reps=8):
-    """The step kernels' roofline at a larger N (the spec bar is set
-    at N >= 16384): whole gradients of an ellipsoid workload (sigma = 0.05,
-    T = 20), per-launch times from the graph's phase events (sweep / T)."""
+    """The step kernels' roofline at a larger N (16384 landmarks: several
+    waves per launch, where the pair loops rather than the fixed per-launch
+    costs set the time): whole gradients of an ellipsoid workload
+    (sigma = 0.05, T = 20), per-launch times from the graph's phase events
+    (sweep / T)."""
     import torch
     q, p, t = _grad_inputs(dev, n)
     bufs = (q, p, t, torch.empty_like(q), torch.empty_like(q))

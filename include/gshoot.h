@@ -274,7 +274,8 @@ typedef struct gs_server_config {
  * and a small request finishes after its own work instead of the largest
  * request's.  Under GS_SCHED_LANES the server keeps two engines: requests of
  * at most lane_split landmarks go to a small lane (a quarter of the memory
- * budget, the fair schedule, a stream of its own), the others to a large
+ * budget, the fair schedule, a stream of its own at the device's highest
+ * priority), the others to a large
  * lane (the rest of the budget, every resident request in every round, on
  * `stream`).  gs_server_step runs one round of the large lane and, on a
  * second host thread at the same time, as many rounds of the small lane as

@@ -1070,7 +1070,12 @@ gs_status gs_server_create(const gs_server_config* cfg, gs_server** out) {
     sv->eng.schedule = GS_SCHED_ALL;
     sv->small.schedule = GS_SCHED_FAIR;
     const uint64_t small_budget = cfg->memory_budget / 4;
-    cudaError_t e = cudaStreamCreateWithFlags(&sv->small_st, cudaStreamNonBlocking);
+    // The small lane's stream has the device's highest priority: its short
+    // kernels take SM slots as the large lane's CTAs finish instead of
+    // queueing behind every CTA of a large launch.
+    int least = 0, greatest = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&sv->small_st, cudaStreamNonBlocking, greatest);
     if (e != cudaSuccess) {
       gs::set_last_error(cudaGetErrorString(e));
       delete sv;

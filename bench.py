@@ -438,6 +438,7 @@ def measure_served(gsh, count, max_iter=200, budget=120 << 30, rate=200.0, T=T_S
         "timing": "wall clock from arrival to result, host inputs, queueing included",
         "per_request": [{"N": ns[k], "iters": infos[k]["iters"], "evals": infos[k]["evals"],
                          "status": infos[k]["status"], "loss": infos[k]["loss"],
+                         "grad_ratio": infos[k]["grad_norm"] / max(infos[k]["grad_norm0"], 1e-300),
                          "avg_dist": infos[k]["avg_dist"], "max_dist": infos[k]["max_dist"],
                          "latency_s": float(lat[k]), "service_s": float(svc[k]),
                          "queue_s": float(lat[k] - svc[k])} for k in range(count)],

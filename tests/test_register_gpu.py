@@ -80,3 +80,29 @@ def test_register_rejects_bad_memory():
     q0, t = case(n=64)
     with pytest.raises(gs().GShootError):
         gs().register(q0, t, 5, 0.2, 10.0, m=0)
+
+
+def test_register_stops_at_grad_tol_like_the_oracle():
+    # The stopping rule ||g|| <= grad_tol ||g0||: the oracle stops this case
+    # (256 landmarks, sigma = 0.2, lambda = 10, T = 10) after 32 iterations at
+    # grad_tol 1e-3.  Single-problem, packed and served runs stop there too,
+    # with status 0 (converged), before max_iter.
+    q0, t = case()
+    r = oracle.register(q0.astype(np.float64), t.astype(np.float64), 10, 0.2, 10.0, max_iter=500, grad_tol=1e-3)
+    assert r["status"] == 0 and r["iters"] < 500
+    _, info = gs().register(q0, t, 10, 0.2, 10.0, max_iter=500, grad_tol=1e-3)
+    (_, binfo), = gs().register_batch([dict(q0=q0, target=t, sigma=0.2, lam=10.0)], T=10, max_iter=500,
+                                      grad_tol=1e-3)
+    sv = gs().Server(T=10, max_iter=500, grad_tol=1e-3, memory_budget=256 << 20, max_problems=4)
+    rid = sv.submit(q0, t, 0.2, 10.0)
+    while sv.poll(rid) is None:
+        sv.step()
+    sinfo = sv.poll(rid)[1]
+    sv.close()
+    for name, inf in (("register", info), ("register_batch", binfo), ("server", sinfo)):
+        print(name, inf["iters"], inf["status"], inf["grad_norm"] / inf["grad_norm0"])
+        assert inf["status"] == 0, name
+        assert inf["grad_norm"] <= 1e-3 * inf["grad_norm0"], name
+        assert abs(inf["iters"] - r["iters"]) <= 3, name
+        assert abs(inf["loss"] - r["f"]) < 1e-4 * r["f"], name
+    assert sinfo["iters"] == binfo["iters"] and sinfo["loss"] == binfo["loss"]  # the server runs the packed path

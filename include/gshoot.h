@@ -345,9 +345,10 @@ gs_status gs_time_pair_kernels(const gs_params* prm, const float* q0, const floa
  * uses a file-scope static device array of about 3.3 MB as its scratch.  It
  * never calls cudaMalloc, cudaFree or any allocating routine.
  *
- * Limits: 1 <= N <= 8192.  Larger N is rejected with GS_EINVAL before any
- *   cudaPointerGetAttributes and stages host arrays through its own device
- *   workspace.  Device memory must belong to the current device (the one
+ * Limits: 1 <= N <= 8192.  Larger N is rejected with GS_EINVAL.  q, p, Hq
+ *   and Hp must be device arrays: unlike step_forward, which stages host
+ *   arrays through its own device workspace, this entry point rejects host
+ *   memory with GS_EINVAL.  Device memory must belong to the current device (the one
  *   cudaSetDevice selected in the calling thread): memory of another GPU is
  *   rejected with GS_EINVAL, because this device's kernels cannot safely
  *   read it.  The caller owns every array; the library never keeps a pointer
@@ -355,8 +356,9 @@ gs_status gs_time_pair_kernels(const gs_params* prm, const float* q0, const floa
  * Memory: every GPU that loads the library holds the static array until the
  *   process exits.
  * Set-up: the first call on each device looks up the array's device address
- *   (cudaGetSymbolAddress, with that device current).  Make that first call
- *   before any stream capture begins.
+ *   (cudaGetSymbolAddress, with that device current).
+ * Every call classifies its pointers with cudaPointerGetAttributes, and reads
+ *   the device status word back into host memory.
  * Sharing: every call on a device uses the same array.  Each call clears the
  *   status word and rewrites the rest of the scratch it reads.  Calls whose
  *   work overlaps on the GPU (different streams or host threads) race on the

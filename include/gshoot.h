@@ -556,10 +556,31 @@ int32_t gs_pointer_rule(int32_t type, int32_t ptr_device, int32_t current_device
  */
 gs_status gs_measure_peaks(double* rates, double* ms_out, double target_ms, void* stream);
 
+/*
+ * gs_measure_pair_loop — diagnostics (no counterpart in the paper): the
+ * inner loop of the pair sums alone, at a chosen number of warps per SM.
+ * kind 0 runs the StepForward loop (16 paired FP32 instructions per source
+ * record of two landmarks), kind 1 the StepBackward loop (36).  Every SM
+ * holds `ctas_per_sm` CTAs of `threads` threads (a multiple of 32, at most
+ * 256; threads * ctas_per_sm <= 1024, and all of them resident at once, or
+ * GS_EINVAL); each thread holds one target and runs the loop `reps` times
+ * (1 to 4096) over 64 records (128 sources) in shared memory, with no
+ * copies, barriers or epilogue.  *cycles_per_record (host): the median over
+ * CTAs of the loop's SM clock cycles divided by reps * 64, i.e. the cycles
+ * one warp takes per record while sharing its scheduler with the other warps
+ * of the SM (warps per scheduler = threads * ctas_per_sm / 128).  The FP32
+ * pipe's share of the time is then 2 * instructions * warps per scheduler /
+ * cycles_per_record.  Synchronises `stream`; allocates and frees its own
+ * small buffers.
+ */
+gs_status gs_measure_pair_loop(int32_t kind, int32_t threads, int32_t ctas_per_sm, int32_t reps,
+                               double* cycles_per_record, void* stream);
+
 /* Library ABI version: 100 * major + minor (101: gs_params gained
  * integrator and kinetic_at; 102: dim; 103: gs_server_config.schedule;
  * 104: gs_set_step_table; 105: gs_step_config; 106: gs_pointer_rule,
- * gs_measure_peaks, gs_set_combine_precision, gs_set_batch_config). */
+ * gs_measure_peaks, gs_set_combine_precision, gs_set_batch_config; 107:
+ * gs_measure_pair_loop). */
 int32_t gs_version(void);
 
 #ifdef __cplusplus

@@ -963,6 +963,6 @@ int32_t gs_pointer_rule(int32_t type, int32_t ptr_device, int32_t current_device
   return static_cast<int32_t>(gs::classify_pointer(type, ptr_device, current_device));
 }
 
-int32_t gs_version(void) { return 106; }
+int32_t gs_version(void) { return 107; }
 
 }  // extern "C"

@@ -16,8 +16,12 @@
 // on the caller's stream.  The best of three timed launches is reported.
 #include <cmath>
 
+#include <algorithm>
+#include <vector>
+
 #include "engine.h"
 #include "gs_device.cuh"
+#include "pair_tile.cuh"
 
 namespace gs {
 namespace {
@@ -114,6 +118,48 @@ gs_status time_unit(int which, int iters, int blocks, float* sink, cudaStream_t 
   return GS_OK;
 }
 
+// The inner loop of the pair tiles alone: one target per thread against
+// kLoopRecords source records (two sources each) held in shared memory,
+// `reps` times, with no copies, cluster barriers or epilogue.  Thread 0 of
+// each CTA records the clock cycles of its CTA's loop, which the host turns
+// into cycles per record per warp at a given number of CTAs per SM.
+constexpr int kLoopRecords = 64;
+
+template <bool Bwd>
+__global__ void k_loop_probe(const float4* qp, const float4* ab, int reps, long long* cycles, float* sink) {
+  __shared__ __align__(16) float4 rq[kLoopRecords * 3], ra[kLoopRecords * 3];
+  for (int i = threadIdx.x; i < kLoopRecords * 3; i += blockDim.x) {
+    rq[i] = qp[i];
+    ra[i] = ab[i];
+  }
+  __syncthreads();
+  const int target = static_cast<int>(threadIdx.x) % kLoopRecords;  // 2 * kLoopRecords sources
+  float s = 0.f;
+  const long long t0 = clock64();
+  if constexpr (Bwd) {
+    BwdTile<1, 3> t;
+    t.load(qp, ab, target, kLoopRecords, 2 * kLoopRecords);
+    const float4* bufs[2] = {rq, ra};
+    for (int r = 0; r < reps; ++r) t.consume(bufs, 0, 2 * kLoopRecords);
+    __syncthreads();
+    ds w[6];
+    t.result(0, 1.0f, 0.5f, w);
+    for (int k = 0; k < 6; ++k) s += w[k].hi;
+  } else {
+    FwdTile<1, 3> t;
+    t.load(qp, target, kLoopRecords, 2 * kLoopRecords);
+    const float4* bufs[1] = {rq};
+    for (int r = 0; r < reps; ++r) t.consume(bufs, 0, 2 * kLoopRecords);
+    __syncthreads();
+    ds w[6];
+    t.result(0, 1.0f, w);
+    for (int k = 0; k < 6; ++k) s += w[k].hi;
+  }
+  const long long t1 = clock64();
+  if (s == -1.0f) sink[0] = s;  // keeps the sums live; sink is a scratch word nobody reads
+  if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+}
+
 }  // namespace
 }  // namespace gs
 
@@ -159,4 +205,58 @@ extern "C" gs_status gs_measure_peaks(double* rates, double* ms_out, double targ
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return s;
+}
+
+extern "C" gs_status gs_measure_pair_loop(int32_t kind, int32_t threads, int32_t ctas_per_sm, int32_t reps,
+                                          double* cycles_per_record, void* stream) {
+  using namespace gs;
+  set_last_error("");
+  if (!cycles_per_record) return fail(GS_EINVAL, "cycles_per_record is NULL");
+  if (kind != 0 && kind != 1) return fail(GS_EINVAL, "kind must be 0 (StepForward) or 1 (StepBackward)");
+  if (threads < 32 || threads > 256 || threads % 32 != 0) return fail(GS_EINVAL, "threads must be 32, 64, ..., 256");
+  if (ctas_per_sm < 1 || ctas_per_sm > 16 || threads * ctas_per_sm > 1024)
+    return fail(GS_EINVAL, "ctas_per_sm must be in [1, 16] with threads * ctas_per_sm <= 1024");
+  if (reps < 1 || reps > 4096) return fail(GS_EINVAL, "reps must be in [1, 4096]");
+  const auto kern = kind == 1 ? k_loop_probe<true> : k_loop_probe<false>;
+  int dev = 0, sms = 0, fit = 0;
+  GS_CUDA(cudaGetDevice(&dev));
+  GS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  GS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, kern, threads, 0));
+  if (fit < ctas_per_sm) return fail(GS_EINVAL, "that many CTAs of the probe are not resident on an SM at once");
+  const int blocks = sms * ctas_per_sm;
+  // Source records of a smooth synthetic cloud: q~ in [-0.9, 0.9], p, alpha
+  // and b~ in [-0.1, 0.1] (every exponent stays in the normal range).
+  std::vector<float4> hq(kLoopRecords * 3), ha(kLoopRecords * 3);
+  for (int i = 0; i < kLoopRecords * 3; ++i) {
+    const float x = static_cast<float>(i);
+    hq[i] = make_float4(0.9f * std::sin(1.7f * x), 0.9f * std::sin(2.3f * x + 1.f), 0.1f * std::cos(0.7f * x),
+                        0.1f * std::cos(1.1f * x + 2.f));
+    ha[i] = make_float4(0.1f * std::sin(0.3f * x), 0.1f * std::cos(0.9f * x), 0.1f * std::sin(1.3f * x + 0.5f),
+                        0.1f * std::cos(0.5f * x + 1.5f));
+  }
+  float4 *dq = nullptr, *da = nullptr;
+  long long* dc = nullptr;
+  float* sink = nullptr;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMalloc(&dq, sizeof(float4) * hq.size());
+  if (e == cudaSuccess) e = cudaMalloc(&da, sizeof(float4) * ha.size());
+  if (e == cudaSuccess) e = cudaMalloc(&dc, sizeof(long long) * blocks);
+  if (e == cudaSuccess) e = cudaMalloc(&sink, sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dq, hq.data(), sizeof(float4) * hq.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(da, ha.data(), sizeof(float4) * ha.size(), cudaMemcpyHostToDevice, st);
+  std::vector<long long> hc(blocks);
+  for (int run = 0; run < 2 && e == cudaSuccess; ++run) {  // the first launch warms up
+    kern<<<blocks, threads, 0, st>>>(dq, da, reps, dc, sink);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), dc, sizeof(long long) * blocks, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(dq);
+  cudaFree(da);
+  cudaFree(dc);
+  cudaFree(sink);
+  if (e != cudaSuccess) return fail(GS_ECUDA, cudaGetErrorString(e));
+  std::sort(hc.begin(), hc.end());
+  *cycles_per_record = static_cast<double>(hc[blocks / 2]) / (static_cast<double>(reps) * kLoopRecords);
+  return GS_OK;
 }

@@ -26,6 +26,11 @@ fastest cluster size for the full-size CTAs (the only ones the RK4, terminal
 and planar kernels exist for).  The cluster size fixes how a target's sum is split, so the table
 also fixes the rounding of every result: it is measured offline once per
 GPU model and never at run time.
+
+`--batch-shapes` times whole packed registrations for every packed launch
+shape.  `--pair-loop` times the inner loops of the pair sums alone
+(gs_measure_pair_loop) at 0.5 to 4 warps per scheduler, which separates the
+loop's own issue limits from the fixed costs of a launch.
 """
 from __future__ import annotations
 
@@ -71,6 +76,9 @@ def main():
                          "(N log-uniform in [1000, 50000])")
     ap.add_argument("--batch-count", type=int, default=128, help="--batch-shapes: problems of the batched mix")
     ap.add_argument("--batch-iters", type=int, default=20, help="--batch-shapes: L-BFGS iterations per problem")
+    ap.add_argument("--pair-loop", action="store_true",
+                    help="time the pair sums' inner loops alone (gs_measure_pair_loop) at 0.5 to 4 warps per "
+                         "scheduler")
     args = ap.parse_args()
     import torch
 
@@ -84,6 +92,9 @@ def main():
         return
     if args.batch_shapes:
         batch_shapes(lib, args.batch_count, args.batch_iters)
+        return
+    if args.pair_loop:
+        pair_loop(lib, stream)
         return
     for n in args.n:
         pr = ls.ellipsoid_pair(n, seed=0, n_bumps=8)
@@ -153,6 +164,31 @@ def main():
 # packed launch shapes (threads, cluster) per kind; a cluster must divide the CTA
 BATCH_FWD = [(128, 8), (128, 4), (128, 16), (64, 8), (64, 16), (64, 4)]
 BATCH_BWD = [(64, 8), (64, 4), (64, 16), (32, 8), (32, 16), (32, 4)]
+
+
+# Paired FP32 instructions per source record (two landmarks) of each loop.
+LOOP_INSTR = {0: 16, 1: 36}
+
+
+def pair_loop(lib, stream, reps=64):
+    """One JSON line per (kernel, CTA size, CTAs per SM): cycles per record per
+    warp, warps per scheduler, and the FP32 pipe's share of the loop's time
+    (each paired instruction holds the pipe for two cycles)."""
+    for kind in (0, 1):
+        for threads in (64, 128):
+            for ctas in (1, 2, 3, 4, 6, 8):
+                if threads * ctas > 1024:
+                    continue
+                cyc = ctypes.c_double(0)
+                wps = threads * ctas / 128.0
+                if lib.gs_measure_pair_loop(kind, threads, ctas, reps, ctypes.byref(cyc), stream) != 0:
+                    print(json.dumps({"kernel": ("StepForward", "StepBackward")[kind], "threads": threads,
+                                      "ctas_per_sm": ctas, "skipped": lib.gs_last_error().decode()}), flush=True)
+                    continue
+                print(json.dumps({"kernel": ("StepForward", "StepBackward")[kind], "threads": threads,
+                                  "ctas_per_sm": ctas, "warps_per_scheduler": wps,
+                                  "cycles_per_record_per_warp": round(cyc.value, 1),
+                                  "fp32_pipe_share": round(2 * LOOP_INSTR[kind] * wps / cyc.value, 3)}), flush=True)
 
 
 def batch_shapes(lib, count, iters, reps=3):

@@ -294,3 +294,14 @@ def test_combine_precision_switch_validates_its_argument():
         assert lib.gs_set_combine_precision(-1) == -1
     finally:
         assert lib.gs_set_combine_precision(0) == 0
+
+
+def test_pair_loop_probe_rejects_bad_arguments():
+    import ctypes
+    import paper_1907_04839_gb300 as gsh
+    lib = gsh.load()
+    c = ctypes.c_double(0)
+    for args in ((2, 64, 1, 1), (1, 48, 1, 1), (1, 288, 1, 1), (1, 256, 8, 1), (1, 64, 0, 1), (1, 64, 1, 0),
+                 (1, 64, 1, 5000)):
+        assert lib.gs_measure_pair_loop(*args, ctypes.byref(c), None) == -1, args
+    assert lib.gs_measure_pair_loop(1, 64, 1, 1, None, None) == -1

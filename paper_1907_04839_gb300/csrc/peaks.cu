@@ -120,13 +120,15 @@ gs_status time_unit(int which, int iters, int blocks, float* sink, cudaStream_t 
 
 // The inner loop of the pair tiles alone: one target per thread against
 // kLoopRecords source records (two sources each) held in shared memory,
-// `reps` times, with no copies, cluster barriers or epilogue.  Thread 0 of
+// `reps` times, with no copies, cluster barriers or epilogue.  The source
+// count arrives as a kernel argument (nsrc = 2 * kLoopRecords), so the loop
+// is compiled with run-time bounds, as in the step kernels.  Thread 0 of
 // each CTA records the clock cycles of its CTA's loop, which the host turns
 // into cycles per record per warp at a given number of CTAs per SM.
 constexpr int kLoopRecords = 64;
 
 template <bool Bwd>
-__global__ void k_loop_probe(const float4* qp, const float4* ab, int reps, long long* cycles, float* sink) {
+__global__ void k_loop_probe(const float4* qp, const float4* ab, int nsrc, int reps, long long* cycles, float* sink) {
   __shared__ __align__(16) float4 rq[kLoopRecords * 3], ra[kLoopRecords * 3];
   for (int i = threadIdx.x; i < kLoopRecords * 3; i += blockDim.x) {
     rq[i] = qp[i];
@@ -140,7 +142,7 @@ __global__ void k_loop_probe(const float4* qp, const float4* ab, int reps, long 
     BwdTile<1, 3> t;
     t.load(qp, ab, target, kLoopRecords, 2 * kLoopRecords);
     const float4* bufs[2] = {rq, ra};
-    for (int r = 0; r < reps; ++r) t.consume(bufs, 0, 2 * kLoopRecords);
+    for (int r = 0; r < reps; ++r) t.consume(bufs, 0, nsrc);
     __syncthreads();
     ds w[6];
     t.result(0, 1.0f, 0.5f, w);
@@ -149,7 +151,7 @@ __global__ void k_loop_probe(const float4* qp, const float4* ab, int reps, long 
     FwdTile<1, 3> t;
     t.load(qp, target, kLoopRecords, 2 * kLoopRecords);
     const float4* bufs[1] = {rq};
-    for (int r = 0; r < reps; ++r) t.consume(bufs, 0, 2 * kLoopRecords);
+    for (int r = 0; r < reps; ++r) t.consume(bufs, 0, nsrc);
     __syncthreads();
     ds w[6];
     t.result(0, 1.0f, w);
@@ -246,7 +248,7 @@ extern "C" gs_status gs_measure_pair_loop(int32_t kind, int32_t threads, int32_t
   if (e == cudaSuccess) e = cudaMemcpyAsync(da, ha.data(), sizeof(float4) * ha.size(), cudaMemcpyHostToDevice, st);
   std::vector<long long> hc(blocks);
   for (int run = 0; run < 2 && e == cudaSuccess; ++run) {  // the first launch warms up
-    kern<<<blocks, threads, 0, st>>>(dq, da, reps, dc, sink);
+    kern<<<blocks, threads, 0, st>>>(dq, da, 2 * kLoopRecords, reps, dc, sink);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), dc, sizeof(long long) * blocks, cudaMemcpyDeviceToHost, st);

@@ -566,9 +566,10 @@ gs_status gs_measure_peaks(double* rates, double* ms_out, double target_ms, void
  * GS_EINVAL); each thread holds one target and runs the loop `reps` times
  * (1 to 4096) over 64 records (128 sources) in shared memory, with no
  * copies, barriers or epilogue.  *cycles_per_record (host): the median over
- * CTAs of the loop's SM clock cycles divided by reps * 64, i.e. the cycles
- * one warp takes per record while sharing its scheduler with the other warps
- * of the SM (warps per scheduler = threads * ctas_per_sm / 128).  The FP32
+ * SMs of the SM clock cycles from the first CTA's loop start to the last
+ * CTA's loop end on that SM, divided by reps * 64, i.e. the cycles per record
+ * of one warp's share when the SM's warps share the schedulers (warps per
+ * scheduler = threads * ctas_per_sm / 128).  The FP32
  * pipe's share of the time is then 2 * instructions * warps per scheduler /
  * cycles_per_record.  Synchronises `stream`; allocates and frees its own
  * small buffers.

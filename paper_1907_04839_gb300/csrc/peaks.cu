@@ -17,6 +17,8 @@
 #include <cmath>
 
 #include <algorithm>
+#include <map>
+#include <utility>
 #include <vector>
 
 #include "engine.h"
@@ -123,8 +125,10 @@ gs_status time_unit(int which, int iters, int blocks, float* sink, cudaStream_t 
 // `reps` times, with no copies, cluster barriers or epilogue.  The source
 // count arrives as a kernel argument (nsrc = 2 * kLoopRecords), so the loop
 // is compiled with run-time bounds, as in the step kernels.  Thread 0 of
-// each CTA records the clock cycles of its CTA's loop, which the host turns
-// into cycles per record per warp at a given number of CTAs per SM.
+// each CTA records its SM and the SM clock at the start and the end of the
+// CTA's loop; the host takes, per SM, the span from the first start to the
+// last end, which is what the SM needs for all of its CTAs' work (warps on
+// one scheduler need not finish together).
 constexpr int kLoopRecords = 64;
 
 template <bool Bwd>
@@ -159,7 +163,13 @@ __global__ void k_loop_probe(const float4* qp, const float4* ab, int nsrc, int r
   }
   const long long t1 = clock64();
   if (s == -1.0f) sink[0] = s;  // keeps the sums live; sink is a scratch word nobody reads
-  if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+  if (threadIdx.x == 0) {
+    unsigned sm;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+    cycles[3 * blockIdx.x] = sm;
+    cycles[3 * blockIdx.x + 1] = t0;
+    cycles[3 * blockIdx.x + 2] = t1;
+  }
 }
 
 }  // namespace
@@ -242,23 +252,35 @@ extern "C" gs_status gs_measure_pair_loop(int32_t kind, int32_t threads, int32_t
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaMalloc(&dq, sizeof(float4) * hq.size());
   if (e == cudaSuccess) e = cudaMalloc(&da, sizeof(float4) * ha.size());
-  if (e == cudaSuccess) e = cudaMalloc(&dc, sizeof(long long) * blocks);
+  if (e == cudaSuccess) e = cudaMalloc(&dc, 3 * sizeof(long long) * blocks);
   if (e == cudaSuccess) e = cudaMalloc(&sink, sizeof(float));
   if (e == cudaSuccess) e = cudaMemcpyAsync(dq, hq.data(), sizeof(float4) * hq.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(da, ha.data(), sizeof(float4) * ha.size(), cudaMemcpyHostToDevice, st);
-  std::vector<long long> hc(blocks);
+  std::vector<long long> hc(3 * static_cast<size_t>(blocks));
   for (int run = 0; run < 2 && e == cudaSuccess; ++run) {  // the first launch warms up
     kern<<<blocks, threads, 0, st>>>(dq, da, 2 * kLoopRecords, reps, dc, sink);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), dc, sizeof(long long) * blocks, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), dc, 3 * sizeof(long long) * blocks, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(dq);
   cudaFree(da);
   cudaFree(dc);
   cudaFree(sink);
   if (e != cudaSuccess) return fail(GS_ECUDA, cudaGetErrorString(e));
-  std::sort(hc.begin(), hc.end());
-  *cycles_per_record = static_cast<double>(hc[blocks / 2]) / (static_cast<double>(reps) * kLoopRecords);
+  // Per SM: first start to last end of its CTAs' loops (one SM clock).
+  std::map<long long, std::pair<long long, long long>> span;
+  for (int b = 0; b < blocks; ++b) {
+    const long long sm = hc[3 * b], t0 = hc[3 * b + 1], t1 = hc[3 * b + 2];
+    auto it = span.find(sm);
+    if (it == span.end())
+      span.emplace(sm, std::make_pair(t0, t1));
+    else
+      it->second = std::make_pair(std::min(it->second.first, t0), std::max(it->second.second, t1));
+  }
+  std::vector<long long> per_sm;
+  for (const auto& kv : span) per_sm.push_back(kv.second.second - kv.second.first);
+  std::sort(per_sm.begin(), per_sm.end());
+  *cycles_per_record = static_cast<double>(per_sm[per_sm.size() / 2]) / (static_cast<double>(reps) * kLoopRecords);
   return GS_OK;
 }

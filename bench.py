@@ -249,14 +249,19 @@ def measure_peaks(lib, stream_ptr, uuid):
     clocks = ClockSampler(uuid)
     clocks.start()
     st = lib.gs_measure_peaks(rates, kms, ctypes.c_double(50.0), stream_ptr)
+    distinct = ctypes.c_double(0.0)
+    st2 = lib.gs_measure_ffma2_distinct(ctypes.byref(distinct), ctypes.c_double(50.0), stream_ptr)
     clk = clocks.stop()
     if st != 0:
         return None
     return {"ffma_tflops": rates[0], "ffma2_tflops": rates[1], "fp32_tflops": max(rates[0], rates[1]),
+            "ffma2_distinct_operands_tflops": distinct.value if st2 == 0 else None,
             "mufu_ex2_per_s": rates[2], "fp64_tflops": rates[3], "kernel_ms": [round(x, 3) for x in kms],
             "sm_mhz": clk.get("sm_mhz"), "clock_reasons": clk.get("reasons"),
             "basis": "gs_measure_peaks: 8 independent chains per thread, 4 x 256-thread CTAs per SM, "
-                     "best of 3 launches of ~50 ms (CUDA events)"}
+                     "best of 3 launches of ~50 ms (CUDA events); ffma2_distinct_operands_tflops: the same "
+                     "FFMA2 chains with three distinct register operands per instruction "
+                     "(gs_measure_ffma2_distinct)"}
 
 
 # ---------------------------------------------------------------- CPU oracle
@@ -990,6 +995,12 @@ def run_gshoot(args, dist):
         "peaks": peaks_meas,
         "combine": None if args.no_samples else measure_combine(gsh, lib, dev),
     }
+    distinct = (peaks_meas or {}).get("ffma2_distinct_operands_tflops")
+    if distinct:
+        # the same lane-operation rates against FFMA2 with three distinct register operands
+        roofline["fp32_pipe_frac_vs_distinct_operand_ffma2"] = roofline["fp32_pipe_frac"] * peak / distinct
+        roofline["forward"]["fp32_pipe_frac_vs_distinct_operand_ffma2"] = (
+            roofline["forward"]["fp32_pipe_frac"] * peak / distinct)
     roofline_large = None if args.no_samples else roofline_at(gsh, lib, dev, 16384, peak, mufu_peak)
     line = {
         "metric": METRIC, "value": value, "unit": "grad-evals/s", "n_gpus": dist.world, "steps": K,

@@ -557,6 +557,17 @@ int32_t gs_pointer_rule(int32_t type, int32_t ptr_device, int32_t current_device
 gs_status gs_measure_peaks(double* rates, double* ms_out, double target_ms, void* stream);
 
 /*
+ * gs_measure_ffma2_distinct — diagnostics (no counterpart in the paper): the
+ * paired FP32 FFMA2 rate, TFLOP/s (host double), measured as in
+ * gs_measure_peaks but with three distinct register operands in every
+ * instruction (each of the 8 chains has its own multiplier and addend).
+ * gs_measure_peaks' rates[1] shares the multiplier and addend across all
+ * instructions.  Synchronises `stream`.  GS_EINVAL for a NULL tflops or
+ * target_ms outside [1, 2000].
+ */
+gs_status gs_measure_ffma2_distinct(double* tflops, double target_ms, void* stream);
+
+/*
  * gs_measure_pair_loop — diagnostics (no counterpart in the paper): the
  * inner loop of the pair sums alone, at a chosen number of warps per SM.
  * kind 0 runs the StepForward loop (16 paired FP32 instructions per source
@@ -581,7 +592,7 @@ gs_status gs_measure_pair_loop(int32_t kind, int32_t threads, int32_t ctas_per_s
  * integrator and kinetic_at; 102: dim; 103: gs_server_config.schedule;
  * 104: gs_set_step_table; 105: gs_step_config; 106: gs_pointer_rule,
  * gs_measure_peaks, gs_set_combine_precision, gs_set_batch_config; 107:
- * gs_measure_pair_loop). */
+ * gs_measure_pair_loop, gs_measure_ffma2_distinct). */
 int32_t gs_version(void);
 
 #ifdef __cplusplus

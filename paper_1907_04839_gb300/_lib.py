@@ -29,7 +29,7 @@ EXPORTS = [
     "gs_set_phase_timing", "gs_phase_times", "gs_set_cluster_policy", "gs_max_active_clusters",
     "gs_set_late_trigger", "gs_check_wait_timeout", "gs_set_step_table", "gs_step_config",
     "gs_pointer_rule", "gs_measure_peaks", "gs_set_combine_precision",
-    "gs_set_batch_config", "gs_measure_pair_loop",
+    "gs_set_batch_config", "gs_measure_pair_loop", "gs_measure_ffma2_distinct",
     "gs_last_error",
     "gs_release_workspace",
     "gs_version",
@@ -155,7 +155,8 @@ def _declare(lib):
                  "step_forward_noalloc", "gs_time_pair_config", "gs_set_step_config", "gs_set_phase_timing",
                  "gs_phase_times", "gs_set_cluster_policy", "gs_max_active_clusters", "gs_set_late_trigger",
                  "gs_set_step_table", "gs_step_config", "gs_check_wait_timeout", "gs_measure_peaks",
-                 "gs_set_combine_precision", "gs_set_batch_config", "gs_measure_pair_loop"):
+                 "gs_set_combine_precision", "gs_set_batch_config", "gs_measure_pair_loop",
+                 "gs_measure_ffma2_distinct"):
         getattr(lib, name).restype = ctypes.c_int
     lib.gs_last_error.restype = ctypes.c_char_p
     lib.gs_last_error.argtypes = []
@@ -166,6 +167,7 @@ def _declare(lib):
     lib.gs_pointer_rule.restype = i32
     lib.gs_pointer_rule.argtypes = [i32, i32, i32]
     lib.gs_measure_pair_loop.argtypes = [i32, i32, i32, i32, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+    lib.gs_measure_ffma2_distinct.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.c_void_p]
 
 
 def load(build_if_missing: bool = True):

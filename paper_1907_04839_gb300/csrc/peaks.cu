@@ -9,7 +9,10 @@
 //   * FFMA:  scalar FP32 fused multiply-add, 2 flops each;
 //   * FFMA2: the paired form (one instruction, two lanes), 2 flops per lane;
 //   * EX2:   MUFU ex2.approx.ftz.f32, results per second;
-//   * DFMA:  FP64 fused multiply-add, 2 flops each.
+//   * DFMA:  FP64 fused multiply-add, 2 flops each;
+//   * FFMA2 with three distinct register operands per instruction (a
+//     separate entry point): the paired rate when no operand is shared
+//     between consecutive instructions.
 // Each kernel runs CH independent dependency chains per thread on every SM
 // (4 CTAs of 256 threads per SM: 8 warps per scheduler), long enough (about
 // 50 ms) that launch overhead does not count, and is timed with CUDA events
@@ -69,6 +72,30 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak_ffma2(int iters, float a,
   if (s == -1.0f) sink[0] = s;
 }
 
+// The paired form with three distinct register operands per instruction:
+// each chain has its own multiplier and addend, so no operand is shared
+// between consecutive instructions (the pair loops' pattern, where most
+// operands are per-record values).
+__global__ void __launch_bounds__(kPeakThreads) k_peak_ffma2_distinct(int iters, float a, float b, float* sink) {
+  float2 x[kChains], y[kChains], z[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) {
+    x[c] = make_float2(1e-3f * threadIdx.x + c, 2e-3f * threadIdx.x - c);
+    y[c] = make_float2(a - 1e-6f * c, a - 2e-6f * c - 1e-7f * threadIdx.x);
+    z[c] = make_float2(b + 1e-6f * c, b + 3e-6f * c + 1e-7f * threadIdx.x);
+  }
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < kInner; ++u)
+#pragma unroll
+      for (int c = 0; c < kChains; ++c) x[c] = __ffma2_rn(x[c], y[c], z[c]);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += x[c].x + x[c].y;
+  if (s == -1.0f) sink[0] = s;
+}
+
 // y <- 2^-y stays in [0.5, 1] for y in [0, 1].
 __global__ void __launch_bounds__(kPeakThreads) k_peak_ex2(int iters, float* sink) {
   float y[kChains];
@@ -111,7 +138,8 @@ gs_status time_unit(int which, int iters, int blocks, float* sink, cudaStream_t 
     case 0: k_peak_ffma<<<blocks, kPeakThreads, 0, st>>>(iters, 0.9999f, 1e-4f, sink); break;
     case 1: k_peak_ffma2<<<blocks, kPeakThreads, 0, st>>>(iters, 0.9999f, 1e-4f, sink); break;
     case 2: k_peak_ex2<<<blocks, kPeakThreads, 0, st>>>(iters, sink); break;
-    default: k_peak_dfma<<<blocks, kPeakThreads, 0, st>>>(iters, 0.9999, 1e-4, sink); break;
+    case 3: k_peak_dfma<<<blocks, kPeakThreads, 0, st>>>(iters, 0.9999, 1e-4, sink); break;
+    default: k_peak_ffma2_distinct<<<blocks, kPeakThreads, 0, st>>>(iters, 0.9999f, 1e-4f, sink); break;
   }
   GS_CUDA(cudaGetLastError());
   GS_CUDA(cudaEventRecord(e1, st));
@@ -172,6 +200,34 @@ __global__ void k_loop_probe(const float4* qp, const float4* ab, int nsrc, int r
   }
 }
 
+// Calibrate the iteration count of unit `which` to about target_ms, then
+// keep the best of three launches: TFLOP/s (ex2 results per second for
+// unit 2) in *rate, the kernel time in *ms_best.
+gs_status measure_unit(int which, int blocks, float* sink, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1,
+                       double target_ms, double* rate, double* ms_best) {
+  int iters = which == 3 ? 64 : 2048;
+  float ms = 0.f;
+  gs_status s = GS_OK;
+  for (int probe = 0; probe < 4 && s == GS_OK; ++probe) {
+    s = time_unit(which, iters, blocks, sink, st, e0, e1, &ms);
+    if (s != GS_OK || ms >= 0.5 * target_ms) break;
+    const double scale = ms > 0.01 ? target_ms / ms : 64.0;
+    iters = static_cast<int>(std::fmin(1e9, std::ceil(iters * std::fmin(scale, 64.0))));
+  }
+  float best = 1e30f;
+  for (int r = 0; r < 3 && s == GS_OK; ++r) {
+    s = time_unit(which, iters, blocks, sink, st, e0, e1, &ms);
+    best = std::fmin(best, ms);
+  }
+  if (s != GS_OK) return s;
+  const bool paired = which == 1 || which == 4;
+  const double ops = static_cast<double>(blocks) * kPeakThreads * iters * kInner * kChains * (paired ? 2 : 1);
+  const double per_s = ops / (best * 1e-3);
+  *rate = which == 2 ? per_s : 2.0 * per_s * 1e-12;
+  if (ms_best) *ms_best = best;
+  return GS_OK;
+}
+
 }  // namespace
 }  // namespace gs
 
@@ -192,28 +248,29 @@ extern "C" gs_status gs_measure_peaks(double* rates, double* ms_out, double targ
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   GS_CUDA(cudaEventCreate(&e0));
   GS_CUDA(cudaEventCreate(&e1));
-  for (int which = 0; which < 4 && s == GS_OK; ++which) {
-    // Calibrate the iteration count to about target_ms, then keep the best
-    // of three launches.
-    int iters = which == 3 ? 64 : 2048;
-    float ms = 0.f;
-    for (int probe = 0; probe < 4 && s == GS_OK; ++probe) {
-      s = time_unit(which, iters, blocks, sink, st, e0, e1, &ms);
-      if (s != GS_OK || ms >= 0.5 * target_ms) break;
-      const double scale = ms > 0.01 ? target_ms / ms : 64.0;
-      iters = static_cast<int>(std::fmin(1e9, std::ceil(iters * std::fmin(scale, 64.0))));
-    }
-    float best = 1e30f;
-    for (int r = 0; r < 3 && s == GS_OK; ++r) {
-      s = time_unit(which, iters, blocks, sink, st, e0, e1, &ms);
-      best = std::fmin(best, ms);
-    }
-    if (s != GS_OK) break;
-    const double ops = static_cast<double>(blocks) * kPeakThreads * iters * kInner * kChains * (which == 1 ? 2 : 1);
-    const double per_s = ops / (best * 1e-3);
-    rates[which] = which == 2 ? per_s : 2.0 * per_s * 1e-12;  // TFLOP/s, or ex2 results per second
-    if (ms_out) ms_out[which] = best;
-  }
+  for (int which = 0; which < 4 && s == GS_OK; ++which)
+    s = measure_unit(which, blocks, sink, st, e0, e1, target_ms, &rates[which], ms_out ? &ms_out[which] : nullptr);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return s;
+}
+
+extern "C" gs_status gs_measure_ffma2_distinct(double* tflops, double target_ms, void* stream) {
+  using namespace gs;
+  set_last_error("");
+  if (!tflops) return fail(GS_EINVAL, "tflops is NULL");
+  if (!(target_ms >= 1.0 && target_ms <= 2000.0)) return fail(GS_EINVAL, "target_ms must be in [1, 2000]");
+  std::lock_guard<std::mutex> lk(engine_mutex());
+  Workspace* w = nullptr;
+  gs_status s = get_workspace(&w);
+  if (s != GS_OK) return s;
+  if ((s = reserve(*w, kPad, 1, 1)) != GS_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float* sink = reinterpret_cast<float*>(w->status + 5);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  GS_CUDA(cudaEventCreate(&e0));
+  GS_CUDA(cudaEventCreate(&e1));
+  s = measure_unit(4, w->num_sms * kPeakCtasPerSm, sink, st, e0, e1, target_ms, tflops, nullptr);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return s;

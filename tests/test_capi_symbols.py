@@ -305,3 +305,13 @@ def test_pair_loop_probe_rejects_bad_arguments():
                  (1, 64, 1, 5000)):
         assert lib.gs_measure_pair_loop(*args, ctypes.byref(c), None) == -1, args
     assert lib.gs_measure_pair_loop(1, 64, 1, 1, None, None) == -1
+
+
+def test_distinct_operand_probe_rejects_bad_arguments():
+    import ctypes
+    import paper_1907_04839_gb300 as gsh
+    lib = gsh.load()
+    d = ctypes.c_double(0)
+    assert lib.gs_measure_ffma2_distinct(None, 20.0, None) == -1
+    assert lib.gs_measure_ffma2_distinct(ctypes.byref(d), 0.5, None) == -1
+    assert lib.gs_measure_ffma2_distinct(ctypes.byref(d), 5000.0, None) == -1

@@ -46,3 +46,13 @@ def test_pair_loop_probe_respects_the_pipe_bound(kind, instr):
         assert cyc >= 0.95 * 2 * instr * wps  # the pipe passes one paired instruction per two cycles
         assert cyc < 50 * 2 * instr * wps
     assert out[8] >= out[4] >= 0.9 * out[2]  # warps sharing a scheduler never speed one another up
+
+
+def test_distinct_operand_ffma2_rate_is_below_the_shared_operand_rate():
+    lib, st = lib_and_stream()
+    rates = (ctypes.c_double * 4)()
+    assert lib.gs_measure_peaks(rates, None, 20.0, st) == 0, lib.gs_last_error()
+    d = ctypes.c_double(0)
+    assert lib.gs_measure_ffma2_distinct(ctypes.byref(d), 20.0, st) == 0, lib.gs_last_error()
+    print(rates[1], d.value)
+    assert 0.25 * rates[1] < d.value <= 1.02 * rates[1]

@@ -67,7 +67,7 @@ INSTR_PER_PAIR_VEL = 9
 # DRAM bytes (read + write) of one k_step_backward launch, from ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum, caches flushed before the
 # launch) of the current kernel, by N.  Empty it whenever the kernel changes.
-DRAM_BYTES_PER_BWD_LAUNCH = {4096: 430080}
+DRAM_BYTES_PER_BWD_LAUNCH = {4096: 425984}
 
 
 def parse():

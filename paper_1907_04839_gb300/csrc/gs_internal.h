@@ -28,7 +28,7 @@ enum : unsigned {
   kErrBadLaunch = 4u,  // a kernel saw an inconsistent launch configuration
 };
 
-constexpr int kPad = 64;      // landmark padding granule = source sub-block
+constexpr int kPad = 64;      // landmark padding granule
 constexpr int kChunk = 128;   // sources staged in shared memory per bulk copy
 constexpr int kStages = 4;    // chunk buffers in flight per CTA
 constexpr int kRecF4 = 3;     // float4 per pair record (two landmarks)

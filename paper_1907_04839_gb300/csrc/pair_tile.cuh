@@ -27,7 +27,10 @@
 
 namespace gs {
 
-constexpr int kSub = 64;    // sources per plain-FP32 sub-block before a Kahan fold
+// Sources per plain-FP32 sub-block before a Kahan fold: one staged chunk.
+// Measured on GB300 in whole gradients (T = 20), 128 against 64: -1.7 % at
+// N = 4096 and 16384, both kernels.
+constexpr int kSub = 128;
 constexpr int kUnroll = 8;  // split lengths are multiples of this
 
 // kStages chunk buffers for NA record arrays (kChunk sources = kChunk/2

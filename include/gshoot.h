@@ -409,7 +409,7 @@ gs_status gs_set_step_config(int32_t kind, int32_t threads, int32_t R, int32_t g
 
 /*
  * gs_set_cluster_policy — tuning (no counterpart in the paper): force the
- * cluster scheduling preference of every fused time-step launch: 0 the
+ * cluster scheduling preference of every fused time-step launch: 0 the CUDA
  * driver's default, 1 spread, 2 load balancing; -1 (the initial state)
  * restores the library's own choice, which is load balancing for grids of
  * 1.5 waves or more and spread below.  Clears the cached graphs.

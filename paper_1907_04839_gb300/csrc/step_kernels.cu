@@ -601,7 +601,7 @@ std::mutex g_attr_mu;
 std::set<const void*> g_attr_done;  // kernels allowed clusters of up to 16 CTAs
 
 // Cluster scheduling preference forced on the step kernels (-1: each
-// configuration's own; 0 the driver's default, 1 spread, 2 load balancing).
+// configuration's own; 0 the CUDA driver's default, 1 spread, 2 load balancing).
 int g_cluster_policy = -1;
 
 // Launch attributes of a step kernel: cluster shape, the scheduling policy

@@ -27,6 +27,7 @@
 #include <deque>
 #include <map>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -1155,16 +1156,22 @@ gs_status gs_server_step(gs_server* sv, int32_t* active, int32_t* queued, int32_
     // round is over (at least one).
     std::atomic<bool> large_done{false};
     gs_status s_small = GS_OK;
+    std::string why_small;  // the worker's error message (the message slot is per thread)
     const int device = sv->eng.device;
     std::thread worker([&] {
-      if (cudaSetDevice(device) != cudaSuccess) {
+      const cudaError_t e = cudaSetDevice(device);
+      if (e != cudaSuccess) {
         s_small = GS_ECUDA;
+        why_small = cudaGetErrorString(e);
         return;
       }
       do {
         std::vector<int> d;
-        if ((s_small = sv->small.round(&d)) != GS_OK) return;
-        if ((s_small = sv->small.finish(d)) != GS_OK) return;
+        if ((s_small = sv->small.round(&d)) == GS_OK) s_small = sv->small.finish(d);
+        if (s_small != GS_OK) {
+          why_small = gs_last_error();
+          return;
+        }
         done_small.insert(done_small.end(), d.begin(), d.end());
       } while (!large_done.load() && has_active(sv->small));
     });
@@ -1173,7 +1180,7 @@ gs_status gs_server_step(gs_server* sv, int32_t* active, int32_t* queued, int32_
     large_done.store(true);
     worker.join();
     if (s != GS_OK) return s;
-    if (s_small != GS_OK) return s_small;
+    if (s_small != GS_OK) return gs::fail(s_small, "small lane: " + why_small);
   } else if (run_small) {
     if ((s = sv->small.round(&done_small)) != GS_OK) return s;
     if ((s = sv->small.finish(done_small)) != GS_OK) return s;
